@@ -1,0 +1,192 @@
+/*
+ * lcs.h -- C ABI of the GB300 particle library (liblcs.so).
+ *
+ * The library advances inertial point particles through a frozen periodic
+ * Eulerian velocity field and keeps them grouped by the virtual subdomain
+ * that contains them, following Tominaga & Onishi, "LCS.jl" (arXiv
+ * 2604.11008):
+ *   - particle equations of motion, Sec. 2.2, Eqs. (5)-(6), with the drag
+ *     factor f = 1 (Stokes drag) and an optional constant gravity g;
+ *   - fluid velocity at the particle by trilinear interpolation from the
+ *     eight surrounding cell-centre values, Sec. 2.2;
+ *   - two-stage second-order Runge-Kutta time integration, Sec. 2.2 (Heun);
+ *   - periodic cube of side L with grid spacing L/N, Sec. 2.1;
+ *   - 3-D domain decomposition, Sec. 2.1, with particle migration by
+ *     mask computation -> prefix scan -> parallel pack, Sec. 2.3.3, and
+ *     unpack with compaction, Sec. 3.2.2.
+ * The P = Px*Py*Pz subdomains are virtual: they are segments of one array
+ * in one GPU's memory, and "communication" is a device-memory scatter.
+ *
+ * Conventions
+ *   - All pointers marked "device" must be CUDA device pointers of the
+ *     current device; "host" means ordinary host memory; "any" accepts both
+ *     (copied with cudaMemcpyDefault).
+ *   - Vectors are structure-of-arrays: a [3][n] double array holds all x
+ *     components, then all y, then all z.
+ *   - The field is [3][N][N][N] doubles, cell (i, j, k) of component c at
+ *     c*N^3 + i + N*(j + N*k) (x fastest); its value belongs to the cell
+ *     centre ((i+1/2)dx, (j+1/2)dx, (k+1/2)dx), dx = L/N.
+ *   - Particle i of a subdomain p = (px, py, pz) has its containing cell
+ *     c_s = min(floor(x_s * N/L), N-1) in [px*N/Px, (px+1)*N/Px) etc., and
+ *     p is numbered px + Px*(py + Py*pz).
+ *   - Every call returns an lcs_status; nothing is thrown across the ABI.
+ *     Errors detected inside kernels are latched in a device status word
+ *     and reported by the next synchronising call (lcs_sync, lcs_get_state,
+ *     lcs_backward); once an error is latched the context answers
+ *     LCS_ERR_STATE to every call except lcs_last_error and lcs_destroy.
+ *   - A context is not thread safe; all its work is ordered on the stream
+ *     given to lcs_init.
+ */
+#ifndef LCS_H_
+#define LCS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lcs_ctx lcs_ctx;
+
+typedef enum {
+  LCS_OK = 0,
+  LCS_ERR_ARG = 1,          /* invalid argument (message in lcs_last_error) */
+  LCS_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+  LCS_ERR_OOM = 3,          /* device allocation failed */
+  LCS_ERR_CAPACITY = 4,     /* a subdomain segment outgrew its capacity */
+  LCS_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
+  LCS_ERR_NONFINITE = 6,    /* a particle position or velocity became NaN/Inf */
+  LCS_ERR_DISPLACEMENT = 7, /* a particle moved by >= L/2, or beyond a neighbouring subdomain, in one step */
+  LCS_ERR_STATE = 8         /* the context holds an earlier error */
+} lcs_status;
+
+typedef enum {
+  LCS_F64 = 0,   /* field kept in FP64 (see field_kernel) */
+  LCS_F32 = 1,   /* field rounded to FP32 (nearest even); FP32 interpolation */
+  LCS_BF16 = 2   /* field rounded to BF16 (nearest even); FP32 interpolation */
+} lcs_dtype;
+
+typedef enum {
+  LCS_KERNEL_AUTO = 0,   /* library choice: LCS_KERNEL_DF for LCS_F64 */
+  LCS_KERNEL_FP64 = 1,   /* FP64 field, all arithmetic in FP64 */
+  LCS_KERNEL_DF = 2      /* FP64 field stored as an unevaluated float pair
+                            (hi + lo, 48 significant bits); interpolation in
+                            float-float arithmetic, integration in FP64 */
+} lcs_kernel;
+
+/* One ensemble: a field, its particles and its parameters. */
+typedef struct {
+  int n;                  /* grid points per axis N (the grid is N^3), >= 2 */
+  double box;             /* side L of the periodic cube (> 0) */
+  int sub[3];             /* virtual subdomains (Px, Py, Pz); N % P_s == 0 */
+  int64_t np;             /* number of particles, >= 0 */
+  lcs_dtype field_dtype;  /* storage precision of the library's field copy */
+  lcs_kernel field_kernel;/* arithmetic of the step for LCS_F64 */
+  const double *field;    /* device [3][N][N][N]; read during lcs_init only */
+  const double *x0;       /* device [3][np] positions, each in [0, L) */
+  const double *v0;       /* device [3][np] velocities */
+  const double *tau;      /* device [np] relaxation times tau_p > 0, or NULL */
+  double tau_const;       /* tau_p of every particle when tau == NULL */
+  const uint32_t *ids;    /* device [np] particle ids, or NULL for 0..np-1 */
+  double dt;              /* time step, 0 < dt <= tau_p for every particle */
+  double g[3];            /* constant acceleration added to dV/dt (gravity) */
+  int sort_every;         /* cell sort after every k-th step (0: never) */
+  int sort_brick;         /* brick edge B of the cell order (0: 8; 1: x-fastest) */
+  int track_images;       /* 1: keep per-axis periodic image counts */
+  int ckpt_every;         /* > 0: tape checkpoints every k steps for lcs_backward */
+} lcs_desc;
+
+/* Create a context for n_ens ensembles (n_ens >= 1) working on `stream`
+ * (a cudaStream_t, may be NULL for the legacy default stream).  Copies the
+ * particles into library-owned device memory, converts the field into the
+ * library's layout and precision, and places every particle in the segment
+ * of its subdomain: the particles of a subdomain keep the order in which
+ * they were given (a stable partition by subdomain).  Validates N % P_s,
+ * tau_p >= dt, positions inside [0, L) (LCS_ERR_ARG otherwise).  On success
+ * *out owns all device memory until lcs_destroy. */
+lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out);
+
+/* Enqueue nsteps time steps (asynchronous).  One step of every ensemble:
+ * interpolate, integrate (Heun) and wrap every particle, flag it by
+ * destination subdomain, and migrate (prefix scan, pack, unpack); after
+ * steps whose 1-based count is a multiple of sort_every, sort every
+ * subdomain's particles stably by cell.  The step loop is recorded once in
+ * a CUDA graph and replayed. */
+lcs_status lcs_step(lcs_ctx *ctx, int64_t nsteps);
+
+/* Standalone migration pass on the current state (asynchronous): a stable
+ * partition by destination subdomain -- each subdomain keeps its own
+ * particles in order, then receives the others in order of their source
+ * subdomain and, within one source, in storage order (Sec. 2.3.3 / 3.2.2).
+ * Works for any destinations, not only neighbours. */
+lcs_status lcs_migrate(lcs_ctx *ctx);
+
+/* Standalone cell sort (asynchronous): stable sort of every subdomain's
+ * segment by cell key.  The key orders the cells of a subdomain brick by
+ * brick (B^3 bricks, brick-major x-fastest, x-fastest inside a brick). */
+lcs_status lcs_sort(lcs_ctx *ctx);
+
+/* Replace the particles of ensemble `ens` (np unchanged).  Pointers are
+ * "any"; x and v are [3][np]; tau ([np]) is required when the context was
+ * created with per-particle tau_p and ignored otherwise; img ([3][np]
+ * int32) may be NULL (zeros).  seg (host, Ptot+1 int64) gives
+ * the segments; particles need not lie in their segment's subdomain until
+ * the next lcs_migrate.  Synchronising. */
+lcs_status lcs_set_state(lcs_ctx *ctx, int ens, const double *x, const double *v,
+                         const double *tau, const uint32_t *ids, const int32_t *img,
+                         const int64_t *seg);
+
+/* Copy the current particles of ensemble `ens` in storage order (segments
+ * contiguous, subdomain 0 first).  Pointers are "any" and may be NULL to
+ * skip an array; seg (Ptot+1 int64) receives the segment bounds.
+ * Synchronising; returns the latched device status. */
+lcs_status lcs_get_state(lcs_ctx *ctx, int ens, double *x, double *v, double *tau,
+                         uint32_t *ids, int32_t *img, int64_t *seg);
+
+/* Copy the field as the kernels of ensemble `ens` see it (after rounding to
+ * the storage precision), expanded to FP64 [3][N][N][N] ("any" pointer).
+ * Synchronising. */
+lcs_status lcs_get_field(lcs_ctx *ctx, int ens, double *out);
+
+/* Gradients of a scalar loss of the final state of ensemble 0 with respect
+ * to the field and the initial state, by the hand-written adjoint of the
+ * Heun step (reverse of the recorded steps, recomputing every segment of
+ * ckpt_every steps from its checkpoint).  Requires ckpt_every > 0 and
+ * track_images = 1 at init.  gx, gv (device [3][np], in particle-id order)
+ * hold dLoss/dX_T and dLoss/dV_T of the final unwrapped positions and
+ * velocities; gU (device [3][N][N][N], accumulated into -- zero it first),
+ * gx0 and gv0 (device [3][np], id order, overwritten) receive the
+ * gradients.  The tape covers the steps since lcs_init.  Synchronising. */
+lcs_status lcs_backward(lcs_ctx *ctx, const double *gx, const double *gv, double *gU,
+                        double *gx0, double *gv0);
+
+/* Wait for all enqueued work; return the latched device status. */
+lcs_status lcs_sync(lcs_ctx *ctx);
+
+/* Human-readable description of the last error of ctx (never NULL). */
+const char *lcs_last_error(lcs_ctx *ctx);
+
+/* Release every resource of ctx (NULL is ignored). */
+void lcs_destroy(lcs_ctx *ctx);
+
+/* Number of kernel launches enqueued by ctx since lcs_init. */
+int64_t lcs_launch_count(lcs_ctx *ctx);
+
+/* Stable partition of n keys into nbins bins -- a counting sort; the
+ * paper's mask -> prefix scan -> parallel pack (Sec. 2.3.3) is the case
+ * nbins = 2, where the rank of a mask-1 element within bin 1 is its
+ * exclusive scan value.  perm[r] receives the index of the key placed at
+ * rank r (bins ascending, equal keys in input order); bin_off (nbins+1)
+ * receives the bin starts.  keys, perm, bin_off are device pointers;
+ * 1 <= nbins <= 65536, 0 <= n < 2^31.  A key >= nbins is placed in bin
+ * nbins-1 and, if status (device int32, may be NULL) is given, LCS_ERR_ARG
+ * is written there (LCS_OK otherwise).  Scratch is allocated and freed with
+ * cudaMallocAsync / cudaFreeAsync on `stream`.  Asynchronous. */
+lcs_status lcs_partition(const uint32_t *keys, int64_t n, int nbins, uint32_t *perm,
+                         int64_t *bin_off, int32_t *status, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LCS_H_ */

@@ -1,0 +1,258 @@
+"""GB300 particle library: thin Python binding over the C ABI of liblcs.so.
+
+Everything that computes runs in the CUDA kernels behind ``include/lcs.h``;
+this module only marshals arguments (torch CUDA tensors for device memory,
+torch's current stream for ordering).  There is no CPU fallback: if the
+compiled library is missing, importing the binding's entry points raises.
+
+Method: Tominaga & Onishi, "LCS.jl" (arXiv 2604.11008) -- inertial particles
+with Stokes drag (Eqs. 5-6, f = 1) and gravity, trilinear interpolation
+from cell-centre values and two-stage RK2 (Sec. 2.2), periodic cube
+(Sec. 2.1), and prefix-scan particle migration between subdomains
+(Sec. 2.3.3), here between virtual subdomains in one GPU's memory.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblcs.so")
+
+LCS_OK, LCS_ERR_ARG, LCS_ERR_CUDA, LCS_ERR_OOM, LCS_ERR_CAPACITY = 0, 1, 2, 3, 4
+LCS_ERR_TIMEOUT, LCS_ERR_NONFINITE, LCS_ERR_DISPLACEMENT, LCS_ERR_STATE = 5, 6, 7, 8
+STATUS_NAMES = {0: "LCS_OK", 1: "LCS_ERR_ARG", 2: "LCS_ERR_CUDA", 3: "LCS_ERR_OOM",
+                4: "LCS_ERR_CAPACITY", 5: "LCS_ERR_TIMEOUT", 6: "LCS_ERR_NONFINITE",
+                7: "LCS_ERR_DISPLACEMENT", 8: "LCS_ERR_STATE"}
+DTYPES = {"f64": 0, "f32": 1, "bf16": 2}
+KERNELS = {"auto": 0, "fp64": 1, "df": 2}
+
+# Every symbol declared in include/lcs.h.
+EXPORTS = ("lcs_init", "lcs_step", "lcs_migrate", "lcs_sort", "lcs_set_state", "lcs_get_state",
+           "lcs_get_field", "lcs_backward", "lcs_sync", "lcs_last_error", "lcs_destroy",
+           "lcs_launch_count", "lcs_partition")
+
+
+class LcsError(RuntimeError):
+    def __init__(self, status: int, msg: str = ""):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+
+
+class Desc(C.Structure):
+    _fields_ = [("n", C.c_int), ("box", C.c_double), ("sub", C.c_int * 3), ("np", C.c_int64),
+                ("field_dtype", C.c_int), ("field_kernel", C.c_int), ("field", C.c_void_p),
+                ("x0", C.c_void_p), ("v0", C.c_void_p), ("tau", C.c_void_p),
+                ("tau_const", C.c_double), ("ids", C.c_void_p), ("dt", C.c_double),
+                ("g", C.c_double * 3), ("sort_every", C.c_int), ("sort_brick", C.c_int),
+                ("track_images", C.c_int), ("ckpt_every", C.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """Load liblcs.so (built by ``paper_2604_11008_gb300.build``); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"liblcs.so not built ({LIB_PATH}); run "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        P, i32, i64 = C.c_void_p, C.c_int, C.c_int64
+        L.lcs_init.argtypes = [C.POINTER(Desc), i32, P, C.POINTER(P)]
+        L.lcs_step.argtypes = [P, i64]
+        L.lcs_migrate.argtypes = [P]
+        L.lcs_sort.argtypes = [P]
+        L.lcs_set_state.argtypes = [P, i32, P, P, P, P, P, P]
+        L.lcs_get_state.argtypes = [P, i32, P, P, P, P, P, P]
+        L.lcs_get_field.argtypes = [P, i32, P]
+        L.lcs_backward.argtypes = [P, P, P, P, P, P]
+        L.lcs_sync.argtypes = [P]
+        L.lcs_last_error.argtypes = [P]
+        L.lcs_last_error.restype = C.c_char_p
+        L.lcs_destroy.argtypes = [P]
+        L.lcs_destroy.restype = None
+        L.lcs_launch_count.argtypes = [P]
+        L.lcs_launch_count.restype = i64
+        L.lcs_partition.argtypes = [P, i64, i32, P, P, P, P]
+        for name in ("lcs_init", "lcs_step", "lcs_migrate", "lcs_sort", "lcs_set_state",
+                     "lcs_get_state", "lcs_get_field", "lcs_backward", "lcs_sync",
+                     "lcs_partition"):
+            getattr(L, name).restype = i32
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(C.c_void_p)
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        t = torch.as_tensor(np.asarray(t))
+    return t.to(device="cuda", dtype=dtype).contiguous()
+
+
+class Simulator:
+    """Particles of one or more ensembles advancing in frozen periodic fields.
+
+    Parameters mirror ``lcs_desc`` of include/lcs.h.  Arrays may be numpy or
+    torch; they are copied to the current CUDA device.
+    """
+
+    def __init__(self, field, x0, v0, dt, tau=None, tau_const=0.0, g=(0.0, 0.0, 0.0),
+                 sub=(1, 1, 1), box=2 * math.pi, field_dtype="f64", kernel="auto", ids=None,
+                 sort_every=0, sort_brick=0, track_images=False, ckpt_every=0, stream=None,
+                 ensembles=None):
+        import torch
+        self._keep = []
+        self._stream = stream
+        specs = ensembles if ensembles is not None else [dict(
+            field=field, x0=x0, v0=v0, dt=dt, tau=tau, tau_const=tau_const, g=g, sub=sub,
+            box=box, field_dtype=field_dtype, kernel=kernel, ids=ids, sort_every=sort_every,
+            sort_brick=sort_brick, track_images=track_images, ckpt_every=ckpt_every)]
+        descs = (Desc * len(specs))()
+        self.meta = []
+        for k, sp in enumerate(specs):
+            f = _dev(sp["field"], torch.float64)
+            x = _dev(sp["x0"], torch.float64)
+            v = _dev(sp["v0"], torch.float64)
+            t = None if sp.get("tau") is None else _dev(sp["tau"], torch.float64)
+            i = None if sp.get("ids") is None else _dev(sp["ids"], torch.int32)
+            self._keep += [f, x, v, t, i]
+            d = descs[k]
+            d.n = int(f.shape[-1])
+            d.box = float(sp.get("box", 2 * math.pi))
+            d.sub[:] = [int(s) for s in sp.get("sub", (1, 1, 1))]
+            d.np = int(x.shape[1])
+            d.field_dtype = DTYPES[sp.get("field_dtype", "f64")]
+            d.field_kernel = KERNELS[sp.get("kernel", "auto")]
+            d.field, d.x0, d.v0 = f.data_ptr(), x.data_ptr(), v.data_ptr()
+            d.tau = t.data_ptr() if t is not None else None
+            d.tau_const = float(sp.get("tau_const", 0.0))
+            d.ids = i.data_ptr() if i is not None else None
+            d.dt = float(sp["dt"])
+            d.g[:] = [float(a) for a in sp.get("g", (0.0, 0.0, 0.0))]
+            d.sort_every = int(sp.get("sort_every", 0))
+            d.sort_brick = int(sp.get("sort_brick", 0))
+            d.track_images = int(bool(sp.get("track_images", False)))
+            d.ckpt_every = int(sp.get("ckpt_every", 0))
+            self.meta.append(dict(n=d.n, np=d.np, P=int(np.prod(d.sub[:])), has_tau=t is not None,
+                                  tau_const=d.tau_const, box=d.box))
+        self._ctx = C.c_void_p()
+        st = lib().lcs_init(descs, len(specs), _stream(stream), C.byref(self._ctx))
+        self._keep = []  # inputs are read during lcs_init only
+        if st != LCS_OK:
+            raise LcsError(st, "lcs_init failed")
+
+    # -- helpers
+    def _check(self, st):
+        if st != LCS_OK:
+            msg = lib().lcs_last_error(self._ctx).decode()
+            raise LcsError(st, msg)
+
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            lib().lcs_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- calls
+    def step(self, nsteps: int = 1):
+        self._check(lib().lcs_step(self._ctx, int(nsteps)))
+
+    def migrate(self):
+        self._check(lib().lcs_migrate(self._ctx))
+
+    def sort(self):
+        self._check(lib().lcs_sort(self._ctx))
+
+    def sync(self):
+        self._check(lib().lcs_sync(self._ctx))
+
+    @property
+    def launches(self) -> int:
+        return int(lib().lcs_launch_count(self._ctx))
+
+    def get_state(self, ens: int = 0, device: str = "cuda", out=None):
+        """Current particles in storage order: dict of x, v (3, np), tau, ids, img, seg."""
+        import torch
+        m = self.meta[ens]
+        n, P = m["np"], m["P"]
+        if out is None:
+            kw = dict(device=device)
+            if device == "cpu":
+                kw["pin_memory"] = torch.cuda.is_available()
+            out = dict(x=torch.empty((3, n), dtype=torch.float64, **kw),
+                       v=torch.empty((3, n), dtype=torch.float64, **kw),
+                       tau=torch.empty(n, dtype=torch.float64, **kw),
+                       ids=torch.empty(n, dtype=torch.int32, **kw),
+                       img=torch.empty((3, n), dtype=torch.int32, **kw))
+        seg = np.empty(P + 1, dtype=np.int64)
+        self._check(lib().lcs_get_state(self._ctx, ens, _ptr(out["x"]), _ptr(out["v"]),
+                                        _ptr(out.get("tau")), _ptr(out.get("ids")),
+                                        _ptr(out.get("img")), _ptr(seg)))
+        out["seg"] = seg
+        return out
+
+    def set_state(self, x, v, ids, seg, tau=None, img=None, ens: int = 0):
+        import torch
+        xs = _dev(x, torch.float64)
+        vs = _dev(v, torch.float64)
+        ii = _dev(ids, torch.int32)
+        tt = None if tau is None else _dev(tau, torch.float64)
+        im = None if img is None else _dev(img, torch.int32)
+        seg = np.ascontiguousarray(seg, dtype=np.int64)
+        self._check(lib().lcs_set_state(self._ctx, ens, _ptr(xs), _ptr(vs), _ptr(tt), _ptr(ii),
+                                        _ptr(im), _ptr(seg)))
+
+    def get_field(self, ens: int = 0):
+        import torch
+        n = self.meta[ens]["n"]
+        out = torch.empty((3, n, n, n), dtype=torch.float64, device="cuda")
+        self._check(lib().lcs_get_field(self._ctx, ens, _ptr(out)))
+        return out
+
+
+def partition(keys, nbins: int, stream=None):
+    """Stable partition of uint32 keys into nbins bins (counting sort).
+
+    Returns (perm, bin_off, status) as CUDA tensors; perm[r] = index of the
+    key at rank r, bin_off the bin starts, status an int32 LCS_* code."""
+    import torch
+    k = _dev(keys, torch.int32)
+    n = int(k.numel())
+    perm = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+    off = torch.empty(nbins + 1, dtype=torch.int64, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    st = lib().lcs_partition(_ptr(k), n, int(nbins), _ptr(perm), _ptr(off), _ptr(status),
+                             _stream(stream))
+    if st != LCS_OK:
+        raise LcsError(st, "lcs_partition failed")
+    return perm[:n], off, status

@@ -1,0 +1,615 @@
+// C ABI of liblcs: context creation, the captured step loop, standalone
+// migration / sort passes, state I/O and the stateless partition.
+// See include/lcs.h for the contract of every entry point.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lcs_internal.cuh"
+
+using namespace lcs;
+
+namespace lcs {
+// kernels defined in lcs_sort.cu
+__global__ void k_keys_cell(StepArgs a, uint32_t *key, uint32_t *pay, int B, int nbx, int nby);
+__global__ void k_keys_dest(StepArgs a, uint32_t *key, uint32_t *pay);
+__global__ void k_one_segment(const int64_t *cstart, int P, int64_t *cs1, int *to1);
+__global__ void k_bin_bounds(const uint32_t *key, const int64_t *cs1, int shift, int nbins,
+                             int64_t *start);
+__global__ void k_relayout(StepArgs a, int from_starts);
+__global__ void k_gather(StepArgs a, const uint32_t *pay);
+__global__ void k_set_phase(StepArgs a);
+__global__ void k_input_meta(StepArgs a, const int64_t *seg_dev);
+__global__ void k_iota(uint32_t *p, const int64_t *cstart, int P);
+__global__ void k_compact(StepArgs a, Rec out);
+__global__ void k_partition_in(const uint32_t *keys, int64_t n, uint32_t nbins, uint32_t *k,
+                               uint32_t *p, int32_t *status);
+__global__ void k_partition_tables(int64_t n, int64_t *cs1, int *to1, int32_t *status);
+}  // namespace lcs
+
+namespace {
+
+int ceil_log2(int64_t v) {
+  int b = 0;
+  while ((int64_t(1) << b) < v) ++b;
+  return b;
+}
+
+struct Ens {
+  lcs_desc d{};
+  FieldKind kind = FK_F64;
+  int64_t np = 0, cap = 0;
+  int brick = 8, nb[3] = {1, 1, 1}, key_bits = 0, mig_bits = 1;
+  int max_tiles = 0, max_stiles = 0, step_grid = 1;
+  void *field = nullptr;
+  StepArgs a{};
+  SortArgs s{};
+  int64_t *cs1 = nullptr;
+  int *to1 = nullptr;
+  int64_t steps = 0;
+};
+
+}  // namespace
+
+struct lcs_ctx {
+  std::vector<Ens> ens;
+  cudaStream_t st = nullptr;      // the caller's stream: all work runs here
+  cudaStream_t cap_st = nullptr;  // private stream used only to record graphs
+  int failed = 0;  // latched host-side status (LCS_ERR_*)
+  std::string err;
+  std::vector<void *> allocs;
+  cudaGraphExec_t g_step = nullptr, g_sort = nullptr;
+  int64_t launches = 0;
+  int sms = 152;
+};
+
+namespace {
+
+lcs_status fail(lcs_ctx *c, lcs_status s, const std::string &msg) {
+  if (c) {
+    if (!c->failed) c->failed = s;
+    c->err = msg;
+  }
+  return s;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(c, e_ == cudaErrorMemoryAllocation ? LCS_ERR_OOM : LCS_ERR_CUDA,       \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                    \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(lcs_ctx *c, T **p, int64_t n) {
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, (size_t)std::max<int64_t>(n, 1) * sizeof(T));
+  if (e == cudaSuccess) {
+    c->allocs.push_back(q);
+    *p = (T *)q;
+  }
+  return e;
+}
+
+lcs_status alloc_rec(lcs_ctx *c, Rec &r, int64_t cap, bool has_tau, bool has_img) {
+  for (int s = 0; s < 3; ++s) {
+    CK(dalloc(c, &r.x[s], cap));
+    CK(dalloc(c, &r.v[s], cap));
+    r.img[s] = nullptr;
+    if (has_img) CK(dalloc(c, &r.img[s], cap));
+  }
+  r.tau = nullptr;
+  if (has_tau) CK(dalloc(c, &r.tau, cap));
+  CK(dalloc(c, &r.id, cap));
+  return LCS_OK;
+}
+
+int grid_for(int64_t n, int block, int cap_blocks) {
+  int64_t g = (n + block - 1) / block;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, cap_blocks));
+}
+
+// The standalone migration: stable sort of the whole live set by
+// 2*dest + (dest != source), new counts from the bin starts, gather.
+lcs_status enqueue_migrate(lcs_ctx *c, Ens &e) {
+  cudaStream_t st = c->st;  // never captured
+  const int gs = grid_for(e.np, 256, c->sms * 8);
+  k_keys_dest<<<gs, 256, 0, st>>>(e.a, e.s.key[0], e.s.pay[0]);
+  k_one_segment<<<1, 1, 0, st>>>(e.a.m.cstart, e.a.geo.Ptot, e.cs1, e.to1);
+  SortArgs s = e.s;
+  s.nseg = 1, s.cstart = e.cs1, s.tile_off = e.to1;
+  int ob = 0;
+  CK(radix_sort(s, e.mig_bits, &ob, st, &c->launches));
+  k_bin_bounds<<<gs, 256, 0, st>>>(s.key[ob], e.cs1, 1, e.a.geo.Ptot, e.a.m.cstart);
+  k_relayout<<<1, 1024, 0, st>>>(e.a, 1);
+  k_gather<<<gs, 256, 0, st>>>(e.a, s.pay[ob]);
+  k_set_phase<<<1, 1024, 0, st>>>(e.a);
+  c->launches += 7;
+  CK(cudaGetLastError());
+  return LCS_OK;
+}
+
+// The cell sort: stable per-segment sort by brick-major cell key.
+lcs_status enqueue_sort(lcs_ctx *c, Ens &e, cudaStream_t st) {
+  const int gs = grid_for(e.np, 256, c->sms * 8);
+  k_keys_cell<<<gs, 256, 0, st>>>(e.a, e.s.key[0], e.s.pay[0], e.brick, e.nb[0], e.nb[1]);
+  int ob = 0;
+  CK(radix_sort(e.s, e.key_bits, &ob, st, &c->launches));
+  k_relayout<<<1, 1024, 0, st>>>(e.a, 0);
+  k_gather<<<gs, 256, 0, st>>>(e.a, e.s.pay[ob]);
+  k_set_phase<<<1, 1024, 0, st>>>(e.a);
+  c->launches += 4;
+  CK(cudaGetLastError());
+  return LCS_OK;
+}
+
+lcs_status enqueue_step(lcs_ctx *c, Ens &e, cudaStream_t st) {
+  CK(cudaMemsetAsync(e.a.m.tile_status, 0, sizeof(unsigned long long) * e.max_tiles, st));
+  CK(launch_step(e.a, e.kind, e.step_grid, st));
+  CK(launch_finish(e.a, st));
+  CK(launch_unpack(e.a, st));
+  CK(launch_flip(e.a, st));
+  c->launches += 4;
+  return LCS_OK;
+}
+
+lcs_status capture(lcs_ctx *c, bool with_sort, cudaGraphExec_t *out) {
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(c->cap_st, cudaStreamCaptureModeThreadLocal));
+  lcs_status r = LCS_OK;
+  const int64_t l0 = c->launches;
+  for (auto &e : c->ens) {
+    if (r == LCS_OK) r = enqueue_step(c, e, c->cap_st);
+    if (r == LCS_OK && with_sort && e.d.sort_every > 0) r = enqueue_sort(c, e, c->cap_st);
+  }
+  c->launches = l0;  // counted again at each replay
+  cudaError_t ee = cudaStreamEndCapture(c->cap_st, &g);
+  if (r != LCS_OK) {
+    if (g) cudaGraphDestroy(g);
+    return r;
+  }
+  CK(ee);
+  cudaError_t ie = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  CK(ie);
+  return LCS_OK;
+}
+
+int64_t launches_per_step(lcs_ctx *c, bool with_sort) {
+  int64_t n = 0;
+  for (auto &e : c->ens) {
+    n += 4;
+    if (with_sort && e.d.sort_every > 0) {
+      const int passes = e.key_bits ? (e.key_bits + SORT_MAX_BITS - 1) / SORT_MAX_BITS : 0;
+      n += 4 + 5 * passes;
+    }
+  }
+  return n;
+}
+
+lcs_status check_ctx(lcs_ctx *c) {
+  if (!c) return LCS_ERR_ARG;
+  if (c->failed) return LCS_ERR_STATE;
+  return LCS_OK;
+}
+
+lcs_status read_status(lcs_ctx *c) {
+  int dev_status = 0;
+  for (auto &e : c->ens) {
+    int v = 0;
+    CK(cudaMemcpyAsync(&v, e.a.m.status, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (v && !dev_status) dev_status = v;
+  }
+  if (dev_status) {
+    static const char *names[] = {"ok", "argument", "cuda", "out of memory", "capacity",
+                                  "timeout", "non-finite state", "displacement", "state"};
+    return fail(c, (lcs_status)dev_status,
+                std::string("device reported: ") + names[dev_status < 9 ? dev_status : 0]);
+  }
+  return LCS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out) {
+  if (!out) return LCS_ERR_ARG;
+  *out = nullptr;
+  if (!ens || n_ens < 1) return LCS_ERR_ARG;
+  lcs_ctx *c = new lcs_ctx();
+  c->st = (cudaStream_t)stream;
+  if (cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
+    delete c;
+    return LCS_ERR_CUDA;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
+  c->ens.resize(n_ens);
+  lcs_status r = LCS_OK;
+  for (int k = 0; k < n_ens && r == LCS_OK; ++k) {
+    Ens &e = c->ens[k];
+    e.d = ens[k];
+    const lcs_desc &d = e.d;
+    const int P = d.sub[0] * d.sub[1] * d.sub[2];
+    if (d.n < 2 || d.n > 1024 || !(d.box > 0) || d.np < 0 || d.np >= (int64_t(1) << 31) ||
+        d.sub[0] < 1 || d.sub[1] < 1 || d.sub[2] < 1 || d.n % d.sub[0] || d.n % d.sub[1] ||
+        d.n % d.sub[2] || P > 4096 || !(d.dt > 0) || !d.field || (d.np > 0 && (!d.x0 || !d.v0)) ||
+        (!d.tau && !(d.tau_const >= d.dt)) || d.sort_every < 0 || d.sort_brick < 0 ||
+        d.ckpt_every < 0) {
+      r = fail(c, LCS_ERR_ARG, "invalid lcs_desc for ensemble " + std::to_string(k));
+      break;
+    }
+    switch (d.field_dtype) {
+      case LCS_F64:
+        if (d.field_kernel == LCS_KERNEL_DF) {
+          r = fail(c, LCS_ERR_ARG, "LCS_KERNEL_DF is not available in this build");
+        }
+        e.kind = FK_F64;
+        break;
+      case LCS_F32: e.kind = FK_F32; break;
+      case LCS_BF16: e.kind = FK_BF16; break;
+      default: r = fail(c, LCS_ERR_ARG, "unknown field dtype");
+    }
+    if (r != LCS_OK) break;
+    e.np = d.np;
+    e.cap = d.np + d.np / 16 + (int64_t)SLACK_MIN * P + 1024;
+    Geom &g = e.a.geo;
+    g.N = d.n;
+    g.L = d.box;
+    g.inv_dx = (double)d.n / d.box;
+    g.Ptot = P;
+    for (int s = 0; s < 3; ++s) {
+      g.P[s] = d.sub[s];
+      g.W[s] = d.n / d.sub[s];
+    }
+    e.brick = d.sort_brick ? d.sort_brick : 8;
+    int64_t space = (int64_t)e.brick * e.brick * e.brick;
+    for (int s = 0; s < 3; ++s) {
+      e.nb[s] = (g.W[s] + e.brick - 1) / e.brick;
+      space *= e.nb[s];
+    }
+    if (space > (int64_t(1) << 32)) {
+      r = fail(c, LCS_ERR_ARG, "cell key space exceeds 32 bits");
+      break;
+    }
+    e.key_bits = ceil_log2(space);
+    e.mig_bits = std::max(1, ceil_log2(2 * (int64_t)P));
+    e.max_tiles = (int)(e.np / STEP_TILE + P + 2);
+    e.max_stiles = (int)(e.np / SORT_TILE + P + 2);
+    e.a.dt = d.dt;
+    e.a.half_dt = 0.5 * d.dt;
+    e.a.tau_const = d.tau ? 0.0 : d.tau_const;
+    for (int s = 0; s < 3; ++s) e.a.g[s] = d.g[s];
+    const bool has_tau = d.tau != nullptr, has_img = d.track_images != 0;
+    for (int b = 0; b < 2 && r == LCS_OK; ++b) r = alloc_rec(c, e.a.buf[b], e.cap, has_tau, has_img);
+    if (r == LCS_OK) r = alloc_rec(c, e.a.pack, e.cap, has_tau, has_img);
+    if (r != LCS_OK) break;
+    Meta &m = e.a.m;
+    auto A = [&](cudaError_t err) {
+      if (err != cudaSuccess && r == LCS_OK)
+        r = fail(c, err == cudaErrorMemoryAllocation ? LCS_ERR_OOM : LCS_ERR_CUDA,
+                 std::string("allocation: ") + cudaGetErrorString(err));
+    };
+    A(dalloc(c, &e.a.pack_bin, e.cap));
+    for (int b = 0; b < 2; ++b) {
+      A(dalloc(c, &m.lay_base[b], P));
+      A(dalloc(c, &m.lay_cap[b], P));
+    }
+    A(dalloc(c, &m.next_base, P));
+    A(dalloc(c, &m.next_cap, P));
+    A(dalloc(c, &m.cnt, P));
+    A(dalloc(c, &m.cstart, P + 1));
+    A(dalloc(c, &m.tile_off, P + 1));
+    A(dalloc(c, &m.stile_off, P + 1));
+    A(dalloc(c, &m.phase, 1));
+    A(dalloc(c, &m.status, 1));
+    A(dalloc(c, &m.tile_status, e.max_tiles));
+    A(dalloc(c, &m.tile_counter, 1));
+    A(dalloc(c, &m.bincnt, (int64_t)P * NBIN));
+    A(dalloc(c, &m.off_in, (int64_t)P * NBIN));
+    A(dalloc(c, &m.stay_tot, P));
+    A(dalloc(c, &m.mig_tot, P));
+    for (int b = 0; b < 2; ++b) {
+      A(dalloc(c, &e.s.key[b], std::max<int64_t>(e.np, 1)));
+      A(dalloc(c, &e.s.pay[b], std::max<int64_t>(e.np, 1)));
+    }
+    A(dalloc(c, &e.s.hist, (int64_t)e.max_stiles * SORT_MAX_D));
+    A(dalloc(c, &e.s.hist_scan, (int64_t)e.max_stiles * SORT_MAX_D));
+    A(dalloc(c, &e.s.scan_blocks, (int64_t)e.max_stiles * SORT_MAX_D / 4096 + 2));
+    A(dalloc(c, &e.cs1, 2));
+    A(dalloc(c, &e.to1, 2));
+    const int64_t ncell = (int64_t)d.n * d.n * d.n;
+    const int64_t fbytes = e.kind == FK_BF16 ? 8 : e.kind == FK_F32 ? 16 : 32;
+    A(dalloc(c, (char **)&e.field, ncell * fbytes));
+    if (r != LCS_OK) break;
+    e.a.field = e.field;
+    e.a.max_tiles = e.max_tiles;
+    e.a.cap = e.cap;
+    e.s.nseg = P;
+    e.s.cstart = m.cstart;
+    e.s.tile_off = m.stile_off;
+    e.s.max_tiles = e.max_stiles;
+    e.s.status = m.status;
+    cudaStream_t st = c->st;
+    auto C2 = [&](cudaError_t err) {
+      if (err != cudaSuccess && r == LCS_OK)
+        r = fail(c, LCS_ERR_CUDA, std::string("init: ") + cudaGetErrorString(err));
+    };
+    C2(cudaMemsetAsync(m.status, 0, sizeof(int), st));
+    C2(cudaMemsetAsync(m.tile_counter, 0, sizeof(unsigned), st));
+    C2(cudaMemsetAsync(m.bincnt, 0, sizeof(int) * P * NBIN, st));
+    C2(cudaMemsetAsync(m.stay_tot, 0, sizeof(int64_t) * P, st));
+    C2(cudaMemsetAsync(m.mig_tot, 0, sizeof(int64_t) * P, st));
+    C2(launch_field_convert(d.field, d.n, e.kind, e.field, st));
+    // particles -> buffer 1 compacted as one input segment, then migrate
+    Rec &B1 = e.a.buf[1];
+    for (int s = 0; s < 3 && e.np > 0; ++s) {
+      C2(cudaMemcpyAsync(B1.x[s], d.x0 + s * e.np, e.np * 8, cudaMemcpyDefault, st));
+      C2(cudaMemcpyAsync(B1.v[s], d.v0 + s * e.np, e.np * 8, cudaMemcpyDefault, st));
+      if (B1.img[s]) C2(cudaMemsetAsync(B1.img[s], 0, e.np * 4, st));
+    }
+    if (B1.tau && e.np > 0) C2(cudaMemcpyAsync(B1.tau, d.tau, e.np * 8, cudaMemcpyDefault, st));
+    std::vector<int64_t> seg(P + 1, e.np);
+    seg[0] = 0;
+    int64_t *seg_dev = nullptr;
+    C2(cudaMallocAsync((void **)&seg_dev, sizeof(int64_t) * (P + 1), st));
+    C2(cudaMemcpyAsync(seg_dev, seg.data(), sizeof(int64_t) * (P + 1), cudaMemcpyHostToDevice, st));
+    k_input_meta<<<1, 1024, 0, st>>>(e.a, seg_dev);
+    if (d.ids && e.np > 0) {
+      C2(cudaMemcpyAsync(B1.id, d.ids, e.np * 4, cudaMemcpyDefault, st));
+    } else {
+      k_iota<<<grid_for(e.np, 256, c->sms * 8), 256, 0, st>>>(B1.id, m.cstart, P);
+    }
+    C2(cudaFreeAsync(seg_dev, st));
+    C2(cudaGetLastError());
+    if (r == LCS_OK) r = enqueue_migrate(c, e);
+    int occ = step_kernel_occupancy(e.kind);
+    e.step_grid = std::max(1, std::min(e.max_tiles, std::max(1, occ) * c->sms));
+    if (r == LCS_OK) {
+      // tau >= dt and finite tau are checked on the host copy
+      if (d.tau && e.np > 0) {
+        std::vector<double> t(e.np);
+        C2(cudaMemcpy(t.data(), d.tau, e.np * 8, cudaMemcpyDefault));
+        for (int64_t i = 0; i < e.np && r == LCS_OK; ++i)
+          if (!(t[i] >= d.dt) || !std::isfinite(t[i]))
+            r = fail(c, LCS_ERR_ARG, "tau_p must be finite and >= dt");
+      }
+    }
+    if (r == LCS_OK) r = read_status(c);
+  }
+  if (r != LCS_OK) {
+    const lcs_status rr = r;
+    lcs_destroy(c);
+    return rr;
+  }
+  *out = c;
+  return LCS_OK;
+}
+
+lcs_status lcs_step(lcs_ctx *c, int64_t nsteps) {
+  lcs_status r = check_ctx(c);
+  if (r != LCS_OK) return r;
+  if (nsteps < 0) return fail(c, LCS_ERR_ARG, "nsteps < 0");
+  if (nsteps == 0) return LCS_OK;
+  if (!c->g_step) {
+    r = capture(c, false, &c->g_step);
+    if (r != LCS_OK) return r;
+  }
+  bool any_sort = false;
+  for (auto &e : c->ens) any_sort |= e.d.sort_every > 0;
+  if (any_sort && !c->g_sort) {
+    r = capture(c, true, &c->g_sort);
+    if (r != LCS_OK) return r;
+  }
+  for (int64_t k = 0; k < nsteps; ++k) {
+    // all ensembles of a context share the step count; the sort graph is
+    // used when one of them sorts after this step
+    const int64_t next = c->ens[0].steps + 1;
+    bool sort_now = false;
+    for (auto &e : c->ens) sort_now |= e.d.sort_every > 0 && next % e.d.sort_every == 0;
+    CK(cudaGraphLaunch(sort_now ? c->g_sort : c->g_step, c->st));
+    c->launches += launches_per_step(c, sort_now);
+    for (auto &e : c->ens) ++e.steps;
+  }
+  return LCS_OK;
+}
+
+lcs_status lcs_migrate(lcs_ctx *c) {
+  lcs_status r = check_ctx(c);
+  if (r != LCS_OK) return r;
+  for (auto &e : c->ens) {
+    r = enqueue_migrate(c, e);
+    if (r != LCS_OK) return r;
+  }
+  return LCS_OK;
+}
+
+lcs_status lcs_sort(lcs_ctx *c) {
+  lcs_status r = check_ctx(c);
+  if (r != LCS_OK) return r;
+  for (auto &e : c->ens) {
+    r = enqueue_sort(c, e, c->st);
+    if (r != LCS_OK) return r;
+  }
+  return LCS_OK;
+}
+
+lcs_status lcs_set_state(lcs_ctx *c, int ens, const double *x, const double *v,
+                         const double *tau, const uint32_t *ids, const int32_t *img,
+                         const int64_t *seg) {
+  lcs_status r = check_ctx(c);
+  if (r != LCS_OK) return r;
+  if (ens < 0 || ens >= (int)c->ens.size() || !x || !v || !ids || !seg)
+    return fail(c, LCS_ERR_ARG, "lcs_set_state: bad argument");
+  Ens &e = c->ens[ens];
+  const int P = e.a.geo.Ptot;
+  if (seg[0] != 0 || seg[P] != e.np) return fail(c, LCS_ERR_ARG, "lcs_set_state: bad segments");
+  for (int s = 0; s < P; ++s)
+    if (seg[s + 1] < seg[s]) return fail(c, LCS_ERR_ARG, "lcs_set_state: bad segments");
+  cudaStream_t st = c->st;
+  // Place into buffer 1 with the given segments as windows; a relayout copy
+  // moves it to the other buffer with a fresh layout.
+  Rec &B1 = e.a.buf[1];
+  for (int s = 0; s < 3 && e.np > 0; ++s) {
+    CK(cudaMemcpyAsync(B1.x[s], x + s * e.np, e.np * 8, cudaMemcpyDefault, st));
+    CK(cudaMemcpyAsync(B1.v[s], v + s * e.np, e.np * 8, cudaMemcpyDefault, st));
+    if (B1.img[s]) {
+      if (img) CK(cudaMemcpyAsync(B1.img[s], img + s * e.np, e.np * 4, cudaMemcpyDefault, st));
+      else CK(cudaMemsetAsync(B1.img[s], 0, e.np * 4, st));
+    }
+  }
+  if (B1.tau && e.np > 0) {
+    if (!tau) return fail(c, LCS_ERR_ARG, "lcs_set_state: tau required (per-particle tau_p)");
+    CK(cudaMemcpyAsync(B1.tau, tau, e.np * 8, cudaMemcpyDefault, st));
+  }
+  if (e.np > 0) CK(cudaMemcpyAsync(B1.id, ids, e.np * 4, cudaMemcpyDefault, st));
+  int64_t *seg_dev = nullptr;
+  CK(cudaMallocAsync((void **)&seg_dev, sizeof(int64_t) * (P + 1), st));
+  CK(cudaMemcpyAsync(seg_dev, seg, sizeof(int64_t) * (P + 1), cudaMemcpyHostToDevice, st));
+  k_input_meta<<<1, 1024, 0, st>>>(e.a, seg_dev);
+  k_relayout<<<1, 1024, 0, st>>>(e.a, 0);
+  const int gs = grid_for(e.np, 256, c->sms * 8);
+  k_iota<<<gs, 256, 0, st>>>(e.s.pay[0], e.a.m.cstart, P);
+  k_gather<<<gs, 256, 0, st>>>(e.a, e.s.pay[0]);
+  k_set_phase<<<1, 1024, 0, st>>>(e.a);
+  c->launches += 5;
+  CK(cudaFreeAsync(seg_dev, st));
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  return read_status(c);
+}
+
+lcs_status lcs_get_state(lcs_ctx *c, int ens, double *x, double *v, double *tau,
+                         uint32_t *ids, int32_t *img, int64_t *seg) {
+  if (!c) return LCS_ERR_ARG;
+  if (c->failed) return LCS_ERR_STATE;
+  if (ens < 0 || ens >= (int)c->ens.size()) return fail(c, LCS_ERR_ARG, "bad ensemble");
+  Ens &e = c->ens[ens];
+  cudaStream_t st = c->st;
+  const int P = e.a.geo.Ptot;
+  Rec tmp = e.a.pack;
+  k_compact<<<grid_for(e.np, 256, c->sms * 8), 256, 0, st>>>(e.a, tmp);
+  c->launches += 1;
+  CK(cudaGetLastError());
+  for (int s = 0; s < 3 && e.np > 0; ++s) {
+    if (x) CK(cudaMemcpyAsync(x + s * e.np, tmp.x[s], e.np * 8, cudaMemcpyDefault, st));
+    if (v) CK(cudaMemcpyAsync(v + s * e.np, tmp.v[s], e.np * 8, cudaMemcpyDefault, st));
+    if (img) {
+      if (tmp.img[s]) CK(cudaMemcpyAsync(img + s * e.np, tmp.img[s], e.np * 4, cudaMemcpyDefault, st));
+      else CK(cudaMemsetAsync(img + s * e.np, 0, e.np * 4, st));  // device only
+    }
+  }
+  if (tau && e.np > 0) {
+    if (tmp.tau) {
+      CK(cudaMemcpyAsync(tau, tmp.tau, e.np * 8, cudaMemcpyDefault, st));
+    } else {
+      std::vector<double> t(e.np, e.d.tau_const);
+      CK(cudaMemcpyAsync(tau, t.data(), e.np * 8, cudaMemcpyDefault, st));
+      CK(cudaStreamSynchronize(st));
+    }
+  }
+  if (ids && e.np > 0) CK(cudaMemcpyAsync(ids, tmp.id, e.np * 4, cudaMemcpyDefault, st));
+  if (seg) CK(cudaMemcpyAsync(seg, e.a.m.cstart, sizeof(int64_t) * (P + 1), cudaMemcpyDefault, st));
+  CK(cudaStreamSynchronize(st));
+  return read_status(c);
+}
+
+lcs_status lcs_get_field(lcs_ctx *c, int ens, double *out) {
+  lcs_status r = check_ctx(c);
+  if (r != LCS_OK) return r;
+  if (ens < 0 || ens >= (int)c->ens.size() || !out) return fail(c, LCS_ERR_ARG, "bad argument");
+  Ens &e = c->ens[ens];
+  const int64_t ncell = (int64_t)e.d.n * e.d.n * e.d.n;
+  double *tmp = nullptr;
+  CK(cudaMallocAsync((void **)&tmp, ncell * 3 * sizeof(double), c->st));
+  CK(launch_field_expand(e.field, e.d.n, e.kind, tmp, c->st));
+  CK(cudaMemcpyAsync(out, tmp, ncell * 3 * sizeof(double), cudaMemcpyDefault, c->st));
+  CK(cudaFreeAsync(tmp, c->st));
+  c->launches += 1;
+  CK(cudaStreamSynchronize(c->st));
+  return LCS_OK;
+}
+
+lcs_status lcs_backward(lcs_ctx *c, const double *, const double *, double *, double *,
+                        double *) {
+  lcs_status r = check_ctx(c);
+  if (r != LCS_OK) return r;
+  return fail(c, LCS_ERR_ARG, "lcs_backward: not available in this build");
+}
+
+lcs_status lcs_sync(lcs_ctx *c) {
+  lcs_status r = check_ctx(c);
+  if (r != LCS_OK) return r;
+  CK(cudaStreamSynchronize(c->st));
+  return read_status(c);
+}
+
+const char *lcs_last_error(lcs_ctx *c) {
+  if (!c) return "null context";
+  return c->err.c_str();
+}
+
+void lcs_destroy(lcs_ctx *c) {
+  if (!c) return;
+  if (c->st) cudaStreamSynchronize(c->st);
+  else cudaDeviceSynchronize();
+  if (c->g_step) cudaGraphExecDestroy(c->g_step);
+  if (c->g_sort) cudaGraphExecDestroy(c->g_sort);
+  for (void *p : c->allocs) cudaFree(p);
+  if (c->cap_st) cudaStreamDestroy(c->cap_st);
+  delete c;
+}
+
+int64_t lcs_launch_count(lcs_ctx *c) { return c ? c->launches : 0; }
+
+lcs_status lcs_partition(const uint32_t *keys, int64_t n, int nbins, uint32_t *perm,
+                         int64_t *bin_off, int32_t *status, void *stream) {
+  if (n < 0 || n >= (int64_t(1) << 31) || nbins < 1 || nbins > 65536 ||
+      (n > 0 && (!keys || !perm)) || !bin_off)
+    return LCS_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int max_tiles = (int)(n / SORT_TILE + 2);
+  const int64_t nn = std::max<int64_t>(n, 1);
+  char *mem = nullptr;
+  // layout: key[2], pay[2] (n each), hist, hist_scan (tiles * 512), blocks, cs1, to1
+  const int64_t hn = (int64_t)max_tiles * SORT_MAX_D;
+  const int64_t nblk = hn / 4096 + 2;
+  const size_t bytes = 4 * nn * 4 + 2 * hn * 4 + nblk * 4 + 2 * 8 + 2 * 4 + 64;
+  if (cudaMallocAsync((void **)&mem, bytes, st) != cudaSuccess) return LCS_ERR_OOM;
+  SortArgs s{};
+  char *p = mem;
+  auto take = [&](size_t b) { char *q = p; p += (b + 15) / 16 * 16; return q; };
+  s.key[0] = (uint32_t *)take(nn * 4);
+  s.key[1] = (uint32_t *)take(nn * 4);
+  s.pay[0] = (uint32_t *)take(nn * 4);
+  s.pay[1] = perm;
+  s.hist = (int *)take(hn * 4);
+  s.hist_scan = (int *)take(hn * 4);
+  s.scan_blocks = (int *)take(nblk * 4);
+  int64_t *cs1 = (int64_t *)take(16);
+  int *to1 = (int *)take(8);
+  s.nseg = 1, s.cstart = cs1, s.tile_off = to1, s.max_tiles = max_tiles;
+  (void)take(0);
+  const int gs = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
+  k_partition_tables<<<1, 1, 0, st>>>(n, cs1, to1, status);
+  if (n > 0) k_partition_in<<<gs, 256, 0, st>>>(keys, n, (uint32_t)nbins, s.key[0], s.pay[0], status);
+  int ob = 0;
+  cudaError_t err = radix_sort(s, ceil_log2(nbins), &ob, st, nullptr);
+  if (err == cudaSuccess) {
+    if (ob == 0 && n > 0)
+      cudaMemcpyAsync(perm, s.pay[0], n * 4, cudaMemcpyDeviceToDevice, st);
+    k_bin_bounds<<<gs, 256, 0, st>>>(s.key[ob], cs1, 0, nbins, bin_off);
+    err = cudaGetLastError();
+  }
+  cudaFreeAsync(mem, st);
+  return err == cudaSuccess ? LCS_OK : LCS_ERR_CUDA;
+}
+
+}  // extern "C"

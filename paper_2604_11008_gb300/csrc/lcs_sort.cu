@@ -1,0 +1,410 @@
+// Scan-driven stable counting sort (LSD radix over digits of at most
+// SORT_MAX_BITS bits) of (key, payload) pairs, stable within segments, and
+// the particle passes built on it: cell sort, general migration, initial
+// placement, and the stateless partition.
+//
+// Each digit pass is a counting sort: per-tile digit histograms, one
+// exclusive prefix scan over the (segment, digit, tile) histogram table --
+// which gives every (segment, digit, tile) its output offset, the same
+// prefix-scan-gives-the-slot idea as the particle pack of Sec. 2.3.3 -- and
+// a stable scatter that ranks equal digits inside a tile with warp match
+// masks, in input order.
+#include "lcs_internal.cuh"
+
+namespace lcs {
+
+// ---------------------------------------------------------------- histograms
+
+template <int MAXD>
+__global__ void __launch_bounds__(SORT_BLOCK) k_upsweep(SortArgs s, const uint32_t *key, int shift,
+                                                        int D) {
+  __shared__ int h[MAXD];
+  const int total = s.tile_off[s.nseg];
+  for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    for (int d = threadIdx.x; d < D; d += blockDim.x) h[d] = 0;
+    __syncthreads();
+    const int seg = find_segment(s.tile_off, s.nseg, tile);
+    const int t0 = s.tile_off[seg], nt = s.tile_off[seg + 1] - t0, jt = tile - t0;
+    const int64_t a = s.cstart[seg] + (int64_t)jt * SORT_TILE;
+    const int64_t e = min(s.cstart[seg + 1], a + SORT_TILE);
+    for (int64_t i = a + threadIdx.x; i < e; i += blockDim.x)
+      atomicAdd(&h[(key[i] >> shift) & (D - 1)], 1);
+    __syncthreads();
+    int *out = s.hist + (int64_t)t0 * D;
+    for (int d = threadIdx.x; d < D; d += blockDim.x) out[(int64_t)d * nt + jt] = h[d];
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- device scan
+
+constexpr int SCAN_BLOCK = 256, SCAN_ITEMS = 16, SCAN_CHUNK = SCAN_BLOCK * SCAN_ITEMS;
+
+__device__ __forceinline__ int block_excl_scan_int(int v, int *total) {
+  __shared__ int s_w[SCAN_BLOCK / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) s_w[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const int wv = lane < SCAN_BLOCK / 32 ? s_w[lane] : 0;
+    int wi = wv;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    if (lane < SCAN_BLOCK / 32) s_w[lane] = wi - wv;
+    if (lane == SCAN_BLOCK / 32 - 1) *total = wi;
+  }
+  __syncthreads();
+  const int r = inc - v + s_w[warp];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_reduce(SortArgs s, int D) {
+  __shared__ int s_tot;
+  const int64_t n = (int64_t)s.tile_off[s.nseg] * D;
+  const int64_t a = (int64_t)blockIdx.x * SCAN_CHUNK;
+  if (a >= n) return;
+  int sum = 0;
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    const int64_t i = a + (int64_t)threadIdx.x * SCAN_ITEMS + k;
+    if (i < n) sum += s.hist[i];
+  }
+  block_excl_scan_int(sum, &s_tot);
+  if (threadIdx.x == 0) s.scan_blocks[blockIdx.x] = s_tot;
+}
+
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_partials(SortArgs s, int D) {
+  __shared__ int s_tot;
+  const int64_t n = (int64_t)s.tile_off[s.nseg] * D;
+  const int nb = (int)((n + SCAN_CHUNK - 1) / SCAN_CHUNK);
+  int carry = 0;
+  for (int b0 = 0; b0 < nb; b0 += SCAN_BLOCK) {
+    const int b = b0 + threadIdx.x;
+    const int v = b < nb ? s.scan_blocks[b] : 0;
+    const int e = block_excl_scan_int(v, &s_tot);
+    if (b < nb) s.scan_blocks[b] = carry + e;
+    carry += s_tot;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_down(SortArgs s, int D) {
+  __shared__ int s_tot;
+  const int64_t n = (int64_t)s.tile_off[s.nseg] * D;
+  const int64_t a = (int64_t)blockIdx.x * SCAN_CHUNK;
+  if (a >= n) return;
+  int v[SCAN_ITEMS], sum = 0;
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    const int64_t i = a + (int64_t)threadIdx.x * SCAN_ITEMS + k;
+    v[k] = i < n ? s.hist[i] : 0;
+    sum += v[k];
+  }
+  int run = block_excl_scan_int(sum, &s_tot) + s.scan_blocks[blockIdx.x];
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    const int64_t i = a + (int64_t)threadIdx.x * SCAN_ITEMS + k;
+    if (i < n) s.hist_scan[i] = run;
+    run += v[k];
+  }
+}
+
+// ---------------------------------------------------------------- stable scatter
+
+template <int MAXD>
+__global__ void __launch_bounds__(SORT_BLOCK) k_downsweep(SortArgs s, const uint32_t *kin,
+                                                          const uint32_t *pin, uint32_t *kout,
+                                                          uint32_t *pout, int shift, int D) {
+  __shared__ int wc[SORT_BLOCK / 32][MAXD];
+  __shared__ int base[MAXD];
+  const int total = s.tile_off[s.nseg];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1;
+  constexpr int PER_WARP = SORT_TILE / (SORT_BLOCK / 32);  // 512
+  const int64_t n_all = s.cstart[s.nseg];
+  for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    const int seg = find_segment(s.tile_off, s.nseg, tile);
+    const int t0 = s.tile_off[seg], nt = s.tile_off[seg + 1] - t0, jt = tile - t0;
+    const int64_t a = s.cstart[seg] + (int64_t)jt * SORT_TILE;
+    const int64_t e = min(s.cstart[seg + 1], a + SORT_TILE);
+    for (int i = threadIdx.x; i < (SORT_BLOCK / 32) * MAXD; i += blockDim.x) (&wc[0][0])[i] = 0;
+    for (int d = threadIdx.x; d < D; d += blockDim.x)
+      base[d] = s.hist_scan[(int64_t)t0 * D + (int64_t)d * nt + jt];
+    __syncthreads();
+    uint32_t k[SORT_ITEMS], p[SORT_ITEMS];
+    int rk[SORT_ITEMS];
+#pragma unroll
+    for (int r = 0; r < SORT_ITEMS; ++r) {
+      const int64_t i = a + warp * PER_WARP + r * 32 + lane;
+      const bool valid = i < e;
+      k[r] = valid ? kin[i] : 0u;
+      p[r] = valid ? pin[i] : 0u;
+      const int dg = valid ? (int)((k[r] >> shift) & (D - 1)) : MAXD;
+      const unsigned peers = __match_any_sync(0xffffffffu, dg);
+      const int rank = __popc(peers & lt);
+      const int b = valid ? wc[warp][dg] : 0;
+      __syncwarp();
+      if (valid && rank == 0) wc[warp][dg] = b + __popc(peers);
+      __syncwarp();
+      rk[r] = valid ? b + rank : -1;
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < D; d += blockDim.x) {
+      int run = base[d];
+      for (int w = 0; w < SORT_BLOCK / 32; ++w) {
+        const int t = wc[w][d];
+        wc[w][d] = run;
+        run += t;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < SORT_ITEMS; ++r) {
+      if (rk[r] < 0) continue;
+      const int dg = (int)((k[r] >> shift) & (D - 1));
+      const int64_t pos = (int64_t)wc[warp][dg] + rk[r];
+      if (pos < 0 || pos >= n_all) {  // inconsistent histogram: report, never write
+        if (s.status) latch(s.status, LCS_ERR_STATE);
+        continue;
+      }
+      kout[pos] = k[r];
+      pout[pos] = p[r];
+    }
+    __syncthreads();
+  }
+}
+
+int64_t radix_scratch_ints(int max_tiles, int bits) {
+  (void)bits;
+  return (int64_t)max_tiles * SORT_MAX_D;
+}
+
+cudaError_t radix_sort(const SortArgs &s, int bits, int *out_buf, cudaStream_t st,
+                       int64_t *launches) {
+  int ib = 0;
+  if (bits > 0) {
+    const int passes = (bits + SORT_MAX_BITS - 1) / SORT_MAX_BITS;
+    const int b = (bits + passes - 1) / passes;
+    const int grid = max(1, min(s.max_tiles, 152 * 8));
+    const int64_t maxn = (int64_t)s.max_tiles * SORT_MAX_D;
+    const int sgrid = (int)((maxn + SCAN_CHUNK - 1) / SCAN_CHUNK);
+    for (int p = 0, shift = 0; p < passes; ++p, shift += b) {
+      const int bp = min(b, bits - shift);
+      const int D = 1 << bp;
+      if (D <= 64) k_upsweep<64><<<grid, SORT_BLOCK, 0, st>>>(s, s.key[ib], shift, D);
+      else k_upsweep<SORT_MAX_D><<<grid, SORT_BLOCK, 0, st>>>(s, s.key[ib], shift, D);
+      k_scan_reduce<<<sgrid, SCAN_BLOCK, 0, st>>>(s, D);
+      k_scan_partials<<<1, SCAN_BLOCK, 0, st>>>(s, D);
+      k_scan_down<<<sgrid, SCAN_BLOCK, 0, st>>>(s, D);
+      if (D <= 64) k_downsweep<64><<<grid, SORT_BLOCK, 0, st>>>(s, s.key[ib], s.pay[ib], s.key[ib ^ 1],
+                                                       s.pay[ib ^ 1], shift, D);
+      else k_downsweep<SORT_MAX_D><<<grid, SORT_BLOCK, 0, st>>>(s, s.key[ib], s.pay[ib],
+                                                               s.key[ib ^ 1], s.pay[ib ^ 1],
+                                                               shift, D);
+      if (launches) *launches += 5;
+      ib ^= 1;
+      cudaError_t err = cudaGetLastError();
+      if (err != cudaSuccess) return err;
+    }
+  }
+  *out_buf = ib;
+  return cudaSuccess;
+}
+
+}  // namespace lcs
+
+// ---------------------------------------------------------------- particle passes
+
+namespace lcs {
+
+__device__ __forceinline__ int find_segment64(const int64_t *off, int P, int64_t t) {
+  int lo = 0, hi = P;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= t) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int cell_of(const Geom &g, double x) {
+  const int c = (int)floor(__dmul_rn(x, g.inv_dx));
+  return min(max(c, 0), g.N - 1);
+}
+
+// Brick-major cell key within the particle's subdomain (B^3 bricks,
+// x fastest at both levels) -- the order of the cell sort.
+__global__ void k_keys_cell(StepArgs a, uint32_t *key, uint32_t *pay, int B, int nbx, int nby) {
+  const int ph = *a.m.phase;
+  const Rec A = a.buf[ph];
+  const int64_t *base = a.m.lay_base[ph];
+  const int P = a.geo.Ptot;
+  const int64_t n = a.m.cstart[P];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int seg = find_segment64(a.m.cstart, P, i);
+    const int64_t slot = base[seg] + (i - a.m.cstart[seg]);
+    const int ps[3] = {seg % a.geo.P[0], (seg / a.geo.P[0]) % a.geo.P[1],
+                       seg / (a.geo.P[0] * a.geo.P[1])};
+    int l[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      const int c = cell_of(a.geo, A.x[s][slot]);
+      l[s] = min(max(c - ps[s] * a.geo.W[s], 0), a.geo.W[s] - 1);
+    }
+    const uint32_t brick = (uint32_t)((l[2] / B * nby + l[1] / B) * nbx + l[0] / B);
+    const uint32_t in = (uint32_t)(((l[2] % B) * B + l[1] % B) * B + l[0] % B);
+    key[i] = brick * (uint32_t)(B * B * B) + in;
+    pay[i] = (uint32_t)slot;
+  }
+}
+
+// Destination key 2*dest + (dest != source segment): a stable sort by it is
+// the migration order (stayers first, then arrivals by source, Sec. 3.2.2).
+__global__ void k_keys_dest(StepArgs a, uint32_t *key, uint32_t *pay) {
+  const int ph = *a.m.phase;
+  const Rec A = a.buf[ph];
+  const int64_t *base = a.m.lay_base[ph];
+  const int P = a.geo.Ptot;
+  const int64_t n = a.m.cstart[P];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int seg = find_segment64(a.m.cstart, P, i);
+    const int64_t slot = base[seg] + (i - a.m.cstart[seg]);
+    int p[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      const double x = A.x[s][slot];
+      if (!(x >= 0.0 && x < a.geo.L)) latch(a.m.status, LCS_ERR_ARG);
+      p[s] = cell_of(a.geo, x) / a.geo.W[s];
+    }
+    const uint32_t d = (uint32_t)(p[0] + a.geo.P[0] * (p[1] + a.geo.P[1] * p[2]));
+    key[i] = 2u * d + (d != (uint32_t)seg ? 1u : 0u);
+    pay[i] = (uint32_t)slot;
+  }
+}
+
+// Single-segment tables {0, n} and {0, tiles(n)} for whole-array sorts.
+__global__ void k_one_segment(const int64_t *cstart, int P, int64_t *cs1, int *to1) {
+  const int64_t n = cstart[P];
+  cs1[0] = 0, cs1[1] = n;
+  to1[0] = 0, to1[1] = (int)((n + SORT_TILE - 1) / SORT_TILE);
+}
+
+// Bin starts of sorted keys: start[b] = first rank whose (key >> shift) >= b.
+__global__ void k_bin_bounds(const uint32_t *key, const int64_t *cs1, int shift, int nbins,
+                             int64_t *start) {
+  const int64_t n = cs1[1];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int cur = i < n ? (int)umin(key[i] >> shift, (unsigned)nbins - 1u) : nbins;
+    const int prev = i > 0 ? (int)umin(key[i - 1] >> shift, (unsigned)nbins - 1u) : -1;
+    for (int b = prev + 1; b <= cur; ++b) start[b] = i;
+  }
+}
+
+// New counts from compacted starts, then a fresh layout for the output buffer.
+__global__ void __launch_bounds__(1024) k_relayout(StepArgs a, int from_starts) {
+  const int P = a.geo.Ptot;
+  const int ph = *a.m.phase;
+  if (from_starts)
+    for (int d = threadIdx.x; d < P; d += blockDim.x) a.m.cnt[d] = a.m.cstart[d + 1] - a.m.cstart[d];
+  __syncthreads();
+  layout_from_counts(P, a.m.cnt, a.m.cstart, a.m.tile_off, a.m.stile_off, a.m.lay_base[ph ^ 1],
+                     a.m.lay_cap[ph ^ 1]);
+}
+
+// Output rank r (compacted, segment found from cstart) <- input slot pay[r].
+__global__ void k_gather(StepArgs a, const uint32_t *pay) {
+  const int ph = *a.m.phase;
+  const Rec A = a.buf[ph], B = a.buf[ph ^ 1];
+  const int64_t *baseB = a.m.lay_base[ph ^ 1];
+  const int P = a.geo.Ptot;
+  const int64_t n = a.m.cstart[P];
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int d = find_segment64(a.m.cstart, P, r);
+    const uint32_t src = pay[r];
+    if (src >= a.cap) {  // corrupt permutation: report, never read out of bounds
+      latch(a.m.status, LCS_ERR_STATE);
+      continue;
+    }
+    copy_rec(A, src, B, baseB[d] + (r - a.m.cstart[d]));
+  }
+}
+
+// Both buffers take the output layout; the output becomes the input.
+__global__ void k_set_phase(StepArgs a) {
+  const int ph = *a.m.phase;
+  for (int d = threadIdx.x; d < a.geo.Ptot; d += blockDim.x) {
+    a.m.lay_base[ph][d] = a.m.lay_base[ph ^ 1][d];
+    a.m.lay_cap[ph][d] = a.m.lay_cap[ph ^ 1][d];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *a.m.phase = ph ^ 1;
+    *a.m.tile_counter = 0u;
+  }
+}
+
+// Input = buffer 1, one compacted segment per given count (seg bounds).
+__global__ void k_input_meta(StepArgs a, const int64_t *seg_dev) {
+  const int P = a.geo.Ptot;
+  for (int d = threadIdx.x; d < P; d += blockDim.x) {
+    a.m.lay_base[1][d] = seg_dev[d];
+    a.m.lay_cap[1][d] = seg_dev[d + 1] - seg_dev[d];
+    a.m.cnt[d] = seg_dev[d + 1] - seg_dev[d];
+  }
+  for (int d = threadIdx.x; d <= P; d += blockDim.x) a.m.cstart[d] = seg_dev[d];
+  if (threadIdx.x == 0) *a.m.phase = 1;
+}
+
+__global__ void k_iota(uint32_t *p, const int64_t *cstart, int P) {
+  const int64_t n = cstart[P];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = (uint32_t)i;
+}
+
+// Copy the input buffer's live particles to a compacted record set.
+__global__ void k_compact(StepArgs a, Rec out) {
+  const int ph = *a.m.phase;
+  const Rec A = a.buf[ph];
+  const int64_t *base = a.m.lay_base[ph];
+  const int P = a.geo.Ptot;
+  const int64_t n = a.m.cstart[P];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int seg = find_segment64(a.m.cstart, P, i);
+    copy_rec(A, base[seg] + (i - a.m.cstart[seg]), out, i);
+  }
+}
+
+// Stateless partition helpers.
+__global__ void k_partition_in(const uint32_t *keys, int64_t n, uint32_t nbins, uint32_t *k,
+                               uint32_t *p, int32_t *status) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t v = keys[i];
+    if (v >= nbins) {
+      v = nbins - 1;
+      if (status) atomicCAS(status, 0, LCS_ERR_ARG);
+    }
+    k[i] = v;
+    p[i] = (uint32_t)i;
+  }
+}
+
+__global__ void k_partition_tables(int64_t n, int64_t *cs1, int *to1, int32_t *status) {
+  cs1[0] = 0, cs1[1] = n;
+  to1[0] = 0, to1[1] = (int)((n + SORT_TILE - 1) / SORT_TILE);
+  if (status) *status = LCS_OK;
+}
+
+}  // namespace lcs

@@ -1,0 +1,275 @@
+"""Parity of the CUDA path with the CPU oracle (needs a GPU).
+
+Every comparison uses the same seeded inputs on both sides.  Integer work
+(migration order, sort order, segment bounds) must match bit for bit;
+FP64 trajectories within a relative 1e-12 (norm-wise, unwrapped positions
+relative to the displacement, velocities relative to their norm)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import L, assert_same_storage, by_id, gpu_state, traj_errors
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def lcs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2604_11008_gb300 as m
+    from paper_2604_11008_gb300 import build
+    build.build()
+    return m
+
+
+# ---------------------------------------------------------------- partition (Sec. 2.3.3)
+
+def test_partition_worked_example(lcs, worked_example):
+    """mask 0,1,0,1,0: the mask-1 particles 2 and 4 land at 1-based buffer slots 1, 2."""
+    mask = np.array([r[1] for r in worked_example], np.int32)
+    scan = [r[2] for r in worked_example]
+    perm, off, status = lcs.partition(mask, 2)
+    perm, off = perm.cpu().numpy(), off.cpu().numpy()
+    assert int(status.item()) == 0
+    assert list(off) == [0, 3, 5]
+    bin1 = perm[off[1]:off[2]]
+    for slot, p in enumerate(bin1):
+        assert scan[p] == slot + 1
+    assert list(perm) == [0, 2, 4, 1, 3]
+
+
+@pytest.mark.parametrize("n,nbins", [(0, 3), (1, 1), (5, 2), (4095, 7), (4097, 64), (70001, 3),
+                                     (100000, 513), (250000, 65536)])
+def test_partition_is_a_stable_counting_sort(lcs, n, nbins):
+    g = np.random.default_rng(n + nbins)
+    keys = g.integers(0, nbins, n).astype(np.int32)
+    perm, off, status = lcs.partition(keys, nbins)
+    ref = np.argsort(keys, kind="stable")
+    assert np.array_equal(perm.cpu().numpy(), ref)
+    assert np.array_equal(off.cpu().numpy(),
+                          np.concatenate([[0], np.cumsum(np.bincount(keys, minlength=nbins))]))
+    assert int(status.item()) == 0
+
+
+def test_partition_flags_out_of_range_keys(lcs):
+    keys = np.array([0, 5, 1, 9], np.int32)
+    perm, off, status = lcs.partition(keys, 3)
+    assert int(status.item()) == lcs.LCS_ERR_ARG
+    assert list(perm.cpu().numpy()) == [0, 2, 1, 3]
+
+
+# ---------------------------------------------------------------- placement and migration
+
+def make(lcs, field, x, v, dt, tau=None, tau_const=0.1, **kw):
+    return lcs.Simulator(field, x, v, dt, tau=tau, tau_const=tau_const, kernel="fp64", **kw)
+
+
+@pytest.mark.parametrize("P", [(1, 1, 1), (2, 2, 2), (3, 3, 3), (4, 2, 1)])
+def test_initial_placement_matches_oracle(lcs, P):
+    N = 12 if 3 in P else 16
+    field, _, x, v, _ = synth.small_case(30, N, 8, 2.0, 9000, None)
+    sim = make(lcs, field, x, v, 0.01, sub=P)
+    st = gpu_state(sim)
+    ref = oracle.initial_state(N, L, P, x, v, None)
+    assert np.array_equal(st["seg"], ref.seg)
+    assert np.array_equal(st["ids"].astype(np.uint32), ref.ids)
+    assert np.array_equal(st["x"], ref.x) and np.array_equal(st["v"], ref.v)
+
+
+def test_empty_and_single_particle(lcs):
+    field, _, x, v, _ = synth.small_case(31, 8, 4, 2.0, 1, None)
+    for n in (0, 1):
+        sim = make(lcs, field, x[:, :n], v[:, :n], 0.01, sub=(2, 2, 2))
+        sim.step(3)
+        sim.sort()
+        st = gpu_state(sim)
+        assert st["seg"][-1] == n
+        sim.close()
+
+
+def test_migrate_pass_on_arbitrary_segments_bit_exact(lcs):
+    """lcs_migrate on a state whose segments do not match positions equals the
+    sequential-counter migration of the oracle on the same input."""
+    N, P = 12, (3, 2, 2)
+    field, _, x, v, _ = synth.small_case(32, N, 8, 2.0, 20000, None)
+    sim = make(lcs, field, x, v, 0.01, sub=P)
+    g = np.random.default_rng(33)
+    cut = np.sort(g.integers(0, 20000, 11))
+    seg = np.concatenate([[0], cut, [20000]]).astype(np.int64)
+    ids = g.permutation(20000).astype(np.int32)
+    sim.set_state(x[:, ids], v[:, ids], ids, seg)
+    sim.migrate()
+    st = gpu_state(sim)
+    dest, _ = oracle.keys(N, L, P, 1, x[:, ids])
+    perm, seg_out, _ = oracle.migrate(12, seg, dest)
+    assert np.array_equal(st["seg"], seg_out)
+    assert np.array_equal(st["ids"], ids[perm])
+    assert np.array_equal(st["x"], x[:, ids][:, perm])
+
+
+def one_step_identical_inputs(lcs, N, P, n, tau_median, g, seed, dt=0.01, steps_before=3):
+    field, _, x, v, tau = synth.small_case(seed, N, 24, N / 4.0, n, tau_median, dt=dt)
+    sim = make(lcs, field, x, v, dt, tau=tau, sub=P, g=g, track_images=True)
+    sim.step(steps_before)
+    s0 = gpu_state(sim)
+    sim.step(1)
+    s1 = gpu_state(sim)
+    # oracle advance from the GPU's own state, then compare values by id
+    xo, vo = s0["x"].copy(), s0["v"].copy()
+    img = s0["img"].copy()
+    tau_s = s0["tau"] if tau is not None else None
+    oracle.advance(field, L, xo, vo, tau_s, 0.1, dt, g, 1, img=img)
+    xg, vg, ig = by_id(s1["ids"], s1["x"], s1["v"], s1["img"])
+    xr, vr, ir = by_id(s0["ids"], xo, vo, img)
+    dx = np.abs((xg + L * ig) - (xr + L * ir)).max()
+    dv = np.abs(vg - vr).max() / np.abs(vr).max()
+    assert dx < 1e-13 and dv < 1e-13, (dx, dv)
+    # bit-exact migration: the oracle's sequential-counter migration applied to
+    # the GPU's post-step positions in the pre-step storage order
+    pos_of = np.empty(n, np.int64)
+    pos_of[s1["ids"]] = np.arange(n)
+    x_pre = s1["x"][:, pos_of[s0["ids"]]]
+    dest, _ = oracle.keys(N, L, P, 1, x_pre)
+    perm, seg_out, _ = oracle.migrate(int(np.prod(P)), s0["seg"], dest)
+    assert np.array_equal(s1["seg"], seg_out)
+    assert np.array_equal(s1["ids"], s0["ids"][perm])
+    moved = int((dest != np.repeat(np.arange(int(np.prod(P))), np.diff(s0["seg"]))).sum())
+    return moved
+
+
+@pytest.mark.parametrize("N,P,n", [(16, (2, 2, 2), 5000), (24, (3, 3, 3), 30011),
+                                   (32, (4, 2, 1), 70000), (16, (1, 1, 1), 1500),
+                                   (20, (5, 1, 2), 12345)])
+def test_one_step_identical_inputs(lcs, N, P, n):
+    moved = one_step_identical_inputs(lcs, N, P, n, 0.05, (0.0, 0.0, -9.8), seed=40 + n, dt=0.02)
+    if int(np.prod(P)) > 1:
+        assert moved > 0  # the case exercises migration
+
+
+# ---------------------------------------------------------------- trajectories
+
+def run_pair(lcs, N, M, kmax, n, P, dt, steps, tau_median=None, tau_const=0.1, g=(0, 0, 0),
+             sort_every=0, brick=8, seed=50):
+    field, _, x, v, tau = synth.small_case(seed, N, M, kmax, n, tau_median, tau_const, dt=dt)
+    sim = make(lcs, field, x, v, dt, tau=tau, tau_const=tau_const, sub=P, g=g,
+               sort_every=sort_every, sort_brick=brick, track_images=True)
+    sim.step(steps)
+    st = gpu_state(sim)
+    ref = oracle.initial_state(N, L, P, x, v, tau, track_img=True)
+    oracle.run(ref, field, L, P, tau_const, dt, g, steps, sort_every=sort_every, brick=brick)
+    return st, ref, x
+
+
+def test_plain_32_full_trajectory():
+    """The plain FP64 workload: 32^3, 64 modes k 1-4, 32768 particles, tau 0.1,
+    dt 0.01, 100 steps, 2x2x2 subdomains with migration every step."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2604_11008_gb300 as lcs
+    w = synth.WORKLOADS["plain_32"]
+    field, modes = synth.make_field(w)
+    x, v, _ = synth.make_particles(w, w.dt)
+    sim = lcs.Simulator(field, x, v, w.dt, tau_const=w.tau_const, sub=w.sub, kernel="fp64",
+                        track_images=True)
+    sim.step(w.steps)
+    st = gpu_state(sim)
+    ref = oracle.initial_state(w.N, L, w.sub, x, v, None, track_img=True)
+    oracle.run(ref, field, L, w.sub, w.tau_const, w.dt, w.g, w.steps)
+    ex, ev, _, _ = traj_errors(st["x"], st["img"], st["v"], st["ids"], ref, x)
+    assert ex < TOL_FP64 and ev < TOL_FP64, (ex, ev)
+    assert_same_storage(st, ref, w.N, w.sub)
+    assert np.array_equal(np.sort(st["ids"]), np.arange(w.np_))
+
+
+@pytest.mark.parametrize("P,sort_every,brick", [((2, 2, 2), 5, 4), ((3, 3, 3), 4, 8),
+                                                ((1, 1, 1), 3, 1)])
+def test_trajectory_with_gravity_and_sort(lcs, P, sort_every, brick):
+    N = 24
+    st, ref, x0 = run_pair(lcs, N, 32, 6.0, 20000, P, 0.005, 30, tau_median=0.05,
+                           g=(0.0, 0.0, -9.8), sort_every=sort_every, brick=brick, seed=60)
+    ex, ev, _, _ = traj_errors(st["x"], st["img"], st["v"], st["ids"], ref, x0)
+    assert ex < TOL_FP64 and ev < TOL_FP64, (ex, ev)
+    assert_same_storage(st, ref, N, P, brick)
+
+
+def test_sort_pass_bit_exact_on_identical_inputs(lcs):
+    N, P, B = 24, (2, 3, 2), 4
+    field, _, x, v, _ = synth.small_case(70, N, 16, 4.0, 40000, None)
+    sim = make(lcs, field, x, v, 0.01, sub=P)
+    sim.step(4)
+    s0 = gpu_state(sim)
+    sim2 = None
+    sim.sort()  # default brick 8
+    s1 = gpu_state(sim)
+    _, key = oracle.keys(N, L, P, 8, s0["x"])
+    perm = oracle.sort(12, s0["seg"], key)
+    assert np.array_equal(s1["seg"], s0["seg"])
+    assert np.array_equal(s1["ids"], s0["ids"][perm])
+    assert np.array_equal(s1["x"], s0["x"][:, perm])
+    # keys are sorted within segments
+    _, key1 = oracle.keys(N, L, P, 8, s1["x"])
+    for s in range(12):
+        k = key1[s1["seg"][s]:s1["seg"][s + 1]]
+        assert np.all(np.diff(k) >= 0)
+
+
+def test_many_tiles_ragged_tail(lcs):
+    """Several thousand scan tiles per step with a ragged last tile per segment."""
+    N, P = 32, (2, 2, 2)
+    moved = one_step_identical_inputs(lcs, N, P, 1_000_003, 0.05, (0.0, 0.0, -9.8), seed=80,
+                                      dt=0.02, steps_before=1)
+    assert moved > 1000
+
+
+# ---------------------------------------------------------------- errors are latched, not faults
+
+def test_nonfinite_state_is_reported(lcs):
+    field, _, x, v, _ = synth.small_case(90, 8, 4, 2.0, 100, None)
+    sim = make(lcs, field, x, v, 0.01, sub=(2, 1, 1))
+    st = gpu_state(sim)
+    vv = st["v"].copy()
+    vv[0, 7] = np.nan
+    sim.set_state(st["x"], vv, st["ids"], st["seg"])
+    sim.step(1)
+    with pytest.raises(lcs.LcsError) as e:
+        sim.sync()
+    assert e.value.status == lcs.LCS_ERR_NONFINITE
+    with pytest.raises(lcs.LcsError) as e:
+        sim.step(1)
+    assert e.value.status == lcs.LCS_ERR_STATE
+
+
+def test_displacement_beyond_neighbour_is_reported(lcs):
+    field, _, x, v, _ = synth.small_case(91, 12, 4, 2.0, 100, None)
+    sim = make(lcs, field, x, v, 0.01, sub=(4, 1, 1))
+    st = gpu_state(sim)
+    vv = st["v"].copy()
+    vv[0, :] = 250.0   # 2.5 per step: more than one subdomain width (pi/2)
+    sim.set_state(st["x"], vv, st["ids"], st["seg"])
+    sim.step(1)
+    with pytest.raises(lcs.LcsError) as e:
+        sim.sync()
+    assert e.value.status == lcs.LCS_ERR_DISPLACEMENT
+
+
+def test_invalid_arguments(lcs):
+    field, _, x, v, _ = synth.small_case(92, 12, 4, 2.0, 100, None)
+    with pytest.raises(lcs.LcsError) as e:
+        make(lcs, field, x, v, 0.01, sub=(5, 1, 1))      # 12 % 5 != 0
+    assert e.value.status == lcs.LCS_ERR_ARG
+    with pytest.raises(lcs.LcsError) as e:
+        make(lcs, field, x, v, 0.5, tau_const=0.1)       # dt > tau
+    assert e.value.status == lcs.LCS_ERR_ARG
+    xb = x.copy()
+    xb[1, 3] = L                                         # outside [0, L)
+    with pytest.raises(lcs.LcsError) as e:
+        make(lcs, field, xb, v, 0.01)
+    assert e.value.status == lcs.LCS_ERR_ARG
