@@ -1,0 +1,306 @@
+"""Benchmark of the particle hot path: particle-updates/s including migration.
+
+Workload (default ``scale_256``): 256^3 FP64 field of 512 random Fourier
+modes (k 1-32, k^-5/3 spectrum), 16,777,216 particles uniform in the box,
+tau_p log-normal (median 0.05, sigma 0.5), gravity (0, 0, -9.8), 4x4x4
+virtual subdomains with migration every step and a cell sort every 10
+steps, dt from the convective CFL rule.  One bench step = 10 time steps
+(one sort period), so every timed step contains all passes of the path.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun, one process per GPU): every rank runs its own replica
+of the workload (the virtual subdomains of one replica live in one GPU's
+memory; no collective is on the data path); ``value`` sums all ranks' updates
+over the slowest rank's time.  ``--impl reference`` times the CPU oracle on
+this machine's host cores on a bounded sample of the same workload.
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "particle-updates/s incl. prefix-scan migration; % HBM peak; adjoint/fwd ratio"
+UNIT = "particle-updates/s"
+STEPS_PER_BENCH_STEP = 10
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured", d
+    return 6800.0, "fallback", {}
+
+
+# ---------------------------------------------------------------- workload
+
+def build_workload(name: str, device: str, n_override: int | None = None):
+    w = synth.WORKLOADS[name]
+    field, modes = synth.make_field(w, device=device)
+    dt = w.dt if w.dt is not None else synth.cfl_dt(synth.max_speed(field), w.N)
+    n = n_override or w.np_
+    x, v, tau = synth.make_particles(w, dt, n=n)
+    return w, field, modes, dt, x, v, tau
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- CPU oracle leg
+
+def oracle_rate(w, field_np, dt, x, v, tau, n_sample: int, steps: int):
+    """Particle-updates/s of the CPU oracle (single thread) on a sample."""
+    import oracle
+    L = synth.L_BOX
+    xs, vs = x[:, :n_sample].copy(), v[:, :n_sample].copy()
+    ts = None if tau is None else tau[:n_sample].copy()
+    st = oracle.initial_state(w.N, L, w.sub, xs, vs, ts)
+    t0 = time.perf_counter()
+    oracle.run(st, field_np, L, w.sub, w.tau_const, dt, w.g, steps,
+               sort_every=w.sort_every, brick=8)
+    t = time.perf_counter() - t0
+    return n_sample * steps / t, t
+
+
+# ---------------------------------------------------------------- main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="scale_256")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "fp64", "df"])
+    ap.add_argument("--field", default="f64", choices=["f64", "f32", "bf16"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=1 << 20)
+    ap.add_argument("--np", type=int, default=0,
+                    help="particle count override (small profiling cases only)")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+    import paper_2604_11008_gb300 as lcs
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    w, field, modes, dt, x, v, tau = build_workload(args.workload, "cuda", args.np or None)
+    sim = lcs.Simulator(field, x, v, dt, tau=tau, tau_const=w.tau_const, g=w.g, sub=w.sub,
+                        field_dtype=args.field, kernel=args.kernel, sort_every=w.sort_every)
+    n = x.shape[1]
+    K, W = args.steps, args.warmup
+    # the L2 (129 MB) is far smaller than the particle state (~1 GB) and the
+    # field (537 MB): every timed step streams its inputs from HBM
+    for _ in range(W):
+        sim.step(STEPS_PER_BENCH_STEP)
+    sim.sync()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    l0 = sim.launches
+    ev0.record(stream)
+    for _ in range(K):
+        sim.step(STEPS_PER_BENCH_STEP)
+    ev1.record(stream)
+    ev1.synchronize()
+    sim.sync()
+    torch.cuda.synchronize()
+    launches = sim.launches - l0
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        dist.barrier()
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    updates = n * STEPS_PER_BENCH_STEP * K * world
+    value = updates / (ms * 1e-3)
+
+    # per-kernel device time (un-graphed replay of one sort period, events
+    # around every kernel class on the launching stream)
+    prof = sim.profile_steps(STEPS_PER_BENCH_STEP)
+    step_ms, step_n = prof["step"]
+    hbm_peak, peak_kind, peaks = load_peaks()
+    N = w.N
+    rec_bytes = 48 + (8 if tau is not None else 0) + 4
+    field_bytes_cell = {"f64": 24, "f32": 12, "bf16": 6}[args.field]
+    # algorithmic bytes of one step-kernel launch: every record read and
+    # written once, every field value read once
+    alg_bytes = n * 2 * rec_bytes + field_bytes_cell * N ** 3
+    achieved = alg_bytes / (step_ms / step_n * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4), "traffic": None,
+                "kernel": "k_step", "peak_source": peak_kind,
+                "kernel_ms_per_launch": round(step_ms / step_n, 4),
+                "kernel_share": round(step_ms / sum(p[0] for p in prof.values()), 3)}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        st_host = sim.get_state(device="cpu")
+        h2d = n * (24 + 24 + (8 if tau is not None else 0) + 4) + 8 * (len(st_host["seg"]))
+        d2h = h2d
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            sim.set_state(st_host["x"], st_host["v"], st_host["ids"], st_host["seg"],
+                          tau=st_host["tau"] if tau is not None else None)
+            sim.step(STEPS_PER_BENCH_STEP)
+            st_host = sim.get_state(device="cpu", out={k: st_host[k] for k in
+                                                       ("x", "v", "tau", "ids")})
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = e0.elapsed_time(e1)
+        e2e = {"value": n * STEPS_PER_BENCH_STEP * args.e2e_steps * world / (e_ms * 1e-3),
+               "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "wall_s": round(time.perf_counter() - t0, 3)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        field_np = field.cpu().numpy() if args.field == "f64" else None
+        if field_np is not None:
+            steps_cpu = STEPS_PER_BENCH_STEP
+            xs, vs = x, v
+            rate, secs = oracle_rate(w, field_np, dt, xs, vs, tau, args.cpu_sample, steps_cpu)
+            cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"first {args.cpu_sample} particles of the workload, "
+                             f"{steps_cpu} steps incl. migration and one sort, {secs:.1f} s"}
+
+    sim.close()
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+               "warmup": W, "ms_per_step": ms / K, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.field == "f64"
+               else args.field, "data": "synthetic",
+               "config": {"workload": w.name, "grid": f"{N}^3", "modes": w.M,
+                          "particles_per_gpu": n, "subdomains": "x".join(map(str, w.sub)),
+                          "sort_every": w.sort_every, "dt": dt,
+                          "time_steps_per_bench_step": STEPS_PER_BENCH_STEP,
+                          "field_storage": args.field, "kernel": args.kernel,
+                          "l2": "inputs larger than L2 (state ~1 GB, field 0.54 GB)",
+                          "parallelism": f"replicas{world}"},
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": int(launches), "clocks": clk,
+               "kernel_profile_ms": {k: round(v_[0], 4) for k, v_ in prof.items()}}
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_reference(args, world, rank):
+    """The CPU oracle timed on this machine's host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    w, field, modes, dt, x, v, tau = build_workload(args.workload, "cpu",
+                                                      n_override=args.cpu_sample)
+    n = args.cpu_sample
+    import oracle
+    L = synth.L_BOX
+    st = oracle.initial_state(w.N, L, w.sub, x, v, tau)
+    for _ in range(args.warmup):
+        oracle.run(st, field, L, w.sub, w.tau_const, dt, w.g, 1, sort_every=0)
+    t0 = time.perf_counter()
+    done = 0
+    for k in range(args.steps):
+        oracle.run(st, field, L, w.sub, w.tau_const, dt, w.g, STEPS_PER_BENCH_STEP,
+                   sort_every=w.sort_every, brick=8)
+        done += STEPS_PER_BENCH_STEP
+    t = time.perf_counter() - t0
+    value = n * done / t
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": w.name, "grid": f"{w.N}^3", "particles": n,
+                      "subdomains": "x".join(map(str, w.sub)), "sort_every": w.sort_every,
+                      "dt": dt, "time_steps_per_bench_step": STEPS_PER_BENCH_STEP},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"first {n} particles of the workload (bounded sample), "
+                                      f"{done} time steps"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -160,6 +160,23 @@ lcs_status lcs_get_field(lcs_ctx *ctx, int ens, double *out);
 lcs_status lcs_backward(lcs_ctx *ctx, const double *gx, const double *gv, double *gU,
                         double *gx0, double *gv0);
 
+/* Kernel classes reported by lcs_profile_steps. */
+enum {
+  LCS_PROF_STEP = 0,    /* fused interpolate + integrate + scan + pack kernel */
+  LCS_PROF_FINISH = 1,  /* arrival offsets and next layout (one block) */
+  LCS_PROF_UNPACK = 2,  /* placement of the arrivals */
+  LCS_PROF_FLIP = 3,    /* buffer swap (one block) and scan-status reset */
+  LCS_PROF_SORT = 4,    /* the whole cell-sort pass */
+  LCS_PROF_N = 5
+};
+
+/* Tracing: enqueue nsteps steps like lcs_step but without the graph, with
+ * a CUDA event pair around every kernel (class) on the context's stream.
+ * Synchronising.  ms[k] (host, LCS_PROF_N doubles) receives the summed
+ * device time of class k in milliseconds, count[k] (host, may be NULL) the
+ * number of launches.  The particle state advances exactly as lcs_step. */
+lcs_status lcs_profile_steps(lcs_ctx *ctx, int64_t nsteps, double *ms, int64_t *count);
+
 /* Wait for all enqueued work; return the latched device status. */
 lcs_status lcs_sync(lcs_ctx *ctx);
 

@@ -33,7 +33,8 @@ KERNELS = {"auto": 0, "fp64": 1, "df": 2}
 # Every symbol declared in include/lcs.h.
 EXPORTS = ("lcs_init", "lcs_step", "lcs_migrate", "lcs_sort", "lcs_set_state", "lcs_get_state",
            "lcs_get_field", "lcs_backward", "lcs_sync", "lcs_last_error", "lcs_destroy",
-           "lcs_launch_count", "lcs_partition")
+           "lcs_launch_count", "lcs_partition", "lcs_profile_steps")
+PROF_CLASSES = ("step", "finish", "unpack", "flip", "sort")
 
 
 class LcsError(RuntimeError):
@@ -79,9 +80,10 @@ def lib():
         L.lcs_launch_count.argtypes = [P]
         L.lcs_launch_count.restype = i64
         L.lcs_partition.argtypes = [P, i64, i32, P, P, P, P]
+        L.lcs_profile_steps.argtypes = [P, i64, P, P]
         for name in ("lcs_init", "lcs_step", "lcs_migrate", "lcs_sort", "lcs_set_state",
                      "lcs_get_state", "lcs_get_field", "lcs_backward", "lcs_sync",
-                     "lcs_partition"):
+                     "lcs_partition", "lcs_profile_steps"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -195,6 +197,15 @@ class Simulator:
 
     def sync(self):
         self._check(lib().lcs_sync(self._ctx))
+
+    def profile_steps(self, nsteps: int):
+        """Run nsteps un-graphed steps timing every kernel class with CUDA events.
+
+        Returns {class: (total_ms, launches)} for the classes in PROF_CLASSES."""
+        ms = np.zeros(len(PROF_CLASSES), dtype=np.float64)
+        cnt = np.zeros(len(PROF_CLASSES), dtype=np.int64)
+        self._check(lib().lcs_profile_steps(self._ctx, int(nsteps), _ptr(ms), _ptr(cnt)))
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(PROF_CLASSES)}
 
     @property
     def launches(self) -> int:

@@ -157,6 +157,45 @@ lcs_status enqueue_step(lcs_ctx *c, Ens &e, cudaStream_t st) {
   return LCS_OK;
 }
 
+// Un-graphed step with an event pair around each kernel class.
+struct Prof {
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> cls;
+  cudaEvent_t get() {
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    ev.push_back(e);
+    return e;
+  }
+};
+
+lcs_status enqueue_step_profiled(lcs_ctx *c, Ens &e, bool sort_now, Prof &pf) {
+  cudaStream_t st = c->st;
+  auto mark = [&](int cls) {
+    cudaEvent_t e0 = pf.get();
+    cudaEventRecord(e0, st);
+    pf.cls.push_back(cls);
+  };
+  mark(LCS_PROF_FLIP);
+  CK(cudaMemsetAsync(e.a.m.tile_status, 0, sizeof(unsigned long long) * e.max_tiles, st));
+  mark(LCS_PROF_STEP);
+  CK(launch_step(e.a, e.kind, e.step_grid, st));
+  mark(LCS_PROF_FINISH);
+  CK(launch_finish(e.a, st));
+  mark(LCS_PROF_UNPACK);
+  CK(launch_unpack(e.a, st));
+  mark(LCS_PROF_FLIP);
+  CK(launch_flip(e.a, st));
+  c->launches += 4;
+  if (sort_now && e.d.sort_every > 0) {
+    mark(LCS_PROF_SORT);
+    lcs_status r = enqueue_sort(c, e, st);
+    if (r != LCS_OK) return r;
+  }
+  mark(-1);
+  return LCS_OK;
+}
+
 lcs_status capture(lcs_ctx *c, bool with_sort, cudaGraphExec_t *out) {
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(c->cap_st, cudaStreamCaptureModeThreadLocal));
@@ -248,10 +287,7 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
     }
     switch (d.field_dtype) {
       case LCS_F64:
-        if (d.field_kernel == LCS_KERNEL_DF) {
-          r = fail(c, LCS_ERR_ARG, "LCS_KERNEL_DF is not available in this build");
-        }
-        e.kind = FK_F64;
+        e.kind = d.field_kernel == LCS_KERNEL_FP64 ? FK_F64 : FK_DF;
         break;
       case LCS_F32: e.kind = FK_F32; break;
       case LCS_BF16: e.kind = FK_BF16; break;
@@ -287,6 +323,17 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
     e.a.half_dt = 0.5 * d.dt;
     e.a.tau_const = d.tau ? 0.0 : d.tau_const;
     for (int s = 0; s < 3; ++s) e.a.g[s] = d.g[s];
+    {
+      // exact float-pair splits of the DF step's constants
+      auto split = [](double v, float *o) {
+        o[0] = (float)v;
+        o[1] = (float)(v - (double)o[0]);
+      };
+      split(d.dt, e.a.dfk + 0);
+      split(0.5 * d.dt, e.a.dfk + 2);
+      split(d.dt * g.inv_dx, e.a.dfk + 4);
+      for (int s = 0; s < 3; ++s) split(d.dt * d.g[s], e.a.dfk + 6 + 2 * s);
+    }
     const bool has_tau = d.tau != nullptr, has_img = d.track_images != 0;
     for (int b = 0; b < 2 && r == LCS_OK; ++b) r = alloc_rec(c, e.a.buf[b], e.cap, has_tau, has_img);
     if (r == LCS_OK) r = alloc_rec(c, e.a.pack, e.cap, has_tau, has_img);
@@ -542,6 +589,41 @@ lcs_status lcs_backward(lcs_ctx *c, const double *, const double *, double *, do
   lcs_status r = check_ctx(c);
   if (r != LCS_OK) return r;
   return fail(c, LCS_ERR_ARG, "lcs_backward: not available in this build");
+}
+
+lcs_status lcs_profile_steps(lcs_ctx *c, int64_t nsteps, double *ms, int64_t *count) {
+  lcs_status r = check_ctx(c);
+  if (r != LCS_OK) return r;
+  if (nsteps < 0 || !ms) return fail(c, LCS_ERR_ARG, "lcs_profile_steps: bad argument");
+  for (int k = 0; k < LCS_PROF_N; ++k) {
+    ms[k] = 0.0;
+    if (count) count[k] = 0;
+  }
+  for (int64_t k = 0; k < nsteps; ++k) {
+    const int64_t next = c->ens[0].steps + 1;
+    bool sort_now = false;
+    for (auto &e : c->ens) sort_now |= e.d.sort_every > 0 && next % e.d.sort_every == 0;
+    for (auto &e : c->ens) {
+      Prof pf;
+      r = enqueue_step_profiled(c, e, sort_now, pf);
+      if (r == LCS_OK) {
+        CK(cudaStreamSynchronize(c->st));
+        for (size_t i = 0; i + 1 < pf.ev.size(); ++i) {
+          float t = 0.f;
+          cudaEventElapsedTime(&t, pf.ev[i], pf.ev[i + 1]);
+          const int cls = pf.cls[i];
+          if (cls >= 0 && cls < LCS_PROF_N) {
+            ms[cls] += t;
+            if (count) count[cls] += 1;
+          }
+        }
+      }
+      for (auto ev : pf.ev) cudaEventDestroy(ev);
+      if (r != LCS_OK) return r;
+    }
+    for (auto &e : c->ens) ++e.steps;
+  }
+  return read_status(c);
 }
 
 lcs_status lcs_sync(lcs_ctx *c) {

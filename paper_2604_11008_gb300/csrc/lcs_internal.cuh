@@ -92,6 +92,8 @@ struct StepArgs {
   const void *field;
   int max_tiles;
   int64_t cap;       // slots per record buffer
+  // float-pair splits (hi, lo) of dt, dt/2, dt*N/L and dt*g for the DF step
+  float dfk[12];
 };
 
 // Segment containing global tile t: largest s with off[s] <= t.

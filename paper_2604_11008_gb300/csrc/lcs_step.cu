@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cuda/atomic>
 
+#include "lcs_df.cuh"
 #include "lcs_internal.cuh"
 
 namespace lcs {
@@ -191,6 +192,122 @@ __device__ __forceinline__ void interp(const void *field, const Geom &g, double 
   }
 }
 
+// ---------------------------------------------------------------- DF interpolation
+
+// Product of two float pairs without renormalisation: (p, e) with
+// p = RN(a.h b.h) and e = the exact rounding error plus the cross terms.
+__device__ __forceinline__ df mul_un(df a, df b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  return {p, e};
+}
+
+// Trilinear interpolation (Sec. 2.2) in float-float arithmetic from the
+// fixed-point coordinates q[s] = x_s N/L * 2^52.  The field record of a
+// cell holds the float pairs of u, v, w: (hu, hv, hw, lu) (lv, lw, -, -).
+// Corner weights are float-float products of the per-axis weights; each
+// weight-times-value product is split exactly (fma error), the high parts
+// are summed with two_sum and every small term goes to a compensation sum.
+__device__ __forceinline__ void interp_df(const float4 *__restrict__ f, int N,
+                                          const long long q[3], df U[3]) {
+  const Axis ax = axis_from_fix(q[0]), ay = axis_from_fix(q[1]), az = axis_from_fix(q[2]);
+  const int i0 = wrap_cell(ax.i0, N), j0 = wrap_cell(ay.i0, N), k0 = wrap_cell(az.i0, N);
+  const int i1 = i0 + 1 == N ? 0 : i0 + 1, j1 = j0 + 1 == N ? 0 : j0 + 1,
+            k1 = k0 + 1 == N ? 0 : k0 + 1;
+  const df wx[2] = {{__fsub_rn(1.0f, ax.th), -ax.tl}, {ax.th, ax.tl}};
+  const df wy[2] = {{__fsub_rn(1.0f, ay.th), -ay.tl}, {ay.th, ay.tl}};
+  const df wz[2] = {{__fsub_rn(1.0f, az.th), -az.tl}, {az.th, az.tl}};
+  const uint32_t ii[2] = {(uint32_t)i0, (uint32_t)i1};
+  const uint32_t jj[2] = {(uint32_t)j0 * N, (uint32_t)j1 * N};
+  const uint32_t kk[2] = {(uint32_t)k0 * N * N, (uint32_t)k1 * N * N};
+  float s[3], c[3];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const df wab = mul_un(wx[a], wy[b]);
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        const df w = mul_un(wab, wz[d]);
+        const size_t cell = (size_t)(ii[a] + jj[b] + kk[d]);
+        const float4 A = __ldg(f + 2 * cell), B = __ldg(f + 2 * cell + 1);
+        const float hv[3] = {A.x, A.y, A.z}, lv[3] = {A.w, B.x, B.y};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float P = __fmul_rn(w.h, hv[k]);
+          const float E = __fmaf_rn(w.h, hv[k], -P);
+          float t;
+          if (a == 0 && b == 0 && d == 0) {
+            s[k] = P;
+            t = E;
+          } else {
+            const df st = two_sum(s[k], P);
+            s[k] = st.h;
+            t = __fadd_rn(st.l, E);
+          }
+          float small = __fmaf_rn(w.h, lv[k], t);
+          small = __fmaf_rn(w.l, hv[k], small);
+          c[k] = (a == 0 && b == 0 && d == 0) ? small : __fadd_rn(c[k], small);
+        }
+      }
+    }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) U[k] = fast_two_sum(s[k], c[k]);
+}
+
+// Heun step of Eqs. (5)-(6) (f = 1, gravity g) with float-float increments:
+//   h = dt/tau, D1 = U(X) - V, V* = V + h D1 + dt g, X* = X + dt V,
+//   D2 = U(X*) - V*, dV = (h D1 + h D2)/2 + dt g,
+//   dX = dt V + (dt/2)(h D1 + dt g)          [= dt (V + V*)/2]
+// then X' = X + dX and V' = V + dV in FP64, and the periodic wrap.
+__device__ __forceinline__ void heun_step_df(const StepArgs &a, double x[3], double v[3],
+                                             double tau, int img[3], int &bad) {
+  const Geom &g = a.geo;
+  const df dt = {a.dfk[0], a.dfk[1]}, hdt = {a.dfk[2], a.dfk[3]}, cx = {a.dfk[4], a.dfk[5]};
+  const df h = df_mul(dt, df_recip(split_d(tau)));
+  long long q[3];
+  df V[3], U[3], hD1[3], Vs[3];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) q[s] = d_to_fix52(__dmul_rn(x[s], g.inv_dx));
+  interp_df((const float4 *)a.field, g.N, q, U);
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const df gd = {a.dfk[6 + 2 * s], a.dfk[7 + 2 * s]};
+    V[s] = split_d(v[s]);
+    hD1[s] = df_mul(h, df_add(U[s], df_neg(V[s])));
+    Vs[s] = df_add(df_add(V[s], hD1[s]), gd);
+    const df cv = df_mul(cx, V[s]);
+    q[s] += f_to_fix52(cv.h) + f_to_fix52(cv.l);
+  }
+  interp_df((const float4 *)a.field, g.N, q, U);
+  const long long bitsL = __double_as_longlong(g.L);
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const df gd = {a.dfk[6 + 2 * s], a.dfk[7 + 2 * s]};
+    const df hD2 = df_mul(h, df_add(U[s], df_neg(Vs[s])));
+    const df dV = df_add(df_scale2(df_add(hD1[s], hD2), 0.5f), gd);
+    const df dX = df_add(df_mul(dt, V[s]), df_mul(hdt, df_add(hD1[s], gd)));
+    if (!(fabsf(dX.h) < (float)(0.5 * g.L))) bad |= 2;
+    double xn = __dadd_rn(x[s], df_to_double(dX));
+    const double vn = __dadd_rn(v[s], df_to_double(dV));
+    const long long bx = __double_as_longlong(xn);
+    if (((bx >> 52) & 0x7ff) == 0x7ff || ((__double_as_longlong(vn) >> 52) & 0x7ff) == 0x7ff)
+      bad |= 1;
+    if (bx < 0) {
+      xn = __dadd_rn(xn, g.L);
+      img[s] -= 1;
+    } else if (bx >= bitsL) {
+      xn = __dsub_rn(xn, g.L);
+      img[s] += 1;
+    }
+    if (__double_as_longlong(xn) == bitsL) xn = 0.0;
+    x[s] = xn;
+    v[s] = vn;
+  }
+}
+
 // ---------------------------------------------------------------- look-back
 
 constexpr unsigned long long FLAG_AGG = 1ull << 62;
@@ -312,7 +429,9 @@ __device__ __forceinline__ int dest_bin(const Geom &g, int seg, const double x[3
   int bin = 0, mul = 1;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
-    int c = (int)floor(__dmul_rn(x[s], g.inv_dx));
+    // floor of the correctly rounded product x N/L (x >= 0 after the wrap),
+    // taken from its fixed-point form without the FP64 floor
+    int c = (int)(d_to_fix52(__dmul_rn(x[s], g.inv_dx)) >> 52);
     c = min(max(c, 0), g.N - 1);
     const int dc = dir_comp(ps[s], c / g.W[s], g.P[s]);
     if (dc == 2) return -1;
@@ -361,7 +480,8 @@ __global__ void __launch_bounds__(STEP_BLOCK) k_step(StepArgs a) {
       bin[k] = -2;  // invalid item
       if (l0 + k < cnt) {
         load_rec(A, bA + l0 + k, x[k], v[k], tau[k], id[k], img[k], a.tau_const);
-        heun_step<KIND>(a, x[k], v[k], tau[k], img[k], bad);
+        if (KIND == FK_DF) heun_step_df(a, x[k], v[k], tau[k], img[k], bad);
+        else heun_step<KIND>(a, x[k], v[k], tau[k], img[k], bad);
         int b = dest_bin(a.geo, seg, x[k]);
         if (b < 0) {
           bad |= 2;
@@ -442,6 +562,7 @@ cudaError_t launch_step(const StepArgs &a, FieldKind kind, int grid, cudaStream_
     case FK_F64: k_step<FK_F64><<<grid, STEP_BLOCK, 0, st>>>(a); break;
     case FK_F32: k_step<FK_F32><<<grid, STEP_BLOCK, 0, st>>>(a); break;
     case FK_BF16: k_step<FK_BF16><<<grid, STEP_BLOCK, 0, st>>>(a); break;
+    case FK_DF: k_step<FK_DF><<<grid, STEP_BLOCK, 0, st>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -453,6 +574,7 @@ int step_kernel_occupancy(FieldKind kind) {
     case FK_F64: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<FK_F64>, STEP_BLOCK, 0); break;
     case FK_F32: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<FK_F32>, STEP_BLOCK, 0); break;
     case FK_BF16: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<FK_BF16>, STEP_BLOCK, 0); break;
+    case FK_DF: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<FK_DF>, STEP_BLOCK, 0); break;
     default: break;
   }
   return n;
