@@ -151,45 +151,23 @@ __device__ __forceinline__ void stencil64(const Geom &g, double x, double y, dou
       }
 }
 
-template <int KIND>
-__device__ __forceinline__ void interp(const void *field, const Geom &g, double x, double y,
-                                       double z, double &u, double &v, double &w) {
+// FP64 trilinear interpolation of the FP64 field (all arithmetic on the FP64
+// pipe; the reference form of the step, LCS_KERNEL_FP64).
+__device__ __forceinline__ void interp64(const void *field, const Geom &g, double x, double y,
+                                         double z, double &u, double &v, double &w) {
   Stencil S;
   stencil64(g, x, y, z, S);
-  if (KIND == FK_F64) {
-    const double2 *f = (const double2 *)field;
-    double au = 0.0, av = 0.0, aw = 0.0;
+  const double2 *f = (const double2 *)field;
+  double au = 0.0, av = 0.0, aw = 0.0;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const double2 p = __ldg(f + 2 * (size_t)S.c[q]);
-      const double2 r = __ldg(f + 2 * (size_t)S.c[q] + 1);
-      au = fma(S.w[q], p.x, au);
-      av = fma(S.w[q], p.y, av);
-      aw = fma(S.w[q], r.x, aw);
-    }
-    u = au, v = av, w = aw;
-  } else {
-    // FP32 / BF16 storage: FP64 weights rounded to FP32, FP32 accumulation.
-    float au = 0.f, av = 0.f, aw = 0.f;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const float wq = __double2float_rn(S.w[q]);
-      float fu, fv, fw;
-      if (KIND == FK_F32) {
-        const float4 p = __ldg((const float4 *)field + S.c[q]);
-        fu = p.x, fv = p.y, fw = p.z;
-      } else {
-        const uint2 p = __ldg((const uint2 *)field + S.c[q]);
-        fu = __uint_as_float((p.x & 0xffffu) << 16);
-        fv = __uint_as_float(p.x & 0xffff0000u);
-        fw = __uint_as_float((p.y & 0xffffu) << 16);
-      }
-      au = fmaf(wq, fu, au);
-      av = fmaf(wq, fv, av);
-      aw = fmaf(wq, fw, aw);
-    }
-    u = au, v = av, w = aw;
+  for (int q = 0; q < 8; ++q) {
+    const double2 p = __ldg(f + 2 * (size_t)S.c[q]);
+    const double2 r = __ldg(f + 2 * (size_t)S.c[q] + 1);
+    au = fma(S.w[q], p.x, au);
+    av = fma(S.w[q], p.y, av);
+    aw = fma(S.w[q], r.x, aw);
   }
+  u = au, v = av, w = aw;
 }
 
 // ---------------------------------------------------------------- DF interpolation
@@ -257,11 +235,63 @@ __device__ __forceinline__ void interp_df(const float4 *__restrict__ f, int N,
   for (int k = 0; k < 3; ++k) U[k] = fast_two_sum(s[k], c[k]);
 }
 
+// Trilinear interpolation (Sec. 2.2) for FP32 / BF16 field storage: weights
+// from the fixed-point coordinates rounded to FP32, FP32 accumulation.
+template <int KIND>
+__device__ __forceinline__ void interp_lo(const void *__restrict__ field, int N,
+                                          const long long q[3], df U[3]) {
+  const Axis ax = axis_from_fix(q[0]), ay = axis_from_fix(q[1]), az = axis_from_fix(q[2]);
+  const int i0 = wrap_cell(ax.i0, N), j0 = wrap_cell(ay.i0, N), k0 = wrap_cell(az.i0, N);
+  const int i1 = i0 + 1 == N ? 0 : i0 + 1, j1 = j0 + 1 == N ? 0 : j0 + 1,
+            k1 = k0 + 1 == N ? 0 : k0 + 1;
+  const float tx = __fadd_rn(ax.th, ax.tl), ty = __fadd_rn(ay.th, ay.tl),
+              tz = __fadd_rn(az.th, az.tl);
+  const float wx[2] = {__fsub_rn(1.0f, tx), tx}, wy[2] = {__fsub_rn(1.0f, ty), ty},
+              wz[2] = {__fsub_rn(1.0f, tz), tz};
+  const uint32_t ii[2] = {(uint32_t)i0, (uint32_t)i1};
+  const uint32_t jj[2] = {(uint32_t)j0 * N, (uint32_t)j1 * N};
+  const uint32_t kk[2] = {(uint32_t)k0 * N * N, (uint32_t)k1 * N * N};
+  float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const float wab = __fmul_rn(wx[a], wy[b]);
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        const float w = __fmul_rn(wab, wz[d]);
+        const uint32_t cell = ii[a] + jj[b] + kk[d];
+        float f[3];
+        if (KIND == FK_F32) {
+          const float4 p = __ldg((const float4 *)field + cell);
+          f[0] = p.x, f[1] = p.y, f[2] = p.z;
+        } else {
+          const uint2 p = __ldg((const uint2 *)field + cell);
+          f[0] = __uint_as_float((p.x & 0xffffu) << 16);
+          f[1] = __uint_as_float(p.x & 0xffff0000u);
+          f[2] = __uint_as_float((p.y & 0xffffu) << 16);
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) acc[k] = __fmaf_rn(w, f[k], acc[k]);
+      }
+    }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) U[k] = {acc[k], 0.f};
+}
+
+template <int KIND>
+__device__ __forceinline__ void interp_any(const void *field, int N, const long long q[3],
+                                           df U[3]) {
+  if (KIND == FK_DF) interp_df((const float4 *)field, N, q, U);
+  else interp_lo<KIND>(field, N, q, U);
+}
+
 // Heun step of Eqs. (5)-(6) (f = 1, gravity g) with float-float increments:
 //   h = dt/tau, D1 = U(X) - V, V* = V + h D1 + dt g, X* = X + dt V,
 //   D2 = U(X*) - V*, dV = (h D1 + h D2)/2 + dt g,
 //   dX = dt V + (dt/2)(h D1 + dt g)          [= dt (V + V*)/2]
 // then X' = X + dX and V' = V + dV in FP64, and the periodic wrap.
+template <int KIND>
 __device__ __forceinline__ void heun_step_df(const StepArgs &a, double x[3], double v[3],
                                              double tau, int img[3], int &bad) {
   const Geom &g = a.geo;
@@ -271,7 +301,7 @@ __device__ __forceinline__ void heun_step_df(const StepArgs &a, double x[3], dou
   df V[3], U[3], hD1[3], Vs[3];
 #pragma unroll
   for (int s = 0; s < 3; ++s) q[s] = d_to_fix52(__dmul_rn(x[s], g.inv_dx));
-  interp_df((const float4 *)a.field, g.N, q, U);
+  interp_any<KIND>(a.field, g.N, q, U);
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     const df gd = {a.dfk[6 + 2 * s], a.dfk[7 + 2 * s]};
@@ -281,7 +311,7 @@ __device__ __forceinline__ void heun_step_df(const StepArgs &a, double x[3], dou
     const df cv = df_mul(cx, V[s]);
     q[s] += f_to_fix52(cv.h) + f_to_fix52(cv.l);
   }
-  interp_df((const float4 *)a.field, g.N, q, U);
+  interp_any<KIND>(a.field, g.N, q, U);
   const long long bitsL = __double_as_longlong(g.L);
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
@@ -387,21 +417,20 @@ __device__ __forceinline__ void store_rec(const Rec &R, int64_t i, const double 
   R.id[i] = id;
 }
 
-// One Heun step of Eqs. (5)-(6) (f = 1, gravity g) with periodic wrap.
-template <int KIND>
-__device__ __forceinline__ void heun_step(const StepArgs &a, double x[3], double v[3],
+// One Heun step of Eqs. (5)-(6) (f = 1, gravity g) with periodic wrap, in FP64.
+__device__ __forceinline__ void heun_step64(const StepArgs &a, double x[3], double v[3],
                                           double tau, int img[3], int &bad) {
   const Geom &g = a.geo;
   const double itau = 1.0 / tau;
   double u1[3], a1[3], xs[3], vs[3], u2[3];
-  interp<KIND>(a.field, g, x[0], x[1], x[2], u1[0], u1[1], u1[2]);
+  interp64(a.field, g, x[0], x[1], x[2], u1[0], u1[1], u1[2]);
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     a1[s] = (u1[s] - v[s]) * itau + a.g[s];
     xs[s] = x[s] + a.dt * v[s];
     vs[s] = v[s] + a.dt * a1[s];
   }
-  interp<KIND>(a.field, g, xs[0], xs[1], xs[2], u2[0], u2[1], u2[2]);
+  interp64(a.field, g, xs[0], xs[1], xs[2], u2[0], u2[1], u2[2]);
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     const double a2 = (u2[s] - vs[s]) * itau + a.g[s];
@@ -480,8 +509,8 @@ __global__ void __launch_bounds__(STEP_BLOCK) k_step(StepArgs a) {
       bin[k] = -2;  // invalid item
       if (l0 + k < cnt) {
         load_rec(A, bA + l0 + k, x[k], v[k], tau[k], id[k], img[k], a.tau_const);
-        if (KIND == FK_DF) heun_step_df(a, x[k], v[k], tau[k], img[k], bad);
-        else heun_step<KIND>(a, x[k], v[k], tau[k], img[k], bad);
+        if (KIND == FK_F64) heun_step64(a, x[k], v[k], tau[k], img[k], bad);
+        else heun_step_df<KIND>(a, x[k], v[k], tau[k], img[k], bad);
         int b = dest_bin(a.geo, seg, x[k]);
         if (b < 0) {
           bad |= 2;
