@@ -202,6 +202,28 @@ int64_t lcs_launch_count(lcs_ctx *ctx);
 lcs_status lcs_partition(const uint32_t *keys, int64_t n, int nbins, uint32_t *perm,
                          int64_t *bin_off, int32_t *status, void *stream);
 
+/* Largest n accepted by lcs_partition_noalloc. */
+#define LCS_PARTITION_NOALLOC_MAX_N (1 << 20)
+
+/* lcs_partition for callers that cannot allocate device memory where they
+ * call it: code running while its stream is captured into a CUDA graph,
+ * code under a fixed device-memory budget, or latency-critical loops that
+ * cannot afford the synchronisation of cudaMalloc / cudaFree.  Same
+ * arguments, results and asynchrony as lcs_partition, but no allocation of
+ * any kind: the scratch is a file-scope device array of about 13.6 MB that
+ * every GPU loading the library keeps until the process exits.
+ * Limits: n <= LCS_PARTITION_NOALLOC_MAX_N (larger n returns LCS_ERR_ARG
+ * before any work is enqueued), 1 <= nbins <= 65536.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture on that device.  All calls share the one array, so two
+ * calls that may run at the same time on the GPU (different streams without
+ * ordering, or different host threads) race and corrupt each other's
+ * results; order them on one stream.  The paper has no counterpart of this
+ * entry point: it is an interface variant of lcs_partition. */
+lcs_status lcs_partition_noalloc(const uint32_t *keys, int64_t n, int nbins, uint32_t *perm,
+                                 int64_t *bin_off, int32_t *status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

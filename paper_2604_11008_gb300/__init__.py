@@ -33,7 +33,8 @@ KERNELS = {"auto": 0, "fp64": 1, "df": 2}
 # Every symbol declared in include/lcs.h.
 EXPORTS = ("lcs_init", "lcs_step", "lcs_migrate", "lcs_sort", "lcs_set_state", "lcs_get_state",
            "lcs_get_field", "lcs_backward", "lcs_sync", "lcs_last_error", "lcs_destroy",
-           "lcs_launch_count", "lcs_partition", "lcs_profile_steps")
+           "lcs_launch_count", "lcs_partition", "lcs_profile_steps", "lcs_partition_noalloc")
+PARTITION_NOALLOC_MAX_N = 1 << 20
 PROF_CLASSES = ("step", "finish", "unpack", "flip", "sort")
 
 
@@ -81,9 +82,10 @@ def lib():
         L.lcs_launch_count.restype = i64
         L.lcs_partition.argtypes = [P, i64, i32, P, P, P, P]
         L.lcs_profile_steps.argtypes = [P, i64, P, P]
+        L.lcs_partition_noalloc.argtypes = [P, i64, i32, P, P, P, P]
         for name in ("lcs_init", "lcs_step", "lcs_migrate", "lcs_sort", "lcs_set_state",
                      "lcs_get_state", "lcs_get_field", "lcs_backward", "lcs_sync",
-                     "lcs_partition", "lcs_profile_steps"):
+                     "lcs_partition", "lcs_profile_steps", "lcs_partition_noalloc"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
