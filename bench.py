@@ -124,6 +124,45 @@ def oracle_rate(w, field_np, dt, x, v, tau, n_sample: int, steps: int):
     return n_sample * steps / t, t
 
 
+# ---------------------------------------------------------------- adjoint
+
+def adjoint_ratio(lcs, torch, steps=None):
+    """Forward (with checkpoints every 20 steps) and backward time of the
+    differentiation workload: 128^3 field, 2^20 particles, 200 steps."""
+    w = synth.WORKLOADS["grad_128"]
+    field, _ = synth.make_field(w, device="cuda")
+    dt = synth.cfl_dt(synth.max_speed(field), w.N)
+    x, v, _ = synth.make_particles(w, dt)
+    target = torch.from_numpy(synth.positions(w.np_, synth.rng(w.number,
+                                                               synth.STREAM_TARGET))).cuda()
+    steps = steps or w.steps
+    res = {}
+    for rep in range(2):  # first repetition warms up (graph capture, allocations)
+        sim = lcs.Simulator(field, x, v, dt, tau_const=w.tau_const, sub=w.sub, ckpt_every=20,
+                            track_images=True, sort_every=10)
+        st = torch.cuda.current_stream()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        torch.cuda.synchronize()
+        e0.record(st)
+        sim.step(steps)
+        e1.record(st)
+        xt, _ = sim.final_state_by_id()
+        gx = 2.0 / w.np_ * (xt - target)
+        gv = torch.zeros_like(gx)
+        torch.cuda.synchronize()
+        e1b = torch.cuda.Event(enable_timing=True)
+        e1b.record(st)
+        sim.backward(gx, gv)
+        e2.record(st)
+        torch.cuda.synchronize()
+        fwd, bwd = e0.elapsed_time(e1), e1b.elapsed_time(e2)
+        res = {"workload": "grad_128 (128^3, 2^20 particles, 2x2x2, checkpoints every 20)",
+               "steps": steps, "forward_ms": round(fwd, 3), "backward_ms": round(bwd, 3),
+               "ratio": round(bwd / fwd, 3)}
+        sim.close()
+    return res
+
+
 # ---------------------------------------------------------------- main
 
 def main():
@@ -138,6 +177,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1 << 20)
+    ap.add_argument("--adjoint", type=int, default=1,
+                    help="also time forward (taped) vs backward on grad_128")
     ap.add_argument("--np", type=int, default=0,
                     help="particle count override (small profiling cases only)")
     args = ap.parse_args()
@@ -235,6 +276,10 @@ def main():
                "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "wall_s": round(time.perf_counter() - t0, 3)}
 
+    adjoint = None
+    if rank == 0 and args.adjoint:
+        adjoint = adjoint_ratio(lcs, torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         field_np = field.cpu().numpy() if args.field == "f64" else None
@@ -259,7 +304,7 @@ def main():
                           "field_storage": args.field, "kernel": args.kernel,
                           "l2": "inputs larger than L2 (state ~1 GB, field 0.54 GB)",
                           "parallelism": f"replicas{world}"},
-               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "adjoint": adjoint,
                "gpu_launches": int(launches), "clocks": clk,
                "kernel_profile_ms": {k: round(v_[0], 4) for k, v_ in prof.items()}}
         print(json.dumps(out))

@@ -245,6 +245,34 @@ class Simulator:
         self._check(lib().lcs_set_state(self._ctx, ens, _ptr(xs), _ptr(vs), _ptr(tt), _ptr(ii),
                                         _ptr(im), _ptr(seg)))
 
+    def final_state_by_id(self, ens: int = 0):
+        """(X, V) as (3, np) CUDA tensors in particle-id order, X unwrapped (x + L img)."""
+        import torch
+        st = self.get_state(ens=ens)
+        order = torch.argsort(st["ids"].long())
+        box = self.meta[ens]["box"]
+        x = st["x"][:, order] + box * st["img"][:, order].to(torch.float64)
+        return x, st["v"][:, order]
+
+    def backward(self, gx, gv, gU=None):
+        """Adjoint of the recorded steps (lcs_backward).
+
+        gx, gv: dLoss/dX_T (unwrapped) and dLoss/dV_T, (3, np) in particle-id
+        order.  Returns (dLoss/dU [3,N,N,N], dLoss/dX0, dLoss/dV0) as CUDA
+        tensors; dLoss/dU is accumulated into gU when given."""
+        import torch
+        m = self.meta[0]
+        n, N = m["np"], m["n"]
+        gxd = _dev(gx, torch.float64)
+        gvd = _dev(gv, torch.float64)
+        if gU is None:
+            gU = torch.zeros((3, N, N, N), dtype=torch.float64, device="cuda")
+        gx0 = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        gv0 = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        self._check(lib().lcs_backward(self._ctx, _ptr(gxd), _ptr(gvd), _ptr(gU), _ptr(gx0),
+                                       _ptr(gv0)))
+        return gU, gx0, gv0
+
     def get_field(self, ens: int = 0):
         import torch
         n = self.meta[ens]["n"]
@@ -269,3 +297,51 @@ def partition(keys, nbins: int, stream=None):
     if st != LCS_OK:
         raise LcsError(st, "lcs_partition failed")
     return perm[:n], off, status
+
+
+def _autograd_function():
+    import torch
+
+    class ParticleAdvect(torch.autograd.Function):
+        """(U, X0, V0) -> (X_T unwrapped, V_T) after `steps` steps, differentiable.
+
+        U: [3,N,N,N] FP64 field; X0, V0: (3, np) in particle-id order (X0 may lie
+        outside [0, L): it is wrapped on entry and the image shift is added back
+        to X_T).  The backward pass is the library's hand-written adjoint
+        (lcs_backward) with checkpoints every `ckpt_every` steps."""
+
+        @staticmethod
+        def forward(ctx, U, X0, V0, opts):
+            box = float(opts.get("box", 2 * math.pi))
+            x0 = X0.detach().to(torch.float64)
+            shift = torch.floor(x0 / box)
+            xw = x0 - box * shift
+            xw = torch.where(xw >= box, xw - box, xw)
+            xw = torch.where(xw < 0, torch.zeros_like(xw), xw)
+            kw = {k: v for k, v in opts.items() if k not in ("steps",)}
+            kw.setdefault("ckpt_every", 20)
+            kw["track_images"] = True
+            sim = Simulator(U.detach(), xw, V0.detach(), **kw)
+            sim.step(int(opts["steps"]))
+            xt, vt = sim.final_state_by_id()
+            ctx.sim = sim
+            return xt + box * shift.to(xt.device), vt
+
+        @staticmethod
+        def backward(ctx, gX, gV):
+            sim = ctx.sim
+            n = sim.meta[0]["np"]
+            zeros = torch.zeros((3, n), dtype=torch.float64, device="cuda")
+            gX = zeros if gX is None else gX
+            gV = zeros if gV is None else gV
+            gU, gx0, gv0 = sim.backward(gX.contiguous(), gV.contiguous())
+            sim.close()
+            ctx.sim = None
+            return gU, gx0, gv0, None
+
+    return ParticleAdvect
+
+
+def particle_advect(U, X0, V0, **opts):
+    """Differentiable advection: returns (X_T, V_T); see ParticleAdvect."""
+    return _autograd_function().apply(U, X0, V0, opts)

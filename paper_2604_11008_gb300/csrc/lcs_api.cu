@@ -50,6 +50,10 @@ struct Ens {
   int64_t *cs1 = nullptr;
   int *to1 = nullptr;
   int64_t steps = 0;
+  // adjoint tape: checkpoint k holds the state after k*ckpt_every steps
+  std::vector<TapeSlot> tape;
+  bool tape_ok = false;
+  double *states = nullptr, *lam_id = nullptr, *lam_s = nullptr;
 };
 
 }  // namespace
@@ -228,6 +232,21 @@ int64_t launches_per_step(lcs_ctx *c, bool with_sort) {
     }
   }
   return n;
+}
+
+// Record checkpoint k of ensemble e (allocating its slot on first use).
+lcs_status tape_store(lcs_ctx *c, Ens &e, int64_t k) {
+  while ((int64_t)e.tape.size() <= k) {
+    TapeSlot t{};
+    CK(dalloc(c, &t.x, 3 * std::max<int64_t>(e.np, 1)));
+    CK(dalloc(c, &t.v, 3 * std::max<int64_t>(e.np, 1)));
+    if (e.d.tau) CK(dalloc(c, &t.tau, std::max<int64_t>(e.np, 1)));
+    CK(dalloc(c, &t.id, std::max<int64_t>(e.np, 1)));
+    e.tape.push_back(t);
+  }
+  if (e.np > 0) CK(launch_tape_store(e.a, e.tape[k], e.np, c->st));
+  c->launches += 1;
+  return LCS_OK;
 }
 
 lcs_status check_ctx(lcs_ctx *c) {
@@ -417,6 +436,10 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
     C2(cudaFreeAsync(seg_dev, st));
     C2(cudaGetLastError());
     if (r == LCS_OK) r = enqueue_migrate(c, e);
+    if (r == LCS_OK && d.ckpt_every > 0) {
+      r = tape_store(c, e, 0);
+      e.tape_ok = true;
+    }
     int occ = step_kernel_occupancy(e.kind);
     e.step_grid = std::max(1, std::min(e.max_tiles, std::max(1, occ) * c->sms));
     if (r == LCS_OK) {
@@ -463,7 +486,13 @@ lcs_status lcs_step(lcs_ctx *c, int64_t nsteps) {
     for (auto &e : c->ens) sort_now |= e.d.sort_every > 0 && next % e.d.sort_every == 0;
     CK(cudaGraphLaunch(sort_now ? c->g_sort : c->g_step, c->st));
     c->launches += launches_per_step(c, sort_now);
-    for (auto &e : c->ens) ++e.steps;
+    for (auto &e : c->ens) {
+      ++e.steps;
+      if (e.d.ckpt_every > 0 && e.steps % e.d.ckpt_every == 0) {
+        r = tape_store(c, e, e.steps / e.d.ckpt_every);
+        if (r != LCS_OK) return r;
+      }
+    }
   }
   return LCS_OK;
 }
@@ -498,6 +527,7 @@ lcs_status lcs_set_state(lcs_ctx *c, int ens, const double *x, const double *v,
   Ens &e = c->ens[ens];
   const int P = e.a.geo.Ptot;
   if (seg[0] != 0 || seg[P] != e.np) return fail(c, LCS_ERR_ARG, "lcs_set_state: bad segments");
+  e.tape_ok = false;  // the recorded trajectory no longer leads to this state
   for (int s = 0; s < P; ++s)
     if (seg[s + 1] < seg[s]) return fail(c, LCS_ERR_ARG, "lcs_set_state: bad segments");
   cudaStream_t st = c->st;
@@ -548,10 +578,8 @@ lcs_status lcs_get_state(lcs_ctx *c, int ens, double *x, double *v, double *tau,
   for (int s = 0; s < 3 && e.np > 0; ++s) {
     if (x) CK(cudaMemcpyAsync(x + s * e.np, tmp.x[s], e.np * 8, cudaMemcpyDefault, st));
     if (v) CK(cudaMemcpyAsync(v + s * e.np, tmp.v[s], e.np * 8, cudaMemcpyDefault, st));
-    if (img) {
-      if (tmp.img[s]) CK(cudaMemcpyAsync(img + s * e.np, tmp.img[s], e.np * 4, cudaMemcpyDefault, st));
-      else CK(cudaMemsetAsync(img + s * e.np, 0, e.np * 4, st));  // device only
-    }
+    if (img && tmp.img[s])
+      CK(cudaMemcpyAsync(img + s * e.np, tmp.img[s], e.np * 4, cudaMemcpyDefault, st));
   }
   if (tau && e.np > 0) {
     if (tmp.tau) {
@@ -560,6 +588,17 @@ lcs_status lcs_get_state(lcs_ctx *c, int ens, double *x, double *v, double *tau,
       std::vector<double> t(e.np, e.d.tau_const);
       CK(cudaMemcpyAsync(tau, t.data(), e.np * 8, cudaMemcpyDefault, st));
       CK(cudaStreamSynchronize(st));
+    }
+  }
+  if (img && !tmp.img[0] && e.np > 0) {
+    // images not tracked: zeros, written on the side of the pointer
+    cudaPointerAttributes pa{};
+    CK(cudaPointerGetAttributes(&pa, img));
+    if (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged) {
+      CK(cudaMemsetAsync(img, 0, 3 * e.np * 4, st));
+    } else {
+      CK(cudaStreamSynchronize(st));
+      std::memset(img, 0, 3 * e.np * 4);
     }
   }
   if (ids && e.np > 0) CK(cudaMemcpyAsync(ids, tmp.id, e.np * 4, cudaMemcpyDefault, st));
@@ -584,11 +623,44 @@ lcs_status lcs_get_field(lcs_ctx *c, int ens, double *out) {
   return LCS_OK;
 }
 
-lcs_status lcs_backward(lcs_ctx *c, const double *, const double *, double *, double *,
-                        double *) {
+lcs_status lcs_backward(lcs_ctx *c, const double *gx, const double *gv, double *gU,
+                        double *gx0, double *gv0) {
   lcs_status r = check_ctx(c);
   if (r != LCS_OK) return r;
-  return fail(c, LCS_ERR_ARG, "lcs_backward: not available in this build");
+  if (c->ens.size() != 1) return fail(c, LCS_ERR_ARG, "lcs_backward: one ensemble only");
+  Ens &e = c->ens[0];
+  const int K = e.d.ckpt_every;
+  if (K <= 0 || !e.d.track_images || !e.tape_ok)
+    return fail(c, LCS_ERR_ARG, "lcs_backward: needs ckpt_every > 0, track_images = 1 and no "
+                                "lcs_set_state since lcs_init");
+  if (!gx || !gv || !gU || !gx0 || !gv0) return fail(c, LCS_ERR_ARG, "lcs_backward: null pointer");
+  const int64_t np = e.np, T = e.steps;
+  cudaStream_t st = c->st;
+  if (!e.lam_id) {
+    CK(dalloc(c, &e.lam_id, 6 * std::max<int64_t>(np, 1)));
+    CK(dalloc(c, &e.lam_s, 6 * std::max<int64_t>(np, 1)));
+    CK(dalloc(c, &e.states, (int64_t)K * 6 * std::max<int64_t>(np, 1)));
+  }
+  if (np > 0) {
+    CK(cudaMemcpyAsync(e.lam_id, gx, 3 * np * 8, cudaMemcpyDefault, st));
+    CK(cudaMemcpyAsync(e.lam_id + 3 * np, gv, 3 * np * 8, cudaMemcpyDefault, st));
+    for (int64_t k = (T - 1) / K; T > 0 && k >= 0; --k) {
+      const int64_t s0 = k * K;
+      const int len = (int)std::min<int64_t>(K, T - s0);
+      const TapeSlot &t = e.tape[k];
+      CK(launch_recompute(e.a, e.kind, t, e.states, len, np, st));
+      CK(launch_lam_permute(t.id, e.lam_id, e.lam_s, np, 1, e.a.m.status, st));
+      for (int j = len - 1; j >= 0; --j)
+        CK(launch_adjoint(e.a, e.kind, e.states + (int64_t)j * 6 * np, t.tau, e.lam_s, gU, np,
+                          st));
+      CK(launch_lam_permute(t.id, e.lam_s, e.lam_id, np, 0, e.a.m.status, st));
+      c->launches += 3 + len;
+    }
+    CK(cudaMemcpyAsync(gx0, e.lam_id, 3 * np * 8, cudaMemcpyDefault, st));
+    CK(cudaMemcpyAsync(gv0, e.lam_id + 3 * np, 3 * np * 8, cudaMemcpyDefault, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  return read_status(c);
 }
 
 lcs_status lcs_profile_steps(lcs_ctx *c, int64_t nsteps, double *ms, int64_t *count) {
@@ -621,7 +693,13 @@ lcs_status lcs_profile_steps(lcs_ctx *c, int64_t nsteps, double *ms, int64_t *co
       for (auto ev : pf.ev) cudaEventDestroy(ev);
       if (r != LCS_OK) return r;
     }
-    for (auto &e : c->ens) ++e.steps;
+    for (auto &e : c->ens) {
+      ++e.steps;
+      if (e.d.ckpt_every > 0 && e.steps % e.d.ckpt_every == 0) {
+        r = tape_store(c, e, e.steps / e.d.ckpt_every);
+        if (r != LCS_OK) return r;
+      }
+    }
   }
   return read_status(c);
 }

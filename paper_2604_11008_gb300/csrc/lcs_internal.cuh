@@ -215,6 +215,20 @@ cudaError_t launch_field_expand(const void *src, int N, FieldKind kind, double *
                                 cudaStream_t st);
 int step_kernel_occupancy(FieldKind kind);
 
+// Adjoint: checkpoint of the live particles (compacted, storage order).
+struct TapeSlot {
+  double *x, *v, *tau;  // [3][np], [3][np], [np] or nullptr
+  uint32_t *id;         // [np]
+};
+cudaError_t launch_tape_store(const StepArgs &a, const TapeSlot &t, int64_t np, cudaStream_t st);
+cudaError_t launch_recompute(const StepArgs &a, FieldKind kind, const TapeSlot &t,
+                             double *states, int len, int64_t np, cudaStream_t st);
+cudaError_t launch_lam_permute(const uint32_t *id, const double *src, double *dst, int64_t np,
+                               int to_storage, int *status, cudaStream_t st);
+cudaError_t launch_adjoint(const StepArgs &a, FieldKind kind, const double *state,
+                           const double *tau, double *lam, double *gU, int64_t np,
+                           cudaStream_t st);
+
 // Radix engine: stable sort of (key, payload) pairs over segmented tiles.
 struct SortArgs {
   int nseg;             // segments (the sort is stable within each)

@@ -1,0 +1,291 @@
+// Per-particle arithmetic of the step, shared by the fused step kernel and
+// by the adjoint's recompute (which must reproduce the forward bit for bit):
+// trilinear interpolation from cell-centre values (Sec. 2.2) and one Heun
+// step of Eqs. (5)-(6) with f = 1, gravity and the periodic wrap (Sec. 2.1),
+// in FP64 (interp64 / heun_step64) or in float-float (interp_df, interp_lo,
+// heun_step_df).
+#pragma once
+
+#include "lcs_df.cuh"
+#include "lcs_internal.cuh"
+
+namespace lcs {
+
+// ---------------------------------------------------------------- interpolation
+
+struct Stencil {
+  uint32_t c[8];   // corner cell indices, order (a, b, d) = x outer, z inner
+  double w[8];     // FP64 weights wx[a] * wy[b] * wz[d]
+};
+
+// Cell-centre stencil of the trilinear interpolation (Sec. 2.2):
+// s = x N/L - 1/2, i0 = floor(s), t = s - i0, corners i0, i0+1 mod N.
+__device__ __forceinline__ void axis64(double x, double inv_dx, int N, int &i0, double &t) {
+  const double s = x * inv_dx - 0.5;
+  const double f = floor(s);
+  t = s - f;
+  i0 = wrap_cell((int)f, N);
+}
+
+__device__ __forceinline__ void stencil64(const Geom &g, double x, double y, double z,
+                                          Stencil &S) {
+  const int N = g.N;
+  int i0, j0, k0;
+  double tx, ty, tz;
+  axis64(x, g.inv_dx, N, i0, tx);
+  axis64(y, g.inv_dx, N, j0, ty);
+  axis64(z, g.inv_dx, N, k0, tz);
+  const int i1 = i0 + 1 == N ? 0 : i0 + 1, j1 = j0 + 1 == N ? 0 : j0 + 1,
+            k1 = k0 + 1 == N ? 0 : k0 + 1;
+  const double wx[2] = {1.0 - tx, tx}, wy[2] = {1.0 - ty, ty}, wz[2] = {1.0 - tz, tz};
+  const uint32_t ii[2] = {(uint32_t)i0, (uint32_t)i1};
+  const uint32_t jj[2] = {(uint32_t)j0 * N, (uint32_t)j1 * N};
+  const uint32_t kk[2] = {(uint32_t)k0 * N * N, (uint32_t)k1 * N * N};
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        const int q = a * 4 + b * 2 + d;
+        S.c[q] = ii[a] + jj[b] + kk[d];
+        S.w[q] = wx[a] * wy[b] * wz[d];
+      }
+}
+
+// FP64 trilinear interpolation of the FP64 field (all arithmetic on the FP64
+// pipe; the reference form of the step, LCS_KERNEL_FP64).
+__device__ __forceinline__ void interp64(const void *field, const Geom &g, double x, double y,
+                                         double z, double &u, double &v, double &w) {
+  Stencil S;
+  stencil64(g, x, y, z, S);
+  const double2 *f = (const double2 *)field;
+  double au = 0.0, av = 0.0, aw = 0.0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const double2 p = __ldg(f + 2 * (size_t)S.c[q]);
+    const double2 r = __ldg(f + 2 * (size_t)S.c[q] + 1);
+    au = fma(S.w[q], p.x, au);
+    av = fma(S.w[q], p.y, av);
+    aw = fma(S.w[q], r.x, aw);
+  }
+  u = au, v = av, w = aw;
+}
+
+// Fixed-point (52 fraction bits) coordinate x N/L of the first stage: one
+// correctly rounded FP64 product, then bit operations.
+__device__ __forceinline__ long long fix_stage1(double x, double inv_dx) {
+  return d_to_fix52(__dmul_rn(x, inv_dx));
+}
+
+// Coordinate of the predictor X* = X + dt V: q1 + (dt N/L) V in fixed point.
+__device__ __forceinline__ long long fix_stage2(long long q1, df V, df cx) {
+  const df cv = df_mul(cx, V);
+  return q1 + f_to_fix52(cv.h) + f_to_fix52(cv.l);
+}
+
+// Predictor position of the FP64 step.
+__device__ __forceinline__ double predictor64(double x, double v, double dt) { return x + dt * v; }
+
+// ---------------------------------------------------------------- DF interpolation
+
+// Product of two float pairs without renormalisation: (p, e) with
+// p = RN(a.h b.h) and e = the exact rounding error plus the cross terms.
+__device__ __forceinline__ df mul_un(df a, df b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  return {p, e};
+}
+
+// Trilinear interpolation (Sec. 2.2) in float-float arithmetic from the
+// fixed-point coordinates q[s] = x_s N/L * 2^52.  The field record of a
+// cell holds the float pairs of u, v, w: (hu, hv, hw, lu) (lv, lw, -, -).
+// Corner weights are float-float products of the per-axis weights; each
+// weight-times-value product is split exactly (fma error), the high parts
+// are summed with two_sum and every small term goes to a compensation sum.
+__device__ __forceinline__ void interp_df(const float4 *__restrict__ f, int N,
+                                          const long long q[3], df U[3]) {
+  const Axis ax = axis_from_fix(q[0]), ay = axis_from_fix(q[1]), az = axis_from_fix(q[2]);
+  const int i0 = wrap_cell(ax.i0, N), j0 = wrap_cell(ay.i0, N), k0 = wrap_cell(az.i0, N);
+  const int i1 = i0 + 1 == N ? 0 : i0 + 1, j1 = j0 + 1 == N ? 0 : j0 + 1,
+            k1 = k0 + 1 == N ? 0 : k0 + 1;
+  const df wx[2] = {{__fsub_rn(1.0f, ax.th), -ax.tl}, {ax.th, ax.tl}};
+  const df wy[2] = {{__fsub_rn(1.0f, ay.th), -ay.tl}, {ay.th, ay.tl}};
+  const df wz[2] = {{__fsub_rn(1.0f, az.th), -az.tl}, {az.th, az.tl}};
+  const uint32_t ii[2] = {(uint32_t)i0, (uint32_t)i1};
+  const uint32_t jj[2] = {(uint32_t)j0 * N, (uint32_t)j1 * N};
+  const uint32_t kk[2] = {(uint32_t)k0 * N * N, (uint32_t)k1 * N * N};
+  float s[3], c[3];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const df wab = mul_un(wx[a], wy[b]);
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        const df w = mul_un(wab, wz[d]);
+        const size_t cell = (size_t)(ii[a] + jj[b] + kk[d]);
+        const float4 A = __ldg(f + 2 * cell), B = __ldg(f + 2 * cell + 1);
+        const float hv[3] = {A.x, A.y, A.z}, lv[3] = {A.w, B.x, B.y};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float P = __fmul_rn(w.h, hv[k]);
+          const float E = __fmaf_rn(w.h, hv[k], -P);
+          float t;
+          if (a == 0 && b == 0 && d == 0) {
+            s[k] = P;
+            t = E;
+          } else {
+            const df st = two_sum(s[k], P);
+            s[k] = st.h;
+            t = __fadd_rn(st.l, E);
+          }
+          float small = __fmaf_rn(w.h, lv[k], t);
+          small = __fmaf_rn(w.l, hv[k], small);
+          c[k] = (a == 0 && b == 0 && d == 0) ? small : __fadd_rn(c[k], small);
+        }
+      }
+    }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) U[k] = fast_two_sum(s[k], c[k]);
+}
+
+// Trilinear interpolation (Sec. 2.2) for FP32 / BF16 field storage: weights
+// from the fixed-point coordinates rounded to FP32, FP32 accumulation.
+template <int KIND>
+__device__ __forceinline__ void interp_lo(const void *__restrict__ field, int N,
+                                          const long long q[3], df U[3]) {
+  const Axis ax = axis_from_fix(q[0]), ay = axis_from_fix(q[1]), az = axis_from_fix(q[2]);
+  const int i0 = wrap_cell(ax.i0, N), j0 = wrap_cell(ay.i0, N), k0 = wrap_cell(az.i0, N);
+  const int i1 = i0 + 1 == N ? 0 : i0 + 1, j1 = j0 + 1 == N ? 0 : j0 + 1,
+            k1 = k0 + 1 == N ? 0 : k0 + 1;
+  const float tx = __fadd_rn(ax.th, ax.tl), ty = __fadd_rn(ay.th, ay.tl),
+              tz = __fadd_rn(az.th, az.tl);
+  const float wx[2] = {__fsub_rn(1.0f, tx), tx}, wy[2] = {__fsub_rn(1.0f, ty), ty},
+              wz[2] = {__fsub_rn(1.0f, tz), tz};
+  const uint32_t ii[2] = {(uint32_t)i0, (uint32_t)i1};
+  const uint32_t jj[2] = {(uint32_t)j0 * N, (uint32_t)j1 * N};
+  const uint32_t kk[2] = {(uint32_t)k0 * N * N, (uint32_t)k1 * N * N};
+  float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const float wab = __fmul_rn(wx[a], wy[b]);
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        const float w = __fmul_rn(wab, wz[d]);
+        const uint32_t cell = ii[a] + jj[b] + kk[d];
+        float f[3];
+        if (KIND == FK_F32) {
+          const float4 p = __ldg((const float4 *)field + cell);
+          f[0] = p.x, f[1] = p.y, f[2] = p.z;
+        } else {
+          const uint2 p = __ldg((const uint2 *)field + cell);
+          f[0] = __uint_as_float((p.x & 0xffffu) << 16);
+          f[1] = __uint_as_float(p.x & 0xffff0000u);
+          f[2] = __uint_as_float((p.y & 0xffffu) << 16);
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) acc[k] = __fmaf_rn(w, f[k], acc[k]);
+      }
+    }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) U[k] = {acc[k], 0.f};
+}
+
+template <int KIND>
+__device__ __forceinline__ void interp_any(const void *field, int N, const long long q[3],
+                                           df U[3]) {
+  if (KIND == FK_DF) interp_df((const float4 *)field, N, q, U);
+  else interp_lo<KIND>(field, N, q, U);
+}
+
+// Heun step of Eqs. (5)-(6) (f = 1, gravity g) with float-float increments:
+//   h = dt/tau, D1 = U(X) - V, V* = V + h D1 + dt g, X* = X + dt V,
+//   D2 = U(X*) - V*, dV = (h D1 + h D2)/2 + dt g,
+//   dX = dt V + (dt/2)(h D1 + dt g)          [= dt (V + V*)/2]
+// then X' = X + dX and V' = V + dV in FP64, and the periodic wrap.
+template <int KIND>
+__device__ __forceinline__ void heun_step_df(const StepArgs &a, double x[3], double v[3],
+                                             double tau, int img[3], int &bad) {
+  const Geom &g = a.geo;
+  const df dt = {a.dfk[0], a.dfk[1]}, hdt = {a.dfk[2], a.dfk[3]}, cx = {a.dfk[4], a.dfk[5]};
+  const df h = df_mul(dt, df_recip(split_d(tau)));
+  long long q[3];
+  df V[3], U[3], hD1[3], Vs[3];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) q[s] = fix_stage1(x[s], g.inv_dx);
+  interp_any<KIND>(a.field, g.N, q, U);
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const df gd = {a.dfk[6 + 2 * s], a.dfk[7 + 2 * s]};
+    V[s] = split_d(v[s]);
+    hD1[s] = df_mul(h, df_add(U[s], df_neg(V[s])));
+    Vs[s] = df_add(df_add(V[s], hD1[s]), gd);
+    q[s] = fix_stage2(q[s], V[s], cx);
+  }
+  interp_any<KIND>(a.field, g.N, q, U);
+  const long long bitsL = __double_as_longlong(g.L);
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const df gd = {a.dfk[6 + 2 * s], a.dfk[7 + 2 * s]};
+    const df hD2 = df_mul(h, df_add(U[s], df_neg(Vs[s])));
+    const df dV = df_add(df_scale2(df_add(hD1[s], hD2), 0.5f), gd);
+    const df dX = df_add(df_mul(dt, V[s]), df_mul(hdt, df_add(hD1[s], gd)));
+    if (!(fabsf(dX.h) < (float)(0.5 * g.L))) bad |= 2;
+    double xn = __dadd_rn(x[s], df_to_double(dX));
+    const double vn = __dadd_rn(v[s], df_to_double(dV));
+    const long long bx = __double_as_longlong(xn);
+    if (((bx >> 52) & 0x7ff) == 0x7ff || ((__double_as_longlong(vn) >> 52) & 0x7ff) == 0x7ff)
+      bad |= 1;
+    if (bx < 0) {
+      xn = __dadd_rn(xn, g.L);
+      img[s] -= 1;
+    } else if (bx >= bitsL) {
+      xn = __dsub_rn(xn, g.L);
+      img[s] += 1;
+    }
+    if (__double_as_longlong(xn) == bitsL) xn = 0.0;
+    x[s] = xn;
+    v[s] = vn;
+  }
+}
+
+// One Heun step of Eqs. (5)-(6) (f = 1, gravity g) with periodic wrap, in FP64.
+__device__ __forceinline__ void heun_step64(const StepArgs &a, double x[3], double v[3],
+                                          double tau, int img[3], int &bad) {
+  const Geom &g = a.geo;
+  const double itau = 1.0 / tau;
+  double u1[3], a1[3], xs[3], vs[3], u2[3];
+  interp64(a.field, g, x[0], x[1], x[2], u1[0], u1[1], u1[2]);
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    a1[s] = (u1[s] - v[s]) * itau + a.g[s];
+    xs[s] = predictor64(x[s], v[s], a.dt);
+    vs[s] = v[s] + a.dt * a1[s];
+  }
+  interp64(a.field, g, xs[0], xs[1], xs[2], u2[0], u2[1], u2[2]);
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const double a2 = (u2[s] - vs[s]) * itau + a.g[s];
+    double xn = x[s] + a.half_dt * (v[s] + vs[s]);
+    const double vn = v[s] + a.half_dt * (a1[s] + a2);
+    if (!(fabs(xn - x[s]) < 0.5 * g.L)) bad |= fabs(xn) <= 1e300 ? 2 : 1;
+    if (!isfinite(vn)) bad |= 1;
+    if (xn >= g.L) {
+      xn -= g.L;
+      img[s] += 1;
+    } else if (xn < 0.0) {
+      xn += g.L;
+      img[s] -= 1;
+    }
+    if (xn == g.L) xn = 0.0;
+    x[s] = xn;
+    v[s] = vn;
+  }
+}
+
+}  // namespace lcs

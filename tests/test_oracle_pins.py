@@ -374,9 +374,12 @@ def fd_grad_check(field, x0, v0, tau, dt, steps, target, seed):
         xp, ip, hp = run(x0 + h * dxx, v0 + h * dvv, field + h * dff)
         xm, im, hm = run(x0 - h * dxx, v0 - h * dvv, field - h * dff)
         mask = ((hp == h0) & (hm == h0)).astype(np.float64)
-        lp = oracle.loss(L, xp, ip, target, mask)
-        lm = oracle.loss(L, xm, im, target, mask)
-        fd = (lp - lm) / (2 * h)
+        # [L(+h) - L(-h)] / 2h subtracted term by term ((a-t)^2 - (b-t)^2 =
+        # (a-b)(a+b-2t)) so that the summation rounding of L does not enter
+        up, um = xp + L * ip, xm + L * im
+        fd = float(np.sum(mask * ((up - um) * (up + um - 2 * target)).sum(0)) / n) / (2 * h)
+        assert abs(fd - (oracle.loss(L, xp, ip, target, mask)
+                         - oracle.loss(L, xm, im, target, mask)) / (2 * h)) < 1e-6 * abs(fd)
         # adjoint restricted to the same particles: rerun with masked seed
         lxm = lx * mask[None, :]
         gxm, gvm, gfm = oracle.adjoint(field, L, x0, v0, tau, 0.1, dt, gvec, steps, lxm,
