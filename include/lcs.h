@@ -96,7 +96,8 @@ typedef struct {
   int ckpt_every;         /* > 0: tape checkpoints every k steps for lcs_backward */
 } lcs_desc;
 
-/* Create a context for n_ens ensembles (n_ens >= 1) working on `stream`
+/* Create a context for n_ens ensembles (1 <= n_ens <= 1024, all with the same
+ * field_dtype and field_kernel) working on `stream`
  * (a cudaStream_t, may be NULL for the legacy default stream).  Copies the
  * particles into library-owned device memory, converts the field into the
  * library's layout and precision, and places every particle in the segment
@@ -110,8 +111,9 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
  * interpolate, integrate (Heun) and wrap every particle, flag it by
  * destination subdomain, and migrate (prefix scan, pack, unpack); after
  * steps whose 1-based count is a multiple of sort_every, sort every
- * subdomain's particles stably by cell.  The step loop is recorded once in
- * a CUDA graph and replayed. */
+ * subdomain's particles stably by cell.  All ensembles run in the same four
+ * persistent kernel launches per step (their tiles share one work counter),
+ * recorded once in a CUDA graph and replayed. */
 lcs_status lcs_step(lcs_ctx *ctx, int64_t nsteps);
 
 /* Standalone migration pass on the current state (asynchronous): a stable
@@ -177,10 +179,20 @@ enum {
  * number of launches.  The particle state advances exactly as lcs_step. */
 lcs_status lcs_profile_steps(lcs_ctx *ctx, int64_t nsteps, double *ms, int64_t *count);
 
+/* Autotuner: time every step-kernel configuration (threads per block x
+ * particles per thread, i.e. the scan tile) on steps_per_trial real steps of
+ * all ensembles, keep the fastest, and rebuild the step graphs with it.
+ * The trial steps advance the simulation (3 * steps_per_trial steps in
+ * all, recorded like any other step); results do not depend on the choice.
+ * *block and *items (may be NULL) receive the configuration.  Synchronising. */
+lcs_status lcs_tune(lcs_ctx *ctx, int steps_per_trial, int *block, int *items);
+
 /* Wait for all enqueued work; return the latched device status. */
 lcs_status lcs_sync(lcs_ctx *ctx);
 
-/* Human-readable description of the last error of ctx (never NULL). */
+/* Human-readable description of the last error of ctx (never NULL); with
+ * ctx == NULL, the last error of this thread's most recent failed call,
+ * e.g. the reason lcs_init refused its arguments. */
 const char *lcs_last_error(lcs_ctx *ctx);
 
 /* Release every resource of ctx (NULL is ignored). */

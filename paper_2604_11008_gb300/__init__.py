@@ -33,7 +33,8 @@ KERNELS = {"auto": 0, "fp64": 1, "df": 2}
 # Every symbol declared in include/lcs.h.
 EXPORTS = ("lcs_init", "lcs_step", "lcs_migrate", "lcs_sort", "lcs_set_state", "lcs_get_state",
            "lcs_get_field", "lcs_backward", "lcs_sync", "lcs_last_error", "lcs_destroy",
-           "lcs_launch_count", "lcs_partition", "lcs_profile_steps", "lcs_partition_noalloc")
+           "lcs_launch_count", "lcs_partition", "lcs_profile_steps", "lcs_partition_noalloc",
+           "lcs_tune")
 PARTITION_NOALLOC_MAX_N = 1 << 20
 PROF_CLASSES = ("step", "finish", "unpack", "flip", "sort")
 
@@ -83,9 +84,10 @@ def lib():
         L.lcs_partition.argtypes = [P, i64, i32, P, P, P, P]
         L.lcs_profile_steps.argtypes = [P, i64, P, P]
         L.lcs_partition_noalloc.argtypes = [P, i64, i32, P, P, P, P]
+        L.lcs_tune.argtypes = [P, i32, P, P]
         for name in ("lcs_init", "lcs_step", "lcs_migrate", "lcs_sort", "lcs_set_state",
                      "lcs_get_state", "lcs_get_field", "lcs_backward", "lcs_sync",
-                     "lcs_partition", "lcs_profile_steps", "lcs_partition_noalloc"):
+                     "lcs_partition", "lcs_profile_steps", "lcs_partition_noalloc", "lcs_tune"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -162,7 +164,7 @@ class Simulator:
         st = lib().lcs_init(descs, len(specs), _stream(stream), C.byref(self._ctx))
         self._keep = []  # inputs are read during lcs_init only
         if st != LCS_OK:
-            raise LcsError(st, "lcs_init failed")
+            raise LcsError(st, "lcs_init: " + lib().lcs_last_error(None).decode())
 
     # -- helpers
     def _check(self, st):
@@ -208,6 +210,12 @@ class Simulator:
         cnt = np.zeros(len(PROF_CLASSES), dtype=np.int64)
         self._check(lib().lcs_profile_steps(self._ctx, int(nsteps), _ptr(ms), _ptr(cnt)))
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(PROF_CLASSES)}
+
+    def tune(self, steps_per_trial: int = 2):
+        """Autotune the step kernel (advances the simulation); returns (block, items)."""
+        b, it = C.c_int(), C.c_int()
+        self._check(lib().lcs_tune(self._ctx, int(steps_per_trial), C.byref(b), C.byref(it)))
+        return b.value, it.value
 
     @property
     def launches(self) -> int:

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -65,18 +66,34 @@ struct lcs_ctx {
   int failed = 0;  // latched host-side status (LCS_ERR_*)
   std::string err;
   std::vector<void *> allocs;
-  cudaGraphExec_t g_step = nullptr, g_sort = nullptr;
+  // captured step graphs, keyed by which ensembles sort after that step
+  std::map<std::vector<bool>, cudaGraphExec_t> graphs;
   int64_t launches = 0;
   int sms = 152;
+  // batched step over all ensembles (one launch per kernel per step)
+  FieldKind kind = FK_F64;
+  int block = 256, items = 2;   // step tile = block * items (autotuned)
+  int step_grid = 1, total_P = 0;
+  int64_t total_tiles = 0;      // sum of the ensembles' look-back array sizes
+  unsigned long long *tile_status = nullptr;
+  BatchArgs bt{};
+  StepArgs *d_args = nullptr;
+  int *d_ens_P_off = nullptr;
+  unsigned *d_counter = nullptr;           // one tile counter per step group
+  std::vector<std::pair<int, int>> groups;  // (first ensemble, count), count <= GROUP_ENS
+  std::vector<int64_t> group_tiles;         // look-back array size of each group
 };
 
 namespace {
+
+thread_local std::string g_last_init_error = "no error";
 
 lcs_status fail(lcs_ctx *c, lcs_status s, const std::string &msg) {
   if (c) {
     if (!c->failed) c->failed = s;
     c->err = msg;
   }
+  g_last_init_error = msg;
   return s;
 }
 
@@ -151,13 +168,41 @@ lcs_status enqueue_sort(lcs_ctx *c, Ens &e, cudaStream_t st) {
   return LCS_OK;
 }
 
-lcs_status enqueue_step(lcs_ctx *c, Ens &e, cudaStream_t st) {
-  CK(cudaMemsetAsync(e.a.m.tile_status, 0, sizeof(unsigned long long) * e.max_tiles, st));
-  CK(launch_step(e.a, e.kind, e.step_grid, st));
-  CK(launch_finish(e.a, st));
-  CK(launch_unpack(e.a, st));
-  CK(launch_flip(e.a, st));
-  c->launches += 4;
+// The step kernel of every group of ensembles (one launch per 52 ensembles).
+lcs_status launch_steps(lcs_ctx *c, cudaStream_t st) {
+  static thread_local StepGroup<GROUP_ENS> big;
+  for (size_t gi = 0; gi < c->groups.size(); ++gi) {
+    const int first = c->groups[gi].first, cnt = c->groups[gi].second;
+    const int occ = std::max(1, step_kernel_occupancy(c->kind, c->block, c->items));
+    const int grid = (int)std::max<int64_t>(
+        1, std::min<int64_t>(c->group_tiles[gi], (int64_t)occ * c->sms));
+    if (cnt == 1) {
+      StepGroup<1> one;
+      one.a[0] = c->ens[first].a;
+      one.n = 1;
+      one.counter = c->d_counter + gi;
+      CK(launch_step_group<1>(one, c->kind, c->block, c->items, grid, st));
+    } else {
+      for (int k = 0; k < cnt; ++k) big.a[k] = c->ens[first + k].a;
+      big.n = cnt;
+      big.counter = c->d_counter + gi;
+      CK(launch_step_group<GROUP_ENS>(big, c->kind, c->block, c->items, grid, st));
+    }
+    c->launches += 1;
+  }
+  return LCS_OK;
+}
+
+// One step of every ensemble: 1 memset + (step groups + 3) launches, whatever
+// the number of ensembles (one step group per 52 ensembles).
+lcs_status enqueue_step(lcs_ctx *c, cudaStream_t st) {
+  CK(cudaMemsetAsync(c->tile_status, 0, sizeof(unsigned long long) * c->total_tiles, st));
+  lcs_status rs = launch_steps(c, st);
+  if (rs != LCS_OK) return rs;
+  CK(launch_finish(c->bt, st));
+  CK(launch_unpack(c->bt, c->total_P, st));
+  CK(launch_flip(c->bt, st));
+  c->launches += 3;
   return LCS_OK;
 }
 
@@ -173,7 +218,7 @@ struct Prof {
   }
 };
 
-lcs_status enqueue_step_profiled(lcs_ctx *c, Ens &e, bool sort_now, Prof &pf) {
+lcs_status enqueue_step_profiled(lcs_ctx *c, const std::vector<bool> &sorts, Prof &pf) {
   cudaStream_t st = c->st;
   auto mark = [&](int cls) {
     cudaEvent_t e0 = pf.get();
@@ -181,34 +226,41 @@ lcs_status enqueue_step_profiled(lcs_ctx *c, Ens &e, bool sort_now, Prof &pf) {
     pf.cls.push_back(cls);
   };
   mark(LCS_PROF_FLIP);
-  CK(cudaMemsetAsync(e.a.m.tile_status, 0, sizeof(unsigned long long) * e.max_tiles, st));
+  CK(cudaMemsetAsync(c->tile_status, 0, sizeof(unsigned long long) * c->total_tiles, st));
   mark(LCS_PROF_STEP);
-  CK(launch_step(e.a, e.kind, e.step_grid, st));
+  lcs_status rs = launch_steps(c, st);
+  if (rs != LCS_OK) return rs;
   mark(LCS_PROF_FINISH);
-  CK(launch_finish(e.a, st));
+  CK(launch_finish(c->bt, st));
   mark(LCS_PROF_UNPACK);
-  CK(launch_unpack(e.a, st));
+  CK(launch_unpack(c->bt, c->total_P, st));
   mark(LCS_PROF_FLIP);
-  CK(launch_flip(e.a, st));
-  c->launches += 4;
-  if (sort_now && e.d.sort_every > 0) {
+  CK(launch_flip(c->bt, st));
+  c->launches += 3;
+  bool any = false;
+  for (bool b : sorts) any |= b;
+  if (any) {
     mark(LCS_PROF_SORT);
-    lcs_status r = enqueue_sort(c, e, st);
-    if (r != LCS_OK) return r;
+    for (size_t k = 0; k < c->ens.size(); ++k) {
+      if (!sorts[k]) continue;
+      lcs_status r = enqueue_sort(c, c->ens[k], st);
+      if (r != LCS_OK) return r;
+    }
   }
   mark(-1);
   return LCS_OK;
 }
 
-lcs_status capture(lcs_ctx *c, bool with_sort, cudaGraphExec_t *out) {
+// Record one step of every ensemble, followed by the cell sort of the
+// ensembles flagged in `sorts`, as a CUDA graph.
+lcs_status capture(lcs_ctx *c, const std::vector<bool> &sorts, cudaGraphExec_t *out) {
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(c->cap_st, cudaStreamCaptureModeThreadLocal));
   lcs_status r = LCS_OK;
   const int64_t l0 = c->launches;
-  for (auto &e : c->ens) {
-    if (r == LCS_OK) r = enqueue_step(c, e, c->cap_st);
-    if (r == LCS_OK && with_sort && e.d.sort_every > 0) r = enqueue_sort(c, e, c->cap_st);
-  }
+  r = enqueue_step(c, c->cap_st);
+  for (size_t k = 0; k < c->ens.size(); ++k)
+    if (r == LCS_OK && sorts[k]) r = enqueue_sort(c, c->ens[k], c->cap_st);
   c->launches = l0;  // counted again at each replay
   cudaError_t ee = cudaStreamEndCapture(c->cap_st, &g);
   if (r != LCS_OK) {
@@ -222,11 +274,26 @@ lcs_status capture(lcs_ctx *c, bool with_sort, cudaGraphExec_t *out) {
   return LCS_OK;
 }
 
-int64_t launches_per_step(lcs_ctx *c, bool with_sort) {
-  int64_t n = 0;
-  for (auto &e : c->ens) {
-    n += 4;
-    if (with_sort && e.d.sort_every > 0) {
+// Which ensembles sort after step number `next` (1-based).
+std::vector<bool> sort_set(lcs_ctx *c, int64_t next) {
+  std::vector<bool> s(c->ens.size());
+  for (size_t k = 0; k < c->ens.size(); ++k) {
+    const int se = c->ens[k].d.sort_every;
+    s[k] = se > 0 && next % se == 0;
+  }
+  return s;
+}
+
+void drop_graphs(lcs_ctx *c) {
+  for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+}
+
+int64_t launches_per_step(lcs_ctx *c, const std::vector<bool> &sorts) {
+  int64_t n = 3 + (int64_t)c->groups.size();
+  for (size_t k = 0; k < c->ens.size(); ++k) {
+    const Ens &e = c->ens[k];
+    if (sorts[k]) {
       const int passes = e.key_bits ? (e.key_bits + SORT_MAX_BITS - 1) / SORT_MAX_BITS : 0;
       n += 4 + 5 * passes;
     }
@@ -270,6 +337,70 @@ lcs_status read_status(lcs_ctx *c) {
                 std::string("device reported: ") + names[dev_status < 9 ? dev_status : 0]);
   }
   return LCS_OK;
+}
+
+// Copy every ensemble's StepArgs to the device array the batched kernels read.
+lcs_status upload_args(lcs_ctx *c) {
+  std::vector<StepArgs> h(c->ens.size());
+  for (size_t k = 0; k < c->ens.size(); ++k) h[k] = c->ens[k].a;
+  CK(cudaMemcpyAsync(c->d_args, h.data(), sizeof(StepArgs) * h.size(), cudaMemcpyHostToDevice,
+                     c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return LCS_OK;
+}
+
+// Step-tile tables of every ensemble for the current tile size.
+lcs_status retile(lcs_ctx *c) {
+  for (auto &e : c->ens) {
+    e.a.step_tile = c->block * c->items;
+    k_relayout<<<1, 1024, 0, c->st>>>(e.a, 0);
+    c->launches += 1;
+  }
+  CK(cudaGetLastError());
+  return upload_args(c);
+}
+
+// The batched view of the ensembles: one look-back status array, one tile
+// counter, the device copy of every ensemble's arguments.
+lcs_status setup_batch(lcs_ctx *c) {
+  const int n = (int)c->ens.size();
+  if (n > MAX_ENS) return fail(c, LCS_ERR_ARG, "too many ensembles in one context");
+  c->kind = c->ens[0].kind;
+  for (auto &e : c->ens)
+    if (e.kind != c->kind)
+      return fail(c, LCS_ERR_ARG, "all ensembles of a context need the same field storage");
+  c->total_tiles = 0;
+  c->total_P = 0;
+  std::vector<int> poff(n + 1, 0);
+  for (int k = 0; k < n; ++k) {
+    c->total_tiles += c->ens[k].max_tiles;
+    poff[k + 1] = poff[k] + c->ens[k].a.geo.Ptot;
+  }
+  c->total_P = poff[n];
+  CK(dalloc(c, &c->tile_status, c->total_tiles));
+  int64_t off = 0;
+  for (auto &e : c->ens) {
+    e.a.m.tile_status = c->tile_status + off;
+    off += e.max_tiles;
+  }
+  c->groups.clear();
+  c->group_tiles.clear();
+  for (int k = 0; k < n; k += GROUP_ENS) {
+    const int cnt = std::min(GROUP_ENS, n - k);
+    c->groups.emplace_back(k, cnt);
+    int64_t t = 0;
+    for (int j = k; j < k + cnt; ++j) t += c->ens[j].max_tiles;
+    c->group_tiles.push_back(t);
+  }
+  const int ng = (int)c->groups.size();
+  CK(dalloc(c, &c->d_args, n));
+  CK(dalloc(c, &c->d_ens_P_off, n + 1));
+  CK(dalloc(c, &c->d_counter, ng));
+  CK(cudaMemcpyAsync(c->d_ens_P_off, poff.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice,
+                     c->st));
+  CK(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned) * ng, c->st));
+  c->bt = BatchArgs{c->d_args, n, c->d_ens_P_off, c->d_counter, ng};
+  return retile(c);
 }
 
 }  // namespace
@@ -336,7 +467,8 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
     }
     e.key_bits = ceil_log2(space);
     e.mig_bits = std::max(1, ceil_log2(2 * (int64_t)P));
-    e.max_tiles = (int)(e.np / STEP_TILE + P + 2);
+    e.max_tiles = (int)(e.np / 256 + P + 2);  // 256 = smallest step tile of any config
+    e.a.step_tile = c->block * c->items;
     e.max_stiles = (int)(e.np / SORT_TILE + P + 2);
     e.a.dt = d.dt;
     e.a.half_dt = 0.5 * d.dt;
@@ -376,7 +508,6 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
     A(dalloc(c, &m.stile_off, P + 1));
     A(dalloc(c, &m.phase, 1));
     A(dalloc(c, &m.status, 1));
-    A(dalloc(c, &m.tile_status, e.max_tiles));
     A(dalloc(c, &m.tile_counter, 1));
     A(dalloc(c, &m.bincnt, (int64_t)P * NBIN));
     A(dalloc(c, &m.off_in, (int64_t)P * NBIN));
@@ -440,8 +571,6 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
       r = tape_store(c, e, 0);
       e.tape_ok = true;
     }
-    int occ = step_kernel_occupancy(e.kind);
-    e.step_grid = std::max(1, std::min(e.max_tiles, std::max(1, occ) * c->sms));
     if (r == LCS_OK) {
       // tau >= dt and finite tau are checked on the host copy
       if (d.tau && e.np > 0) {
@@ -452,8 +581,9 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
             r = fail(c, LCS_ERR_ARG, "tau_p must be finite and >= dt");
       }
     }
-    if (r == LCS_OK) r = read_status(c);
   }
+  if (r == LCS_OK) r = read_status(c);
+  if (r == LCS_OK) r = setup_batch(c);
   if (r != LCS_OK) {
     const lcs_status rr = r;
     lcs_destroy(c);
@@ -468,24 +598,18 @@ lcs_status lcs_step(lcs_ctx *c, int64_t nsteps) {
   if (r != LCS_OK) return r;
   if (nsteps < 0) return fail(c, LCS_ERR_ARG, "nsteps < 0");
   if (nsteps == 0) return LCS_OK;
-  if (!c->g_step) {
-    r = capture(c, false, &c->g_step);
-    if (r != LCS_OK) return r;
-  }
-  bool any_sort = false;
-  for (auto &e : c->ens) any_sort |= e.d.sort_every > 0;
-  if (any_sort && !c->g_sort) {
-    r = capture(c, true, &c->g_sort);
-    if (r != LCS_OK) return r;
-  }
   for (int64_t k = 0; k < nsteps; ++k) {
-    // all ensembles of a context share the step count; the sort graph is
-    // used when one of them sorts after this step
-    const int64_t next = c->ens[0].steps + 1;
-    bool sort_now = false;
-    for (auto &e : c->ens) sort_now |= e.d.sort_every > 0 && next % e.d.sort_every == 0;
-    CK(cudaGraphLaunch(sort_now ? c->g_sort : c->g_step, c->st));
-    c->launches += launches_per_step(c, sort_now);
+    // all ensembles of a context share the step count
+    const std::vector<bool> sorts = sort_set(c, c->ens[0].steps + 1);
+    auto it = c->graphs.find(sorts);
+    if (it == c->graphs.end()) {
+      cudaGraphExec_t ge = nullptr;
+      r = capture(c, sorts, &ge);
+      if (r != LCS_OK) return r;
+      it = c->graphs.emplace(sorts, ge).first;
+    }
+    CK(cudaGraphLaunch(it->second, c->st));
+    c->launches += launches_per_step(c, sorts);
     for (auto &e : c->ens) {
       ++e.steps;
       if (e.d.ckpt_every > 0 && e.steps % e.d.ckpt_every == 0) {
@@ -672,12 +796,10 @@ lcs_status lcs_profile_steps(lcs_ctx *c, int64_t nsteps, double *ms, int64_t *co
     if (count) count[k] = 0;
   }
   for (int64_t k = 0; k < nsteps; ++k) {
-    const int64_t next = c->ens[0].steps + 1;
-    bool sort_now = false;
-    for (auto &e : c->ens) sort_now |= e.d.sort_every > 0 && next % e.d.sort_every == 0;
-    for (auto &e : c->ens) {
+    const std::vector<bool> sorts = sort_set(c, c->ens[0].steps + 1);
+    {
       Prof pf;
-      r = enqueue_step_profiled(c, e, sort_now, pf);
+      r = enqueue_step_profiled(c, sorts, pf);
       if (r == LCS_OK) {
         CK(cudaStreamSynchronize(c->st));
         for (size_t i = 0; i + 1 < pf.ev.size(); ++i) {
@@ -704,6 +826,37 @@ lcs_status lcs_profile_steps(lcs_ctx *c, int64_t nsteps, double *ms, int64_t *co
   return read_status(c);
 }
 
+lcs_status lcs_tune(lcs_ctx *c, int steps_per_trial, int *block, int *items) {
+  lcs_status r = check_ctx(c);
+  if (r != LCS_OK) return r;
+  if (steps_per_trial < 1) return fail(c, LCS_ERR_ARG, "lcs_tune: steps_per_trial < 1");
+  static const int cfg[][2] = {{256, 2}, {256, 1}, {128, 2}};
+  double best = 1e300;
+  int bi = 0;
+  for (int k = 0; k < 3; ++k) {
+    c->block = cfg[k][0];
+    c->items = cfg[k][1];
+    r = retile(c);
+    if (r != LCS_OK) return r;
+    double ms[LCS_PROF_N];
+    r = lcs_profile_steps(c, steps_per_trial, ms, nullptr);
+    if (r != LCS_OK) return r;
+    if (ms[LCS_PROF_STEP] < best) {
+      best = ms[LCS_PROF_STEP];
+      bi = k;
+    }
+  }
+  c->block = cfg[bi][0];
+  c->items = cfg[bi][1];
+  r = retile(c);
+  if (r != LCS_OK) return r;
+  // graphs recorded with the old configuration are rebuilt on the next lcs_step
+  drop_graphs(c);
+  if (block) *block = c->block;
+  if (items) *items = c->items;
+  return LCS_OK;
+}
+
 lcs_status lcs_sync(lcs_ctx *c) {
   lcs_status r = check_ctx(c);
   if (r != LCS_OK) return r;
@@ -712,7 +865,7 @@ lcs_status lcs_sync(lcs_ctx *c) {
 }
 
 const char *lcs_last_error(lcs_ctx *c) {
-  if (!c) return "null context";
+  if (!c) return g_last_init_error.c_str();
   return c->err.c_str();
 }
 
@@ -720,8 +873,7 @@ void lcs_destroy(lcs_ctx *c) {
   if (!c) return;
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
-  if (c->g_step) cudaGraphExecDestroy(c->g_step);
-  if (c->g_sort) cudaGraphExecDestroy(c->g_sort);
+  drop_graphs(c);
   for (void *p : c->allocs) cudaFree(p);
   if (c->cap_st) cudaStreamDestroy(c->cap_st);
   delete c;

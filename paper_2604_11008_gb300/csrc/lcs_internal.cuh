@@ -27,9 +27,7 @@ namespace lcs {
 constexpr int NBIN = 27;          // neighbour directions including (0,0,0)
 constexpr int BIN_STAY = 13;      // (0,0,0)
 constexpr int SLACK_MIN = 128;
-constexpr int STEP_BLOCK = 256;
-constexpr int STEP_ITEMS = 2;
-constexpr int STEP_TILE = STEP_BLOCK * STEP_ITEMS;
+constexpr int MAX_ENS = 4096;    // ensembles per context
 constexpr int SORT_BLOCK = 256;
 constexpr int SORT_ITEMS = 16;
 constexpr int SORT_TILE = SORT_BLOCK * SORT_ITEMS;  // 4096
@@ -94,7 +92,28 @@ struct StepArgs {
   int64_t cap;       // slots per record buffer
   // float-pair splits (hi, lo) of dt, dt/2, dt*N/L and dt*g for the DF step
   float dfk[12];
+  int step_tile;     // particles per step tile (block size x items per thread)
 };
+
+// The ensembles of one context, as the batched kernels see them.
+struct BatchArgs {
+  const StepArgs *args;     // device array [n_ens]
+  int n_ens;
+  const int *ens_P_off;     // device [n_ens+1] prefix of subdomain counts
+  unsigned int *counter;    // device tile counters, one per step group
+  int ngroups;
+};
+
+// A group of at most CAP ensembles advanced by one step-kernel launch; the
+// whole struct is the kernel's parameter block (<= 32 KB for CAP = GROUP_ENS).
+constexpr int GROUP_ENS = 52;
+template <int CAP>
+struct StepGroup {
+  StepArgs a[CAP];
+  int n;
+  unsigned int *counter;
+};
+static_assert(sizeof(StepGroup<GROUP_ENS>) <= 32764, "kernel parameter block too large");
 
 // Segment containing global tile t: largest s with off[s] <= t.
 __device__ __forceinline__ int find_segment(const int *off, int P, int t) {
@@ -169,15 +188,16 @@ __device__ __forceinline__ int64_t block_excl_scan_1024(int64_t v, int64_t *tota
 
 // Layout of counts: compacted starts, step/sort tile prefixes, and a fresh
 // window layout (capacity = count + count/16 + SLACK_MIN).  One block of 1024.
-__device__ __forceinline__ void layout_from_counts(int P, const int64_t *cnt, int64_t *cstart, int *tile_off,
-                                   int *stile_off, int64_t *base, int64_t *cap) {
+__device__ __forceinline__ void layout_from_counts(int P, int step_tile, const int64_t *cnt,
+                                                   int64_t *cstart, int *tile_off,
+                                                   int *stile_off, int64_t *base, int64_t *cap) {
   __shared__ int64_t s_tot;
   int64_t carry_c = 0, carry_b = 0, carry_t = 0, carry_s = 0;
   for (int d0 = 0; d0 < P; d0 += 1024) {
     const int d = d0 + threadIdx.x;
     const int64_t c = d < P ? cnt[d] : 0;
     const int64_t cp = d < P ? c + c / 16 + SLACK_MIN : 0;
-    const int64_t nt = d < P ? (c + STEP_TILE - 1) / STEP_TILE : 0;
+    const int64_t nt = d < P ? (c + step_tile - 1) / step_tile : 0;
     const int64_t ns = d < P ? (c + SORT_TILE - 1) / SORT_TILE : 0;
     const int64_t ec = block_excl_scan_1024(c, &s_tot);
     const int64_t tc = s_tot;
@@ -207,13 +227,15 @@ __device__ __forceinline__ void layout_from_counts(int P, const int64_t *cnt, in
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_field_convert(const double *src, int N, FieldKind kind, void *dst,
                                  cudaStream_t st);
-cudaError_t launch_step(const StepArgs &a, FieldKind kind, int grid, cudaStream_t st);
-cudaError_t launch_finish(const StepArgs &a, cudaStream_t st);
-cudaError_t launch_unpack(const StepArgs &a, cudaStream_t st);
-cudaError_t launch_flip(const StepArgs &a, cudaStream_t st);
+template <int CAP>
+cudaError_t launch_step_group(const StepGroup<CAP> &pb, FieldKind kind, int block, int items,
+                              int grid, cudaStream_t st);
+cudaError_t launch_finish(const BatchArgs &bt, cudaStream_t st);
+cudaError_t launch_unpack(const BatchArgs &bt, int total_P, cudaStream_t st);
+cudaError_t launch_flip(const BatchArgs &bt, cudaStream_t st);
 cudaError_t launch_field_expand(const void *src, int N, FieldKind kind, double *dst,
                                 cudaStream_t st);
-int step_kernel_occupancy(FieldKind kind);
+int step_kernel_occupancy(FieldKind kind, int block, int items);
 
 // Adjoint: checkpoint of the live particles (compacted, storage order).
 struct TapeSlot {

@@ -316,8 +316,8 @@ __global__ void __launch_bounds__(1024) k_relayout(StepArgs a, int from_starts) 
   if (from_starts)
     for (int d = threadIdx.x; d < P; d += blockDim.x) a.m.cnt[d] = a.m.cstart[d + 1] - a.m.cstart[d];
   __syncthreads();
-  layout_from_counts(P, a.m.cnt, a.m.cstart, a.m.tile_off, a.m.stile_off, a.m.lay_base[ph ^ 1],
-                     a.m.lay_cap[ph ^ 1]);
+  layout_from_counts(P, a.step_tile, a.m.cnt, a.m.cstart, a.m.tile_off, a.m.stile_off,
+                     a.m.lay_base[ph ^ 1], a.m.lay_cap[ph ^ 1]);
 }
 
 // Output rank r (compacted, segment found from cstart) <- input slot pay[r].

@@ -131,40 +131,51 @@ __device__ __forceinline__ unsigned long long pack_sm(unsigned long long stay,
 using atom_u64 = cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>;
 
 // Exclusive (stay, mig) prefix of tile `t` within its segment (first tile of
-// the segment at t0).  Publishes the tile's aggregate, then its inclusive
-// prefix.  Bounded: on timeout the error is latched and the partial sum used.
-__device__ unsigned long long lookback(unsigned long long *status_arr, int t, int t0,
-                                       unsigned long long agg, int *err) {
+// the segment at t0), computed by one whole warp: the tile's aggregate is
+// published first; then the warp reads 32 predecessors per round, stops at
+// the nearest inclusive prefix, and sums the aggregates in between (decoupled
+// look-back, Merrill & Garland 2016).  Finally the tile's own inclusive prefix
+// is published.  Every lane returns the prefix.  Bounded: on timeout the
+// error is latched and the partial sum used.
+__device__ unsigned long long lookback_warp(unsigned long long *status_arr, int t, int t0,
+                                            unsigned long long agg, int *err) {
+  const int lane = threadIdx.x & 31;
   if (t == t0) {
-    atom_u64(status_arr[t]).store(FLAG_PRE | agg, cuda::memory_order_release);
+    if (lane == 0) atom_u64(status_arr[t]).store(FLAG_PRE | agg, cuda::memory_order_release);
     return 0;
   }
-  atom_u64(status_arr[t]).store(FLAG_AGG | agg, cuda::memory_order_release);
+  if (lane == 0) atom_u64(status_arr[t]).store(FLAG_AGG | agg, cuda::memory_order_release);
   unsigned long long excl = 0;
-  int j = t - 1;
+  int j = t - 1;  // newest predecessor not yet summed
   long long spins = 0;
   unsigned ns = 8;
   while (true) {
-    const unsigned long long s = atom_u64(status_arr[j]).load(cuda::memory_order_acquire);
-    const unsigned long long f = s & FLAG_MASK;
-    if (f == FLAG_PRE) {
-      excl += s & VAL_MASK;
-      break;
-    }
-    if (f == FLAG_AGG) {
-      excl += s & VAL_MASK;
-      if (j == t0) break;  // cannot happen (first tile publishes a prefix)
-      --j;
+    const int idx = j - lane;
+    unsigned long long v = FLAG_PRE;  // before the segment start: prefix 0
+    if (idx >= t0) v = atom_u64(status_arr[idx]).load(cuda::memory_order_acquire);
+    const unsigned long long f = v & FLAG_MASK;
+    const unsigned pre = __ballot_sync(0xffffffffu, f == FLAG_PRE);
+    const unsigned inv = __ballot_sync(0xffffffffu, f == 0);
+    const int upto = pre ? __ffs(pre) - 1 : 31;          // lanes 0..upto are needed
+    const unsigned need = upto == 31 ? 0xffffffffu : ((2u << upto) - 1u);
+    if (inv & need) {
+      if (++spins > SPIN_LIMIT / 64) {
+        if (lane == 0) latch(err, LCS_ERR_TIMEOUT);
+        break;
+      }
+      __nanosleep(ns);
+      ns = ns < 256 ? ns * 2 : 256;
       continue;
     }
-    if (++spins > SPIN_LIMIT / 64) {
-      latch(err, LCS_ERR_TIMEOUT);
-      break;
-    }
-    __nanosleep(ns);
-    ns = ns < 256 ? ns * 2 : 256;
+    unsigned long long part = lane <= upto ? (v & VAL_MASK) : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    excl += part;
+    if (pre) break;
+    j -= 32;
   }
-  atom_u64(status_arr[t]).store(FLAG_PRE | (excl + agg), cuda::memory_order_release);
+  if (lane == 0)
+    atom_u64(status_arr[t]).store(FLAG_PRE | (excl + agg), cuda::memory_order_release);
   return excl;
 }
 
@@ -214,142 +225,197 @@ __device__ __forceinline__ int dest_bin(const Geom &g, int seg, const double x[3
   return bin;
 }
 
-template <int KIND>
-__global__ void __launch_bounds__(STEP_BLOCK) k_step(StepArgs a) {
-  __shared__ int s_tile;
-  __shared__ unsigned s_warp[STEP_BLOCK / 32];
-  __shared__ unsigned long long s_excl;
-  __shared__ int s_hist[NBIN];
-  const int ph = *a.m.phase;
+struct StepShared {
+  int tile;
+  unsigned warp[32];
+  unsigned long long excl;
+  int hist[NBIN];
+};
+
+// One tile of one ensemble: integrate + wrap + flag its particles, block scan
+// of the (stay, leave) flags, look-back across the segment's earlier tiles,
+// then stayers to their compacted slot in the output buffer and leavers to
+// the pack buffer.  Tile j of segment s covers particles
+// [j*BLOCK*ITEMS, (j+1)*BLOCK*ITEMS) of the segment, ITEMS consecutive ones
+// per thread.
+template <int KIND, int BLOCK, int ITEMS>
+__device__ __forceinline__ void step_tile(const StepArgs &a, int ph, int tile, StepShared &sh) {
   const Rec A = a.buf[ph], B = a.buf[ph ^ 1];
   const int64_t *baseA = a.m.lay_base[ph];
   const int64_t *baseB = a.m.lay_base[ph ^ 1];
   const int64_t *capB = a.m.lay_cap[ph ^ 1];
   const int P = a.geo.Ptot;
-  const int total = a.m.tile_off[P];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int seg = find_segment(a.m.tile_off, P, tile);
+  const int t0 = a.m.tile_off[seg];
+  const int ntile = a.m.tile_off[seg + 1] - t0;
+  const int jt = tile - t0;
+  const int64_t cnt = a.m.cnt[seg];
+  const int64_t l0 = (int64_t)jt * (BLOCK * ITEMS) + (int64_t)threadIdx.x * ITEMS;
+  const int64_t bA = baseA[seg];
 
-  for (;;) {
-    if (threadIdx.x == 0) s_tile = (int)atomicAdd(a.m.tile_counter, 1u);
-    if (threadIdx.x < NBIN) s_hist[threadIdx.x] = 0;
-    __syncthreads();
-    const int tile = s_tile;
-    if (tile >= total) break;
-    const int seg = find_segment(a.m.tile_off, P, tile);
-    const int t0 = a.m.tile_off[seg];
-    const int ntile = a.m.tile_off[seg + 1] - t0;
-    const int jt = tile - t0;
-    const int64_t cnt = a.m.cnt[seg];
-    const int64_t l0 = (int64_t)jt * STEP_TILE + (int64_t)threadIdx.x * STEP_ITEMS;
-    const int64_t bA = baseA[seg];
-
-    double x[STEP_ITEMS][3], v[STEP_ITEMS][3], tau[STEP_ITEMS];
-    uint32_t id[STEP_ITEMS];
-    int img[STEP_ITEMS][3], bin[STEP_ITEMS];
-    unsigned packed = 0;
-    int bad = 0;
+  double x[ITEMS][3], v[ITEMS][3], tau[ITEMS];
+  uint32_t id[ITEMS];
+  int img[ITEMS][3], bin[ITEMS];
+  unsigned packed = 0;
+  int bad = 0;
 #pragma unroll
-    for (int k = 0; k < STEP_ITEMS; ++k) {
-      bin[k] = -2;  // invalid item
-      if (l0 + k < cnt) {
-        load_rec(A, bA + l0 + k, x[k], v[k], tau[k], id[k], img[k], a.tau_const);
-        if (KIND == FK_F64) heun_step64(a, x[k], v[k], tau[k], img[k], bad);
-        else heun_step_df<KIND>(a, x[k], v[k], tau[k], img[k], bad);
-        int b = dest_bin(a.geo, seg, x[k]);
-        if (b < 0) {
-          bad |= 2;
-          b = BIN_STAY;  // keep it in place; the error is latched
-        }
-        bin[k] = b;
-        if (b == BIN_STAY) {
-          packed += 1u << 16;
-        } else {
-          packed += 1u;
-          atomicAdd(&s_hist[b], 1);
-        }
+  for (int k = 0; k < ITEMS; ++k) {
+    bin[k] = -2;  // invalid item
+    if (l0 + k < cnt) {
+      load_rec(A, bA + l0 + k, x[k], v[k], tau[k], id[k], img[k], a.tau_const);
+      if (KIND == FK_F64) heun_step64(a, x[k], v[k], tau[k], img[k], bad);
+      else heun_step_df<KIND>(a, x[k], v[k], tau[k], img[k], bad);
+      int b = dest_bin(a.geo, seg, x[k]);
+      if (b < 0) {
+        bad |= 2;
+        b = BIN_STAY;  // keep it in place; the error is latched
+      }
+      bin[k] = b;
+      if (b == BIN_STAY) {
+        packed += 1u << 16;
+      } else {
+        packed += 1u;
+        atomicAdd(&sh.hist[b], 1);
       }
     }
-    if (bad & 1) latch(a.m.status, LCS_ERR_NONFINITE);
-    if (bad & 2) latch(a.m.status, LCS_ERR_DISPLACEMENT);
+  }
+  if (bad & 1) latch(a.m.status, LCS_ERR_NONFINITE);
+  if (bad & 2) latch(a.m.status, LCS_ERR_DISPLACEMENT);
 
-    // block exclusive scan of the packed (stay << 16 | mig) counts
-    unsigned incl = packed;
+  // block exclusive scan of the packed (stay << 16 | leave) counts
+  unsigned incl = packed;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) sh.warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned wv = lane < BLOCK / 32 ? sh.warp[lane] : 0u;
+    unsigned wi = wv;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
+      const unsigned y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
     }
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-      unsigned wv = lane < STEP_BLOCK / 32 ? s_warp[lane] : 0u;
-      unsigned wi = wv;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned y = __shfl_up_sync(0xffffffffu, wi, o);
-        if (lane >= o) wi += y;
-      }
-      if (lane < STEP_BLOCK / 32) s_warp[lane] = wi - wv;  // exclusive warp offsets
-      if (lane == STEP_BLOCK / 32 - 1) {
-        const unsigned long long agg = pack_sm(wi >> 16, wi & 0xffffu);
-        const unsigned long long ex = lookback(a.m.tile_status, tile, t0, agg, a.m.status);
-        s_excl = ex;
-        if (jt == ntile - 1) {
-          const unsigned long long inc = ex + agg;
-          a.m.stay_tot[seg] = (int64_t)(inc >> 31);
-          a.m.mig_tot[seg] = (int64_t)(inc & ((1ull << 31) - 1));
-        }
+    if (lane < BLOCK / 32) sh.warp[lane] = wi - wv;  // exclusive warp offsets
+    const unsigned tot = __shfl_sync(0xffffffffu, wi, BLOCK / 32 - 1);
+    const unsigned long long agg = pack_sm(tot >> 16, tot & 0xffffu);
+    const unsigned long long ex = lookback_warp(a.m.tile_status, tile, t0, agg, a.m.status);
+    if (lane == 0) {
+      sh.excl = ex;
+      if (jt == ntile - 1) {
+        const unsigned long long inc = ex + agg;
+        a.m.stay_tot[seg] = (int64_t)(inc >> 31);
+        a.m.mig_tot[seg] = (int64_t)(inc & ((1ull << 31) - 1));
       }
     }
-    __syncthreads();
-    if (threadIdx.x < NBIN && threadIdx.x != BIN_STAY && s_hist[threadIdx.x])
-      atomicAdd(&a.m.bincnt[seg * NBIN + threadIdx.x], s_hist[threadIdx.x]);
+  }
+  __syncthreads();
+  if (threadIdx.x < NBIN && threadIdx.x != BIN_STAY && sh.hist[threadIdx.x])
+    atomicAdd(&a.m.bincnt[seg * NBIN + threadIdx.x], sh.hist[threadIdx.x]);
 
-    const unsigned excl = incl - packed + s_warp[warp];
-    int64_t stay_pos = (int64_t)(s_excl >> 31) + (excl >> 16);
-    int64_t mig_pos = (int64_t)(s_excl & ((1ull << 31) - 1)) + (excl & 0xffffu);
-    const int64_t bB = baseB[seg], cB = capB[seg];
+  const unsigned excl = incl - packed + sh.warp[warp];
+  int64_t stay_pos = (int64_t)(sh.excl >> 31) + (excl >> 16);
+  int64_t mig_pos = (int64_t)(sh.excl & ((1ull << 31) - 1)) + (excl & 0xffffu);
+  const int64_t bB = baseB[seg], cB = capB[seg];
 #pragma unroll
-    for (int k = 0; k < STEP_ITEMS; ++k) {
-      if (bin[k] == -2) continue;
-      if (bin[k] == BIN_STAY) {
-        if (stay_pos < cB) {
-          store_rec(B, bB + stay_pos, x[k], v[k], tau[k], id[k], img[k]);
-        } else {
-          latch(a.m.status, LCS_ERR_CAPACITY);
-        }
-        ++stay_pos;
+  for (int k = 0; k < ITEMS; ++k) {
+    if (bin[k] == -2) continue;
+    if (bin[k] == BIN_STAY) {
+      if (stay_pos < cB) {
+        store_rec(B, bB + stay_pos, x[k], v[k], tau[k], id[k], img[k]);
       } else {
-        const int64_t o = bA + mig_pos;
-        store_rec(a.pack, o, x[k], v[k], tau[k], id[k], img[k]);
-        a.pack_bin[o] = (uint8_t)bin[k];
-        ++mig_pos;
+        latch(a.m.status, LCS_ERR_CAPACITY);
       }
+      ++stay_pos;
+    } else {
+      const int64_t o = bA + mig_pos;
+      store_rec(a.pack, o, x[k], v[k], tau[k], id[k], img[k]);
+      a.pack_bin[o] = (uint8_t)bin[k];
+      ++mig_pos;
+    }
+  }
+}
+
+// Persistent step kernel over the tiles of a group of ensembles: tile ids
+// come from one counter in launch order, so within an ensemble every tile's
+// predecessors were taken by running blocks (the look-back cannot wait on a
+// block that has not started).  The group's arguments travel as the kernel's
+// parameter block (constant bank: usable as instruction operands without
+// registers, and never aliased by the kernel's stores).
+template <int KIND, int BLOCK, int ITEMS, int CAP>
+__global__ void __launch_bounds__(BLOCK, 512 / BLOCK)
+    k_step(const __grid_constant__ StepGroup<CAP> pb) {
+  __shared__ StepShared sh;
+  __shared__ int s_off[CAP + 1];
+  const int n = pb.n;
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int e = 0; e < n; ++e) {
+      s_off[e] = acc;
+      acc += pb.a[e].m.tile_off[pb.a[e].geo.Ptot];
+    }
+    s_off[n] = acc;
+  }
+  __syncthreads();
+  const int total = s_off[n];
+  for (;;) {
+    if (threadIdx.x == 0) sh.tile = (int)atomicAdd(pb.counter, 1u);
+    if (threadIdx.x < NBIN) sh.hist[threadIdx.x] = 0;
+    __syncthreads();
+    const int g = sh.tile;
+    if (g >= total) break;
+    if (CAP == 1) {
+      step_tile<KIND, BLOCK, ITEMS>(pb.a[0], *pb.a[0].m.phase, g, sh);
+    } else {
+      int e = 0, hi = n;  // s_off[e] <= g < s_off[hi]
+      while (hi - e > 1) {
+        const int mid = (e + hi) >> 1;
+        if (s_off[mid] <= g) e = mid; else hi = mid;
+      }
+      step_tile<KIND, BLOCK, ITEMS>(pb.a[e], *pb.a[e].m.phase, g - s_off[e], sh);
     }
     __syncthreads();
   }
 }
 
-cudaError_t launch_step(const StepArgs &a, FieldKind kind, int grid, cudaStream_t st) {
-  switch (kind) {
-    case FK_F64: k_step<FK_F64><<<grid, STEP_BLOCK, 0, st>>>(a); break;
-    case FK_F32: k_step<FK_F32><<<grid, STEP_BLOCK, 0, st>>>(a); break;
-    case FK_BF16: k_step<FK_BF16><<<grid, STEP_BLOCK, 0, st>>>(a); break;
-    case FK_DF: k_step<FK_DF><<<grid, STEP_BLOCK, 0, st>>>(a); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
-}
+#define LCS_STEP_CONFIGS(X, K, C) X(K, 256, 2, C) X(K, 256, 1, C) X(K, 128, 2, C)
+#define LCS_ALL_CONFIGS(X)                                                              \
+  LCS_STEP_CONFIGS(X, FK_F64, 1) LCS_STEP_CONFIGS(X, FK_DF, 1)                          \
+  LCS_STEP_CONFIGS(X, FK_F32, 1) LCS_STEP_CONFIGS(X, FK_BF16, 1)                        \
+  LCS_STEP_CONFIGS(X, FK_F64, GROUP_ENS) LCS_STEP_CONFIGS(X, FK_DF, GROUP_ENS)          \
+  LCS_STEP_CONFIGS(X, FK_F32, GROUP_ENS) LCS_STEP_CONFIGS(X, FK_BF16, GROUP_ENS)
 
-int step_kernel_occupancy(FieldKind kind) {
-  int n = 0;
-  switch (kind) {
-    case FK_F64: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<FK_F64>, STEP_BLOCK, 0); break;
-    case FK_F32: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<FK_F32>, STEP_BLOCK, 0); break;
-    case FK_BF16: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<FK_BF16>, STEP_BLOCK, 0); break;
-    case FK_DF: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<FK_DF>, STEP_BLOCK, 0); break;
-    default: break;
+template <int CAP>
+cudaError_t launch_step_group(const StepGroup<CAP> &pb, FieldKind kind, int block, int items,
+                              int grid, cudaStream_t st) {
+#define LCS_LAUNCH(K, B, I, C)                                           \
+  if (C == CAP && kind == K && block == B && items == I) {              \
+    k_step<K, B, I, CAP><<<grid, B, 0, st>>>(pb);                        \
+    return cudaGetLastError();                                           \
   }
+  LCS_STEP_CONFIGS(LCS_LAUNCH, FK_F64, CAP)
+  LCS_STEP_CONFIGS(LCS_LAUNCH, FK_DF, CAP)
+  LCS_STEP_CONFIGS(LCS_LAUNCH, FK_F32, CAP)
+  LCS_STEP_CONFIGS(LCS_LAUNCH, FK_BF16, CAP)
+#undef LCS_LAUNCH
+  return cudaErrorInvalidValue;
+}
+template cudaError_t launch_step_group<1>(const StepGroup<1> &, FieldKind, int, int, int,
+                                          cudaStream_t);
+template cudaError_t launch_step_group<GROUP_ENS>(const StepGroup<GROUP_ENS> &, FieldKind, int,
+                                                  int, int, cudaStream_t);
+
+int step_kernel_occupancy(FieldKind kind, int block, int items) {
+  int n = 0;
+#define LCS_OCC(K, B, I, C)                                                         \
+  if (C == GROUP_ENS && kind == K && block == B && items == I)                      \
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<K, B, I, C>, B, 0);
+  LCS_ALL_CONFIGS(LCS_OCC)
+#undef LCS_OCC
   return n;
 }
 
@@ -357,7 +423,7 @@ int step_kernel_occupancy(FieldKind kind) {
 
 // Per destination d: arrival offsets of every (source, direction) pair in
 // source order after the stayers, the new count, and the next layout.
-__global__ void __launch_bounds__(1024) k_finish(StepArgs a) {
+__device__ __forceinline__ void finish_body(const StepArgs &a) {
   const Geom &g = a.geo;
   const int P = g.Ptot;
   const int ph = *a.m.phase;
@@ -399,12 +465,15 @@ __global__ void __launch_bounds__(1024) k_finish(StepArgs a) {
     a.m.cnt[d] = off;
   }
   __syncthreads();
-  layout_from_counts(P, a.m.cnt, a.m.cstart, a.m.tile_off, a.m.stile_off, a.m.next_base,
-                     a.m.next_cap);
+  layout_from_counts(P, a.step_tile, a.m.cnt, a.m.cstart, a.m.tile_off, a.m.stile_off,
+                     a.m.next_base, a.m.next_cap);
 }
 
-cudaError_t launch_finish(const StepArgs &a, cudaStream_t st) {
-  k_finish<<<1, 1024, 0, st>>>(a);
+// One block per ensemble.
+__global__ void __launch_bounds__(1024) k_finish(BatchArgs bt) { finish_body(bt.args[blockIdx.x]); }
+
+cudaError_t launch_finish(const BatchArgs &bt, cudaStream_t st) {
+  k_finish<<<bt.n_ens, 1024, 0, st>>>(bt);
   return cudaGetLastError();
 }
 
@@ -413,11 +482,10 @@ cudaError_t launch_finish(const StepArgs &a, cudaStream_t st) {
 // One block per source subdomain: place its packed leavers, in pack order,
 // after the stayers of their destination (offsets from k_finish), keeping
 // the order within each (source, direction) pair.
-__global__ void __launch_bounds__(256) k_unpack(StepArgs a) {
+__device__ __forceinline__ void unpack_body(const StepArgs &a, int s) {
   __shared__ int s_wc[8][NBIN];
   __shared__ int s_run[NBIN];
   const Geom &g = a.geo;
-  const int s = blockIdx.x;
   const int ph = *a.m.phase;
   const Rec B = a.buf[ph ^ 1];
   const int64_t bA = a.m.lay_base[ph][s];
@@ -469,8 +537,15 @@ __global__ void __launch_bounds__(256) k_unpack(StepArgs a) {
   if (threadIdx.x == 0) a.m.mig_tot[s] = 0;
 }
 
-cudaError_t launch_unpack(const StepArgs &a, cudaStream_t st) {
-  k_unpack<<<a.geo.Ptot, 256, 0, st>>>(a);
+// One block per (ensemble, source subdomain); ens_P_off is the prefix of the
+// ensembles' subdomain counts.
+__global__ void __launch_bounds__(256) k_unpack(BatchArgs bt) {
+  const int e = find_segment(bt.ens_P_off, bt.n_ens, (int)blockIdx.x);
+  unpack_body(bt.args[e], blockIdx.x - bt.ens_P_off[e]);
+}
+
+cudaError_t launch_unpack(const BatchArgs &bt, int total_P, cudaStream_t st) {
+  k_unpack<<<total_P, 256, 0, st>>>(bt);
   return cudaGetLastError();
 }
 
@@ -478,7 +553,9 @@ cudaError_t launch_unpack(const StepArgs &a, cudaStream_t st) {
 
 // The old input buffer becomes the next output with the layout from
 // k_finish; the output becomes the input.
-__global__ void k_flip(StepArgs a) {
+// One block per ensemble; block 0 also resets the step groups' tile counters.
+__global__ void k_flip(BatchArgs bt) {
+  const StepArgs &a = bt.args[blockIdx.x];
   const int ph = *a.m.phase;
   for (int d = threadIdx.x; d < a.geo.Ptot; d += blockDim.x) {
     a.m.lay_base[ph][d] = a.m.next_base[d];
@@ -489,10 +566,12 @@ __global__ void k_flip(StepArgs a) {
     *a.m.phase = ph ^ 1;
     *a.m.tile_counter = 0u;
   }
+  if (blockIdx.x == 0)
+    for (int k = threadIdx.x; k < bt.ngroups; k += blockDim.x) bt.counter[k] = 0u;
 }
 
-cudaError_t launch_flip(const StepArgs &a, cudaStream_t st) {
-  k_flip<<<1, 1024, 0, st>>>(a);
+cudaError_t launch_flip(const BatchArgs &bt, cudaStream_t st) {
+  k_flip<<<bt.n_ens, 1024, 0, st>>>(bt);
   return cudaGetLastError();
 }
 

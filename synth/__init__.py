@@ -257,3 +257,28 @@ def small_case(seed: int, N: int, M: int, kmax: float, n: int, tau_median: float
     tau = None if tau_median is None else lognormal_tau(n, tau_median, sigma, dt,
                                                          rng(seed, STREAM_TAU))
     return field, modes, x, v, tau
+
+
+def batch_ensembles(n_ens: int = 48, number: int = 5, device: str = "cpu", scale: float = 1.0):
+    """The batching workload: n_ens independent ensembles.
+
+    Grid N uniform in {64, 96, 128, 256}; 256 modes with k in [1, N/8];
+    particle count 10^clip(N(5.5, 0.5), 4, 7) (times `scale`); tau_p uniform
+    in [0.01, 1]; no gravity; 2x2x2 subdomains; dt from the CFL rule per
+    ensemble.  Returns a list of dicts with field, x0, v0, tau, dt, n."""
+    g = rng(number, STREAM_ENS)
+    sizes = g.choice([64, 96, 128, 256], size=n_ens)
+    counts = 10.0 ** np.clip(g.normal(5.5, 0.5, size=n_ens), 4.0, 7.0)
+    out = []
+    for e in range(n_ens):
+        N = int(sizes[e])
+        gm = rng(number * 1000 + e, STREAM_FIELD)
+        modes = draw_modes(256, 1.0, N / 8.0, gm)
+        field = field_from_modes(modes, N, device=device)
+        dt = cfl_dt(max_speed(field), N)
+        n = max(1, int(counts[e] * scale))
+        x = positions(n, rng(number * 1000 + e, STREAM_POS))
+        tau = rng(number * 1000 + e, STREAM_TAU).uniform(0.01, 1.0, size=n)
+        tau = np.maximum(tau, dt)
+        out.append(dict(field=field, x0=x, v0=np.zeros_like(x), tau=tau, dt=dt, n=n, N=N))
+    return out
