@@ -163,6 +163,53 @@ def adjoint_ratio(lcs, torch, steps=None):
     return res
 
 
+# ---------------------------------------------------------------- batching
+
+def batch_throughput(lcs, torch, steps=500, n_ens=48):
+    """The batching workload (48 ensembles, grids 64-256^3, 10^4-10^7
+    particles, FP32 fields, 2x2x2, sort every 10, 500 steps): total
+    particle-updates/s of all ensembles in one context (autotuned) against
+    the same ensembles stepped one context at a time in FP64 and in FP32."""
+    ens = synth.batch_ensembles(n_ens, device="cuda")
+    total = sum(e["n"] for e in ens)
+    st = torch.cuda.current_stream()
+
+    def timed(sim, k):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        sim.step(k)
+        e1.record(st)
+        sim.sync()
+        return e0.elapsed_time(e1)
+
+    spec = lambda e, dtype: dict(field=e["field"], x0=e["x0"], v0=e["v0"], dt=e["dt"],
+                                 tau=e["tau"], sub=(2, 2, 2), sort_every=10, field_dtype=dtype)
+    sim = lcs.Simulator(None, None, None, None, ensembles=[spec(e, "f32") for e in ens])
+    block, items = sim.tune(2)
+    timed(sim, 4)  # the remaining steps of the first sort period
+    ms_batch = timed(sim, steps)
+    launches = sim.launches
+    sim.close()
+    solo = {}
+    for dtype in ("f64", "f32"):
+        ms = 0.0
+        for e in ens:
+            s1 = lcs.Simulator(**spec(e, dtype))
+            timed(s1, 10)  # warm-up: graph capture
+            ms += timed(s1, steps)
+            s1.close()
+        solo[dtype] = ms
+    rate = lambda ms_: total * steps / (ms_ * 1e-3)
+    return {"workload": f"{n_ens} ensembles, grids 64-256^3, {total} particles, FP32 fields, "
+                        f"2x2x2 each, sort every 10",
+            "steps": steps, "value_batched_f32": rate(ms_batch),
+            "value_one_by_one_f64": rate(solo["f64"]), "value_one_by_one_f32": rate(solo["f32"]),
+            "speedup_vs_one_by_one_f64": round(solo["f64"] / ms_batch, 3),
+            "speedup_vs_one_by_one_f32": round(solo["f32"] / ms_batch, 3),
+            "tuned_block": block, "tuned_items": items, "unit": UNIT}
+
+
 # ---------------------------------------------------------------- main
 
 def main():
@@ -177,6 +224,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1 << 20)
+    ap.add_argument("--batch", type=int, default=1,
+                    help="also time the 48-ensemble batching workload")
     ap.add_argument("--adjoint", type=int, default=1,
                     help="also time forward (taped) vs backward on grad_128")
     ap.add_argument("--np", type=int, default=0,
@@ -279,6 +328,9 @@ def main():
     adjoint = None
     if rank == 0 and args.adjoint:
         adjoint = adjoint_ratio(lcs, torch)
+    batch = None
+    if rank == 0 and args.batch:
+        batch = batch_throughput(lcs, torch)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -304,7 +356,7 @@ def main():
                           "field_storage": args.field, "kernel": args.kernel,
                           "l2": "inputs larger than L2 (state ~1 GB, field 0.54 GB)",
                           "parallelism": f"replicas{world}"},
-               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "adjoint": adjoint,
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "adjoint": adjoint, "batch": batch,
                "gpu_launches": int(launches), "clocks": clk,
                "kernel_profile_ms": {k: round(v_[0], 4) for k, v_ in prof.items()}}
         print(json.dumps(out))
