@@ -210,6 +210,37 @@ def batch_throughput(lcs, torch, steps=500, n_ens=48):
             "tuned_block": block, "tuned_items": items, "unit": UNIT}
 
 
+# ---------------------------------------------------------------- precision variants
+
+def precision_throughput(lcs, torch, steps=20):
+    """The precision workload (512^3 field, 10^8 particles, 8x8x8, gravity,
+    sort every 10): particle-updates/s with the field stored in FP64
+    (float-float kernel), FP32 and BF16, and the FP32-over-FP64 speedup."""
+    w = synth.WORKLOADS["precision_512"]
+    field, _ = synth.make_field(w, device="cuda")
+    dt = synth.cfl_dt(synth.max_speed(field), w.N)
+    x, v, tau = synth.make_particles(w, dt)
+    st = torch.cuda.current_stream()
+    out = {"workload": "precision_512 (512^3, 1e8 particles, 8x8x8, sort every 10)",
+           "steps": steps, "unit": UNIT}
+    for dtype in ("f64", "f32", "bf16"):
+        sim = lcs.Simulator(field, x, v, dt, tau=tau, g=w.g, sub=w.sub, field_dtype=dtype,
+                            sort_every=w.sort_every)
+        sim.step(10)
+        sim.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        sim.step(steps)
+        e1.record(st)
+        sim.sync()
+        out[dtype] = w.np_ * steps / (e0.elapsed_time(e1) * 1e-3)
+        sim.close()
+        torch.cuda.empty_cache()
+    out["f32_speedup_vs_f64"] = round(out["f32"] / out["f64"], 3)
+    out["bf16_speedup_vs_f64"] = round(out["bf16"] / out["f64"], 3)
+    return out
+
+
 # ---------------------------------------------------------------- main
 
 def main():
@@ -224,6 +255,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1 << 20)
+    ap.add_argument("--precision", type=int, default=1,
+                    help="also time FP64/FP32/BF16 field storage on precision_512")
     ap.add_argument("--batch", type=int, default=1,
                     help="also time the 48-ensemble batching workload")
     ap.add_argument("--adjoint", type=int, default=1,
@@ -331,6 +364,9 @@ def main():
     batch = None
     if rank == 0 and args.batch:
         batch = batch_throughput(lcs, torch)
+    precision = None
+    if rank == 0 and args.precision:
+        precision = precision_throughput(lcs, torch)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -357,6 +393,7 @@ def main():
                           "l2": "inputs larger than L2 (state ~1 GB, field 0.54 GB)",
                           "parallelism": f"replicas{world}"},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "adjoint": adjoint, "batch": batch,
+               "precision": precision,
                "gpu_launches": int(launches), "clocks": clk,
                "kernel_profile_ms": {k: round(v_[0], 4) for k, v_ in prof.items()}}
         print(json.dumps(out))
