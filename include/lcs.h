@@ -180,12 +180,14 @@ enum {
 lcs_status lcs_profile_steps(lcs_ctx *ctx, int64_t nsteps, double *ms, int64_t *count);
 
 /* Autotuner: time every step-kernel configuration (threads per block x
- * particles per thread, i.e. the scan tile) on steps_per_trial real steps of
- * all ensembles, keep the fastest, and rebuild the step graphs with it.
- * The trial steps advance the simulation (3 * steps_per_trial steps in
- * all, recorded like any other step); results do not depend on the choice.
- * *block and *items (may be NULL) receive the configuration.  Synchronising. */
-lcs_status lcs_tune(lcs_ctx *ctx, int steps_per_trial, int *block, int *items);
+ * particles per thread, i.e. the scan tile: 256x2, 256x1, 128x2) on
+ * steps_per_trial real steps of all ensembles, keep the fastest, and
+ * rebuild the step graphs with it.  The trial steps advance the simulation
+ * (3 * steps_per_trial steps in all, recorded like any other step); results
+ * do not depend on the choice.  *block and *items (may be NULL) receive the
+ * choice; trial_ms (host, 3 doubles, may be NULL) the step-kernel
+ * milliseconds of each configuration in that order.  Synchronising. */
+lcs_status lcs_tune(lcs_ctx *ctx, int steps_per_trial, int *block, int *items, double *trial_ms);
 
 /* Wait for all enqueued work; return the latched device status. */
 lcs_status lcs_sync(lcs_ctx *ctx);

@@ -84,7 +84,7 @@ def lib():
         L.lcs_partition.argtypes = [P, i64, i32, P, P, P, P]
         L.lcs_profile_steps.argtypes = [P, i64, P, P]
         L.lcs_partition_noalloc.argtypes = [P, i64, i32, P, P, P, P]
-        L.lcs_tune.argtypes = [P, i32, P, P]
+        L.lcs_tune.argtypes = [P, i32, P, P, P]
         for name in ("lcs_init", "lcs_step", "lcs_migrate", "lcs_sort", "lcs_set_state",
                      "lcs_get_state", "lcs_get_field", "lcs_backward", "lcs_sync",
                      "lcs_partition", "lcs_profile_steps", "lcs_partition_noalloc", "lcs_tune"):
@@ -212,9 +212,13 @@ class Simulator:
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(PROF_CLASSES)}
 
     def tune(self, steps_per_trial: int = 2):
-        """Autotune the step kernel (advances the simulation); returns (block, items)."""
+        """Autotune the step kernel's scan tile (advances the simulation by
+        3 * steps_per_trial steps); returns (threads per block, items per thread)."""
         b, it = C.c_int(), C.c_int()
-        self._check(lib().lcs_tune(self._ctx, int(steps_per_trial), C.byref(b), C.byref(it)))
+        ms = np.zeros(3, dtype=np.float64)
+        self._check(lib().lcs_tune(self._ctx, int(steps_per_trial), C.byref(b), C.byref(it),
+                                   _ptr(ms)))
+        self.tune_trials_ms = ms
         return b.value, it.value
 
     @property

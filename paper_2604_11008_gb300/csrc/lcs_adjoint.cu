@@ -76,7 +76,8 @@ __global__ void k_recompute(StepArgs a, TapeSlot t, double *states, int len, int
     }
     int bad = 0;
     if (KIND == FK_F64) heun_step64(a, x, v, tau, img, bad);
-    else heun_step_df<KIND>(a, x, v, tau, img, bad);
+    else if (KIND == FK_DF) heun_step_df<KIND>(a, x, v, tau, img, bad);
+    else heun_step_lo<KIND>(a, x, v, tau, img, bad);
   }
 }
 
@@ -307,7 +308,8 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs p) {
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
       q1[s] = fix_stage1(x[s], a.geo.inv_dx);
-      q2[s] = fix_stage2(q1[s], split_d(v[s]), cx);
+      q2[s] = KIND == FK_DF ? fix_stage2(q1[s], split_d(v[s]), cx)
+                            : fix_stage2_lo(q1[s], split_d(v[s]).h, a.dfk[4]);
     }
     astage_from_fix(q1, N, S1);
     astage_from_fix(q2, N, S2);

@@ -72,7 +72,8 @@ struct lcs_ctx {
   int sms = 152;
   // batched step over all ensembles (one launch per kernel per step)
   FieldKind kind = FK_F64;
-  int block = 256, items = 2;   // step tile = block * items (autotuned)
+  int mode = 0;                 // step kernel variant (one: block tiles)
+  int block = 256, items = 2;   // threads per block, particles per thread (autotuned)
   int step_grid = 1, total_P = 0;
   int64_t total_tiles = 0;      // sum of the ensembles' look-back array sizes
   unsigned long long *tile_status = nullptr;
@@ -173,7 +174,7 @@ lcs_status launch_steps(lcs_ctx *c, cudaStream_t st) {
   static thread_local StepGroup<GROUP_ENS> big;
   for (size_t gi = 0; gi < c->groups.size(); ++gi) {
     const int first = c->groups[gi].first, cnt = c->groups[gi].second;
-    const int occ = std::max(1, step_kernel_occupancy(c->kind, c->block, c->items));
+    const int occ = std::max(1, step_kernel_occupancy(c->kind, c->mode, c->block, c->items));
     const int grid = (int)std::max<int64_t>(
         1, std::min<int64_t>(c->group_tiles[gi], (int64_t)occ * c->sms));
     if (cnt == 1) {
@@ -181,12 +182,12 @@ lcs_status launch_steps(lcs_ctx *c, cudaStream_t st) {
       one.a[0] = c->ens[first].a;
       one.n = 1;
       one.counter = c->d_counter + gi;
-      CK(launch_step_group<1>(one, c->kind, c->block, c->items, grid, st));
+      CK(launch_step_group<1>(one, c->kind, c->mode, c->block, c->items, grid, st));
     } else {
       for (int k = 0; k < cnt; ++k) big.a[k] = c->ens[first + k].a;
       big.n = cnt;
       big.counter = c->d_counter + gi;
-      CK(launch_step_group<GROUP_ENS>(big, c->kind, c->block, c->items, grid, st));
+      CK(launch_step_group<GROUP_ENS>(big, c->kind, c->mode, c->block, c->items, grid, st));
     }
     c->launches += 1;
   }
@@ -454,6 +455,7 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
     for (int s = 0; s < 3; ++s) {
       g.P[s] = d.sub[s];
       g.W[s] = d.n / d.sub[s];
+      g.Wrcp[s] = (unsigned)(((uint64_t(1) << 32) + g.W[s] - 1) / g.W[s]);
     }
     e.brick = d.sort_brick ? d.sort_brick : 8;
     int64_t space = (int64_t)e.brick * e.brick * e.brick;
@@ -467,7 +469,7 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
     }
     e.key_bits = ceil_log2(space);
     e.mig_bits = std::max(1, ceil_log2(2 * (int64_t)P));
-    e.max_tiles = (int)(e.np / 256 + P + 2);  // 256 = smallest step tile of any config
+    e.max_tiles = (int)(e.np / 32 + P + 2);  // 32 = smallest step tile of any config
     e.a.step_tile = c->block * c->items;
     e.max_stiles = (int)(e.np / SORT_TILE + P + 2);
     e.a.dt = d.dt;
@@ -826,10 +828,11 @@ lcs_status lcs_profile_steps(lcs_ctx *c, int64_t nsteps, double *ms, int64_t *co
   return read_status(c);
 }
 
-lcs_status lcs_tune(lcs_ctx *c, int steps_per_trial, int *block, int *items) {
+lcs_status lcs_tune(lcs_ctx *c, int steps_per_trial, int *block, int *items, double *trial_ms) {
   lcs_status r = check_ctx(c);
   if (r != LCS_OK) return r;
   if (steps_per_trial < 1) return fail(c, LCS_ERR_ARG, "lcs_tune: steps_per_trial < 1");
+  // (threads per block, particles per thread)
   static const int cfg[][2] = {{256, 2}, {256, 1}, {128, 2}};
   double best = 1e300;
   int bi = 0;
@@ -841,6 +844,7 @@ lcs_status lcs_tune(lcs_ctx *c, int steps_per_trial, int *block, int *items) {
     double ms[LCS_PROF_N];
     r = lcs_profile_steps(c, steps_per_trial, ms, nullptr);
     if (r != LCS_OK) return r;
+    if (trial_ms) trial_ms[k] = ms[LCS_PROF_STEP];
     if (ms[LCS_PROF_STEP] < best) {
       best = ms[LCS_PROF_STEP];
       bi = k;
@@ -850,8 +854,7 @@ lcs_status lcs_tune(lcs_ctx *c, int steps_per_trial, int *block, int *items) {
   c->items = cfg[bi][1];
   r = retile(c);
   if (r != LCS_OK) return r;
-  // graphs recorded with the old configuration are rebuilt on the next lcs_step
-  drop_graphs(c);
+  drop_graphs(c);  // graphs recorded with the old configuration are rebuilt
   if (block) *block = c->block;
   if (items) *items = c->items;
   return LCS_OK;

@@ -54,6 +54,7 @@ struct Geom {
   int N;
   int P[3];
   int W[3];        // N / P_s (cells per subdomain along s)
+  unsigned Wrcp[3];  // ceil(2^32 / W): c / W = umulhi(c, Wrcp) for 0 <= c < 2^11
   int Ptot;
   double L;
   double inv_dx;   // N / L, one correctly rounded division on the host
@@ -92,7 +93,7 @@ struct StepArgs {
   int64_t cap;       // slots per record buffer
   // float-pair splits (hi, lo) of dt, dt/2, dt*N/L and dt*g for the DF step
   float dfk[12];
-  int step_tile;     // particles per step tile (block size x items per thread)
+  int step_tile;     // particles per step tile (block or warp lanes x items per lane)
 };
 
 // The ensembles of one context, as the batched kernels see them.
@@ -228,14 +229,14 @@ __device__ __forceinline__ void layout_from_counts(int P, int step_tile, const i
 cudaError_t launch_field_convert(const double *src, int N, FieldKind kind, void *dst,
                                  cudaStream_t st);
 template <int CAP>
-cudaError_t launch_step_group(const StepGroup<CAP> &pb, FieldKind kind, int block, int items,
-                              int grid, cudaStream_t st);
+cudaError_t launch_step_group(const StepGroup<CAP> &pb, FieldKind kind, int mode, int block,
+                              int items, int grid, cudaStream_t st);
 cudaError_t launch_finish(const BatchArgs &bt, cudaStream_t st);
 cudaError_t launch_unpack(const BatchArgs &bt, int total_P, cudaStream_t st);
 cudaError_t launch_flip(const BatchArgs &bt, cudaStream_t st);
 cudaError_t launch_field_expand(const void *src, int N, FieldKind kind, double *dst,
                                 cudaStream_t st);
-int step_kernel_occupancy(FieldKind kind, int block, int items);
+int step_kernel_occupancy(FieldKind kind, int mode, int block, int items);
 
 // Adjoint: checkpoint of the live particles (compacted, storage order).
 struct TapeSlot {

@@ -84,6 +84,12 @@ __device__ __forceinline__ long long fix_stage2(long long q1, df V, df cx) {
   return q1 + f_to_fix52(cv.h) + f_to_fix52(cv.l);
 }
 
+// The same for the FP32 increments of FP32 / BF16 storage: q1 + fix(cx V)
+// with cx = dt N/L and V both rounded to FP32.
+__device__ __forceinline__ long long fix_stage2_lo(long long q1, float V, float cx) {
+  return q1 + f_to_fix52(cx * V);
+}
+
 // Predictor position of the FP64 step.
 __device__ __forceinline__ double predictor64(double x, double v, double dt) { return x + dt * v; }
 
@@ -238,6 +244,58 @@ __device__ __forceinline__ void heun_step_df(const StepArgs &a, double x[3], dou
     if (!(fabsf(dX.h) < (float)(0.5 * g.L))) bad |= 2;
     double xn = __dadd_rn(x[s], df_to_double(dX));
     const double vn = __dadd_rn(v[s], df_to_double(dV));
+    const long long bx = __double_as_longlong(xn);
+    if (((bx >> 52) & 0x7ff) == 0x7ff || ((__double_as_longlong(vn) >> 52) & 0x7ff) == 0x7ff)
+      bad |= 1;
+    if (bx < 0) {
+      xn = __dadd_rn(xn, g.L);
+      img[s] -= 1;
+    } else if (bx >= bitsL) {
+      xn = __dsub_rn(xn, g.L);
+      img[s] += 1;
+    }
+    if (__double_as_longlong(xn) == bitsL) xn = 0.0;
+    x[s] = xn;
+    v[s] = vn;
+  }
+}
+
+// Heun step of Eqs. (5)-(6) for FP32 / BF16 field storage: the same
+// formulas as heun_step_df with the increments in FP32 (the field itself
+// carries 2^-24 or 2^-8 relative error), accumulated into the FP64 state
+// X' = X + dX, V' = V + dV; the cell coordinates stay the exact fixed-point
+// ones.
+template <int KIND>
+__device__ __forceinline__ void heun_step_lo(const StepArgs &a, double x[3], double v[3],
+                                             double tau, int img[3], int &bad) {
+  const Geom &g = a.geo;
+  const float dt = a.dfk[0], cx = a.dfk[4];
+  const float h = dt * __frcp_rn(split_d(tau).h);
+  long long q[3];
+  df U[3];
+  float V[3], hD1[3], Vs[3];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) q[s] = fix_stage1(x[s], g.inv_dx);
+  interp_lo<KIND>(a.field, g.N, q, U);
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const float gd = a.dfk[6 + 2 * s];
+    V[s] = split_d(v[s]).h;
+    hD1[s] = h * (U[s].h - V[s]);
+    Vs[s] = V[s] + hD1[s] + gd;
+    q[s] = fix_stage2_lo(q[s], V[s], cx);
+  }
+  interp_lo<KIND>(a.field, g.N, q, U);
+  const long long bitsL = __double_as_longlong(g.L);
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const float gd = a.dfk[6 + 2 * s];
+    const float hD2 = h * (U[s].h - Vs[s]);
+    const float dV = 0.5f * (hD1[s] + hD2) + gd;
+    const float dX = dt * (V[s] + 0.5f * (hD1[s] + gd));
+    if (!(fabsf(dX) < (float)(0.5 * g.L))) bad |= 2;
+    double xn = __dadd_rn(x[s], f2d_bits(dX));
+    const double vn = __dadd_rn(v[s], f2d_bits(dV));
     const long long bx = __double_as_longlong(xn);
     if (((bx >> 52) & 0x7ff) == 0x7ff || ((__double_as_longlong(vn) >> 52) & 0x7ff) == 0x7ff)
       bad |= 1;

@@ -217,7 +217,7 @@ __device__ __forceinline__ int dest_bin(const Geom &g, int seg, const double x[3
     // taken from its fixed-point form without the FP64 floor
     int c = (int)(d_to_fix52(__dmul_rn(x[s], g.inv_dx)) >> 52);
     c = min(max(c, 0), g.N - 1);
-    const int dc = dir_comp(ps[s], c / g.W[s], g.P[s]);
+    const int dc = dir_comp(ps[s], (int)__umulhi((unsigned)c, g.Wrcp[s]), g.P[s]);
     if (dc == 2) return -1;
     bin += (dc + 1) * mul;
     mul *= 3;
@@ -225,25 +225,23 @@ __device__ __forceinline__ int dest_bin(const Geom &g, int seg, const double x[3
   return bin;
 }
 
-struct StepShared {
+struct BlockShared {
   int tile;
   unsigned warp[32];
   unsigned long long excl;
   int hist[NBIN];
 };
 
-// One tile of one ensemble: integrate + wrap + flag its particles, block scan
-// of the (stay, leave) flags, look-back across the segment's earlier tiles,
-// then stayers to their compacted slot in the output buffer and leavers to
-// the pack buffer.  Tile j of segment s covers particles
-// [j*BLOCK*ITEMS, (j+1)*BLOCK*ITEMS) of the segment, ITEMS consecutive ones
-// per thread.
+// One tile of one ensemble, processed by one block: integrate + wrap + flag
+// its particles, block scan of the (stay, leave) flags, look-back across the
+// segment's earlier tiles (by warp 0), then stayers to their compacted slot
+// in the output buffer and leavers to the pack buffer.  Tile j of segment s
+// covers particles [j*BLOCK*ITEMS, (j+1)*BLOCK*ITEMS) of the segment, ITEMS
+// consecutive ones per thread.
 template <int KIND, int BLOCK, int ITEMS>
-__device__ __forceinline__ void step_tile(const StepArgs &a, int ph, int tile, StepShared &sh) {
+__device__ __forceinline__ void step_block_tile(const StepArgs &a, int ph, int tile,
+                                                BlockShared &sh) {
   const Rec A = a.buf[ph], B = a.buf[ph ^ 1];
-  const int64_t *baseA = a.m.lay_base[ph];
-  const int64_t *baseB = a.m.lay_base[ph ^ 1];
-  const int64_t *capB = a.m.lay_cap[ph ^ 1];
   const int P = a.geo.Ptot;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int seg = find_segment(a.m.tile_off, P, tile);
@@ -252,8 +250,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int ph, int tile, S
   const int jt = tile - t0;
   const int64_t cnt = a.m.cnt[seg];
   const int64_t l0 = (int64_t)jt * (BLOCK * ITEMS) + (int64_t)threadIdx.x * ITEMS;
-  const int64_t bA = baseA[seg];
-
+  const int64_t bA = a.m.lay_base[ph][seg];
   double x[ITEMS][3], v[ITEMS][3], tau[ITEMS];
   uint32_t id[ITEMS];
   int img[ITEMS][3], bin[ITEMS];
@@ -261,15 +258,16 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int ph, int tile, S
   int bad = 0;
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k) {
-    bin[k] = -2;  // invalid item
+    bin[k] = -2;
     if (l0 + k < cnt) {
       load_rec(A, bA + l0 + k, x[k], v[k], tau[k], id[k], img[k], a.tau_const);
       if (KIND == FK_F64) heun_step64(a, x[k], v[k], tau[k], img[k], bad);
-      else heun_step_df<KIND>(a, x[k], v[k], tau[k], img[k], bad);
+      else if (KIND == FK_DF) heun_step_df<KIND>(a, x[k], v[k], tau[k], img[k], bad);
+      else heun_step_lo<KIND>(a, x[k], v[k], tau[k], img[k], bad);
       int b = dest_bin(a.geo, seg, x[k]);
       if (b < 0) {
         bad |= 2;
-        b = BIN_STAY;  // keep it in place; the error is latched
+        b = BIN_STAY;
       }
       bin[k] = b;
       if (b == BIN_STAY) {
@@ -282,8 +280,6 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int ph, int tile, S
   }
   if (bad & 1) latch(a.m.status, LCS_ERR_NONFINITE);
   if (bad & 2) latch(a.m.status, LCS_ERR_DISPLACEMENT);
-
-  // block exclusive scan of the packed (stay << 16 | leave) counts
   unsigned incl = packed;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -300,7 +296,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int ph, int tile, S
       const unsigned y = __shfl_up_sync(0xffffffffu, wi, o);
       if (lane >= o) wi += y;
     }
-    if (lane < BLOCK / 32) sh.warp[lane] = wi - wv;  // exclusive warp offsets
+    if (lane < BLOCK / 32) sh.warp[lane] = wi - wv;
     const unsigned tot = __shfl_sync(0xffffffffu, wi, BLOCK / 32 - 1);
     const unsigned long long agg = pack_sm(tot >> 16, tot & 0xffffu);
     const unsigned long long ex = lookback_warp(a.m.tile_status, tile, t0, agg, a.m.status);
@@ -316,11 +312,10 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int ph, int tile, S
   __syncthreads();
   if (threadIdx.x < NBIN && threadIdx.x != BIN_STAY && sh.hist[threadIdx.x])
     atomicAdd(&a.m.bincnt[seg * NBIN + threadIdx.x], sh.hist[threadIdx.x]);
-
   const unsigned excl = incl - packed + sh.warp[warp];
   int64_t stay_pos = (int64_t)(sh.excl >> 31) + (excl >> 16);
   int64_t mig_pos = (int64_t)(sh.excl & ((1ull << 31) - 1)) + (excl & 0xffffu);
-  const int64_t bB = baseB[seg], cB = capB[seg];
+  const int64_t bB = a.m.lay_base[ph ^ 1][seg], cB = a.m.lay_cap[ph ^ 1][seg];
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k) {
     if (bin[k] == -2) continue;
@@ -340,16 +335,12 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int ph, int tile, S
   }
 }
 
-// Persistent step kernel over the tiles of a group of ensembles: tile ids
-// come from one counter in launch order, so within an ensemble every tile's
-// predecessors were taken by running blocks (the look-back cannot wait on a
-// block that has not started).  The group's arguments travel as the kernel's
-// parameter block (constant bank: usable as instruction operands without
-// registers, and never aliased by the kernel's stores).
+// Persistent step kernel with block tiles: blocks take tile ids from one
+// counter in order (predecessors always belong to running blocks).
 template <int KIND, int BLOCK, int ITEMS, int CAP>
 __global__ void __launch_bounds__(BLOCK, 512 / BLOCK)
-    k_step(const __grid_constant__ StepGroup<CAP> pb) {
-  __shared__ StepShared sh;
+    k_step_block(const __grid_constant__ StepGroup<CAP> pb) {
+  __shared__ BlockShared sh;
   __shared__ int s_off[CAP + 1];
   const int n = pb.n;
   if (threadIdx.x == 0) {
@@ -369,33 +360,31 @@ __global__ void __launch_bounds__(BLOCK, 512 / BLOCK)
     const int g = sh.tile;
     if (g >= total) break;
     if (CAP == 1) {
-      step_tile<KIND, BLOCK, ITEMS>(pb.a[0], *pb.a[0].m.phase, g, sh);
+      step_block_tile<KIND, BLOCK, ITEMS>(pb.a[0], *pb.a[0].m.phase, g, sh);
     } else {
-      int e = 0, hi = n;  // s_off[e] <= g < s_off[hi]
+      int e = 0, hi = n;
       while (hi - e > 1) {
         const int mid = (e + hi) >> 1;
         if (s_off[mid] <= g) e = mid; else hi = mid;
       }
-      step_tile<KIND, BLOCK, ITEMS>(pb.a[e], *pb.a[e].m.phase, g - s_off[e], sh);
+      step_block_tile<KIND, BLOCK, ITEMS>(pb.a[e], *pb.a[e].m.phase, g - s_off[e], sh);
     }
     __syncthreads();
   }
 }
 
-#define LCS_STEP_CONFIGS(X, K, C) X(K, 256, 2, C) X(K, 256, 1, C) X(K, 128, 2, C)
-#define LCS_ALL_CONFIGS(X)                                                              \
-  LCS_STEP_CONFIGS(X, FK_F64, 1) LCS_STEP_CONFIGS(X, FK_DF, 1)                          \
-  LCS_STEP_CONFIGS(X, FK_F32, 1) LCS_STEP_CONFIGS(X, FK_BF16, 1)                        \
-  LCS_STEP_CONFIGS(X, FK_F64, GROUP_ENS) LCS_STEP_CONFIGS(X, FK_DF, GROUP_ENS)          \
-  LCS_STEP_CONFIGS(X, FK_F32, GROUP_ENS) LCS_STEP_CONFIGS(X, FK_BF16, GROUP_ENS)
+// (threads per block, particles per thread) configurations the tuner tries
+#define LCS_STEP_CONFIGS(X, K, C) \
+  X(K, k_step_block, 0, 256, 2, C) X(K, k_step_block, 0, 256, 1, C) \
+  X(K, k_step_block, 0, 128, 2, C)
 
 template <int CAP>
-cudaError_t launch_step_group(const StepGroup<CAP> &pb, FieldKind kind, int block, int items,
-                              int grid, cudaStream_t st) {
-#define LCS_LAUNCH(K, B, I, C)                                           \
-  if (C == CAP && kind == K && block == B && items == I) {              \
-    k_step<K, B, I, CAP><<<grid, B, 0, st>>>(pb);                        \
-    return cudaGetLastError();                                           \
+cudaError_t launch_step_group(const StepGroup<CAP> &pb, FieldKind kind, int mode, int block,
+                              int items, int grid, cudaStream_t st) {
+#define LCS_LAUNCH(K, KER, M, B, I, C)                                      \
+  if (kind == K && mode == M && block == B && items == I) {                 \
+    KER<K, B, I, CAP><<<grid, B, 0, st>>>(pb);                              \
+    return cudaGetLastError();                                              \
   }
   LCS_STEP_CONFIGS(LCS_LAUNCH, FK_F64, CAP)
   LCS_STEP_CONFIGS(LCS_LAUNCH, FK_DF, CAP)
@@ -404,17 +393,20 @@ cudaError_t launch_step_group(const StepGroup<CAP> &pb, FieldKind kind, int bloc
 #undef LCS_LAUNCH
   return cudaErrorInvalidValue;
 }
-template cudaError_t launch_step_group<1>(const StepGroup<1> &, FieldKind, int, int, int,
+template cudaError_t launch_step_group<1>(const StepGroup<1> &, FieldKind, int, int, int, int,
                                           cudaStream_t);
 template cudaError_t launch_step_group<GROUP_ENS>(const StepGroup<GROUP_ENS> &, FieldKind, int,
-                                                  int, int, cudaStream_t);
+                                                  int, int, int, cudaStream_t);
 
-int step_kernel_occupancy(FieldKind kind, int block, int items) {
+int step_kernel_occupancy(FieldKind kind, int mode, int block, int items) {
   int n = 0;
-#define LCS_OCC(K, B, I, C)                                                         \
-  if (C == GROUP_ENS && kind == K && block == B && items == I)                      \
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<K, B, I, C>, B, 0);
-  LCS_ALL_CONFIGS(LCS_OCC)
+#define LCS_OCC(K, KER, M, B, I, C)                                                  \
+  if (kind == K && mode == M && block == B && items == I)                            \
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, KER<K, B, I, C>, B, 0);
+  LCS_STEP_CONFIGS(LCS_OCC, FK_F64, GROUP_ENS)
+  LCS_STEP_CONFIGS(LCS_OCC, FK_DF, GROUP_ENS)
+  LCS_STEP_CONFIGS(LCS_OCC, FK_F32, GROUP_ENS)
+  LCS_STEP_CONFIGS(LCS_OCC, FK_BF16, GROUP_ENS)
 #undef LCS_OCC
   return n;
 }
