@@ -186,8 +186,8 @@ def batch_throughput(lcs, torch, steps=500, n_ens=48):
     spec = lambda e, dtype: dict(field=e["field"], x0=e["x0"], v0=e["v0"], dt=e["dt"],
                                  tau=e["tau"], sub=(2, 2, 2), sort_every=10, field_dtype=dtype)
     sim = lcs.Simulator(None, None, None, None, ensembles=[spec(e, "f32") for e in ens])
-    block, items = sim.tune(2)
-    timed(sim, 4)  # the remaining steps of the first sort period
+    block, items, mode = sim.tune(2)  # 16 steps: 8 configurations x 2
+    timed(sim, 4)  # graph capture; the timed steps start on a sort period
     ms_batch = timed(sim, steps)
     launches = sim.launches
     sim.close()
@@ -207,7 +207,7 @@ def batch_throughput(lcs, torch, steps=500, n_ens=48):
             "value_one_by_one_f64": rate(solo["f64"]), "value_one_by_one_f32": rate(solo["f32"]),
             "speedup_vs_one_by_one_f64": round(solo["f64"] / ms_batch, 3),
             "speedup_vs_one_by_one_f32": round(solo["f32"] / ms_batch, 3),
-            "tuned_block": block, "tuned_items": items, "unit": UNIT}
+            "tuned_block": block, "tuned_items": items, "tuned_mode": mode, "unit": UNIT}
 
 
 # ---------------------------------------------------------------- precision variants
@@ -261,6 +261,8 @@ def main():
                     help="also time the 48-ensemble batching workload")
     ap.add_argument("--adjoint", type=int, default=1,
                     help="also time forward (taped) vs backward on grad_128")
+    ap.add_argument("--step-config", default="",
+                    help="threads,items,mode of the step kernel instead of autotuning")
     ap.add_argument("--np", type=int, default=0,
                     help="particle count override (small profiling cases only)")
     args = ap.parse_args()
@@ -286,7 +288,12 @@ def main():
                         field_dtype=args.field, kernel=args.kernel, sort_every=w.sort_every)
     n = x.shape[1]
     K, W = args.steps, args.warmup
-    tuned = sim.tune(2)  # picks the scan tile; advances the state by 6 steps
+    if args.step_config:
+        tuned = tuple(int(t) for t in args.step_config.split(","))
+        sim.set_step_config(*tuned)
+        sim.tune_trials_ms = []
+    else:
+        tuned = sim.tune(2)  # picks the step kernel; advances the state 2 steps per trial
     # the L2 (129 MB) is far smaller than the particle state (~1 GB) and the
     # field (537 MB): every timed step streams its inputs from HBM
     for _ in range(W):
@@ -391,7 +398,7 @@ def main():
                           "sort_every": w.sort_every, "dt": dt,
                           "time_steps_per_bench_step": STEPS_PER_BENCH_STEP,
                           "field_storage": args.field, "kernel": args.kernel,
-                          "tuned_block_items": list(tuned),
+                          "tuned_block_items_mode": list(tuned),
                           "tune_trials_ms": [round(float(t), 3) for t in sim.tune_trials_ms],
                           "l2": "inputs larger than L2 (state ~1 GB, field 0.54 GB)",
                           "parallelism": f"replicas{world}"},

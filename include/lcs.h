@@ -34,6 +34,8 @@
  *     and reported by the next synchronising call (lcs_sync, lcs_get_state,
  *     lcs_backward); once an error is latched the context answers
  *     LCS_ERR_STATE to every call except lcs_last_error and lcs_destroy.
+ *     A call on a live context that refuses its arguments (LCS_ERR_ARG)
+ *     does nothing and latches nothing; the context stays usable.
  *   - A context is not thread safe; all its work is ordered on the stream
  *     given to lcs_init.
  */
@@ -179,15 +181,49 @@ enum {
  * number of launches.  The particle state advances exactly as lcs_step. */
 lcs_status lcs_profile_steps(lcs_ctx *ctx, int64_t nsteps, double *ms, int64_t *count);
 
-/* Autotuner: time every step-kernel configuration (threads per block x
- * particles per thread, i.e. the scan tile: 256x2, 256x1, 128x2) on
- * steps_per_trial real steps of all ensembles, keep the fastest, and
- * rebuild the step graphs with it.  The trial steps advance the simulation
- * (3 * steps_per_trial steps in all, recorded like any other step); results
- * do not depend on the choice.  *block and *items (may be NULL) receive the
- * choice; trial_ms (host, 3 doubles, may be NULL) the step-kernel
- * milliseconds of each configuration in that order.  Synchronising. */
-lcs_status lcs_tune(lcs_ctx *ctx, int steps_per_trial, int *block, int *items, double *trial_ms);
+/* Step-kernel modes (all give identical results):
+ *   LCS_STEP_PLAIN          records and field read from global memory;
+ *   LCS_STEP_STAGED_FIELD   each tile first copies the box of field cells
+ *                           around its particles into shared memory (64 KB;
+ *                           a tile whose box is larger reads global memory);
+ *                           not available with LCS_KERNEL_FP64;
+ *   LCS_STEP_PREFETCH       the records of a block's next tile are brought
+ *                           into shared memory by bulk asynchronous copies
+ *                           while the current tile is processed. */
+#define LCS_STEP_PLAIN 0
+#define LCS_STEP_STAGED_FIELD 1
+#define LCS_STEP_PREFETCH 2
+
+/* Number of step-kernel configurations lcs_tune tries. */
+#define LCS_TUNE_CONFIGS 8
+
+/* Autotuner: time every step-kernel configuration on steps_per_trial real
+ * steps of all ensembles, keep the fastest, and rebuild the step graphs with
+ * it.  The configurations, in order, as (threads per block, particles per
+ * thread, mode): (256,2,0) (256,1,0) (128,2,0) (256,2,1) (128,2,1)
+ * (256,2,2) (128,2,2) (256,1,2).  The first two numbers fix the scan tile.
+ * Configurations of mode LCS_STEP_STAGED_FIELD are skipped for the all-FP64
+ * kernel.  The trial steps advance the simulation (steps_per_trial steps per
+ * tried configuration, recorded like any other step); results do not depend
+ * on the choice.  *block, *items, *mode (may be NULL) receive the choice;
+ * trial_ms (host, LCS_TUNE_CONFIGS doubles, may be NULL) the step-kernel
+ * milliseconds of each configuration in that order, -1 for one skipped.
+ * Synchronising. */
+lcs_status lcs_tune(lcs_ctx *ctx, int steps_per_trial, int *block, int *items, int *mode,
+                    double *trial_ms);
+
+/* Select one of the LCS_TUNE_CONFIGS step-kernel configurations by hand
+ * (the values lcs_tune chooses among); the step graphs are rebuilt.
+ * Results do not depend on the choice.  LCS_ERR_ARG for a combination not
+ * in the list, or mode LCS_STEP_STAGED_FIELD with the all-FP64 kernel.
+ * Synchronising. */
+lcs_status lcs_set_step_config(lcs_ctx *ctx, int block, int items, int mode);
+
+/* Number of step tiles, summed over the ensembles since lcs_init, whose
+ * field cells were read from a shared-memory box (LCS_STEP_STAGED_FIELD
+ * only; tiles whose box did not fit read global memory and are not
+ * counted).  *count is host memory.  Synchronising. */
+lcs_status lcs_staged_tiles(lcs_ctx *ctx, int64_t *count);
 
 /* Wait for all enqueued work; return the latched device status. */
 lcs_status lcs_sync(lcs_ctx *ctx);

@@ -24,6 +24,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "liblcs.so")
 
 LCS_OK, LCS_ERR_ARG, LCS_ERR_CUDA, LCS_ERR_OOM, LCS_ERR_CAPACITY = 0, 1, 2, 3, 4
 LCS_ERR_TIMEOUT, LCS_ERR_NONFINITE, LCS_ERR_DISPLACEMENT, LCS_ERR_STATE = 5, 6, 7, 8
+LCS_TUNE_CONFIGS = 8  # step-kernel configurations lcs_tune tries
+STEP_PLAIN, STEP_STAGED_FIELD, STEP_PREFETCH = 0, 1, 2  # step-kernel modes
 STATUS_NAMES = {0: "LCS_OK", 1: "LCS_ERR_ARG", 2: "LCS_ERR_CUDA", 3: "LCS_ERR_OOM",
                 4: "LCS_ERR_CAPACITY", 5: "LCS_ERR_TIMEOUT", 6: "LCS_ERR_NONFINITE",
                 7: "LCS_ERR_DISPLACEMENT", 8: "LCS_ERR_STATE"}
@@ -34,7 +36,7 @@ KERNELS = {"auto": 0, "fp64": 1, "df": 2}
 EXPORTS = ("lcs_init", "lcs_step", "lcs_migrate", "lcs_sort", "lcs_set_state", "lcs_get_state",
            "lcs_get_field", "lcs_backward", "lcs_sync", "lcs_last_error", "lcs_destroy",
            "lcs_launch_count", "lcs_partition", "lcs_profile_steps", "lcs_partition_noalloc",
-           "lcs_tune")
+           "lcs_tune", "lcs_set_step_config", "lcs_staged_tiles")
 PARTITION_NOALLOC_MAX_N = 1 << 20
 PROF_CLASSES = ("step", "finish", "unpack", "flip", "sort")
 
@@ -84,10 +86,13 @@ def lib():
         L.lcs_partition.argtypes = [P, i64, i32, P, P, P, P]
         L.lcs_profile_steps.argtypes = [P, i64, P, P]
         L.lcs_partition_noalloc.argtypes = [P, i64, i32, P, P, P, P]
-        L.lcs_tune.argtypes = [P, i32, P, P, P]
+        L.lcs_tune.argtypes = [P, i32, P, P, P, P]
+        L.lcs_set_step_config.argtypes = [P, i32, i32, i32]
+        L.lcs_staged_tiles.argtypes = [P, P]
         for name in ("lcs_init", "lcs_step", "lcs_migrate", "lcs_sort", "lcs_set_state",
                      "lcs_get_state", "lcs_get_field", "lcs_backward", "lcs_sync",
-                     "lcs_partition", "lcs_profile_steps", "lcs_partition_noalloc", "lcs_tune"):
+                     "lcs_partition", "lcs_profile_steps", "lcs_partition_noalloc", "lcs_tune",
+                     "lcs_set_step_config", "lcs_staged_tiles"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -212,14 +217,28 @@ class Simulator:
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(PROF_CLASSES)}
 
     def tune(self, steps_per_trial: int = 2):
-        """Autotune the step kernel's scan tile (advances the simulation by
-        3 * steps_per_trial steps); returns (threads per block, items per thread)."""
-        b, it = C.c_int(), C.c_int()
-        ms = np.zeros(3, dtype=np.float64)
+        """Autotune the step kernel (scan tile and kernel mode); advances the
+        simulation by steps_per_trial steps per tried configuration.  Returns
+        (threads per block, items per thread, mode); the step-kernel
+        milliseconds of every configuration are kept in tune_trials_ms (-1
+        where skipped)."""
+        b, it, md = C.c_int(), C.c_int(), C.c_int()
+        ms = np.zeros(LCS_TUNE_CONFIGS, dtype=np.float64)
         self._check(lib().lcs_tune(self._ctx, int(steps_per_trial), C.byref(b), C.byref(it),
-                                   _ptr(ms)))
+                                   C.byref(md), _ptr(ms)))
         self.tune_trials_ms = ms
-        return b.value, it.value
+        return b.value, it.value, md.value
+
+    def set_step_config(self, block: int, items: int, mode: int = STEP_PLAIN):
+        """Pin one of the step-kernel configurations lcs_tune chooses among."""
+        self._check(lib().lcs_set_step_config(self._ctx, int(block), int(items), int(mode)))
+
+    @property
+    def staged_tiles(self) -> int:
+        """Step tiles so far whose field cells came from a shared-memory box."""
+        n = C.c_int64()
+        self._check(lib().lcs_staged_tiles(self._ctx, C.byref(n)))
+        return n.value
 
     @property
     def launches(self) -> int:

@@ -72,7 +72,8 @@ struct lcs_ctx {
   int sms = 152;
   // batched step over all ensembles (one launch per kernel per step)
   FieldKind kind = FK_F64;
-  int mode = 0;                 // step kernel variant (one: block tiles)
+  int mode = 0;                 // step kernel: 0 plain, 1 staged field box, 2 prefetched records
+  bool pf_tau = false, pf_img = false;  // some ensemble has per-particle tau / images
   int block = 256, items = 2;   // threads per block, particles per thread (autotuned)
   int step_grid = 1, total_P = 0;
   int64_t total_tiles = 0;      // sum of the ensembles' look-back array sizes
@@ -98,6 +99,14 @@ lcs_status fail(lcs_ctx *c, lcs_status s, const std::string &msg) {
   return s;
 }
 
+// An argument error of a call on a live context: the call does nothing and
+// the context stays usable (no error is latched).
+lcs_status reject(lcs_ctx *c, const std::string &msg) {
+  c->err = msg;
+  g_last_init_error = msg;
+  return LCS_ERR_ARG;
+}
+
 #define CK(call)                                                                          \
   do {                                                                                    \
     cudaError_t e_ = (call);                                                              \
@@ -117,7 +126,10 @@ cudaError_t dalloc(lcs_ctx *c, T **p, int64_t n) {
   return e;
 }
 
+// Record arrays get 4 elements (>= 16 bytes) of slack: the step kernel's bulk
+// copies round a tile's rows out to 16-byte boundaries.
 lcs_status alloc_rec(lcs_ctx *c, Rec &r, int64_t cap, bool has_tau, bool has_img) {
+  cap += 4;
   for (int s = 0; s < 3; ++s) {
     CK(dalloc(c, &r.x[s], cap));
     CK(dalloc(c, &r.v[s], cap));
@@ -174,18 +186,23 @@ lcs_status launch_steps(lcs_ctx *c, cudaStream_t st) {
   static thread_local StepGroup<GROUP_ENS> big;
   for (size_t gi = 0; gi < c->groups.size(); ++gi) {
     const int first = c->groups[gi].first, cnt = c->groups[gi].second;
-    const int occ = std::max(1, step_kernel_occupancy(c->kind, c->mode, c->block, c->items));
+    const int occ = std::max(
+        1, step_kernel_occupancy(c->kind, c->mode, c->block, c->items, c->pf_tau, c->pf_img));
     const int grid = (int)std::max<int64_t>(
         1, std::min<int64_t>(c->group_tiles[gi], (int64_t)occ * c->sms));
     if (cnt == 1) {
       StepGroup<1> one;
       one.a[0] = c->ens[first].a;
       one.n = 1;
+      one.pf_tau = c->pf_tau;
+      one.pf_img = c->pf_img;
       one.counter = c->d_counter + gi;
       CK(launch_step_group<1>(one, c->kind, c->mode, c->block, c->items, grid, st));
     } else {
       for (int k = 0; k < cnt; ++k) big.a[k] = c->ens[first + k].a;
       big.n = cnt;
+      big.pf_tau = c->pf_tau;
+      big.pf_img = c->pf_img;
       big.counter = c->d_counter + gi;
       CK(launch_step_group<GROUP_ENS>(big, c->kind, c->mode, c->block, c->items, grid, st));
     }
@@ -367,9 +384,12 @@ lcs_status setup_batch(lcs_ctx *c) {
   const int n = (int)c->ens.size();
   if (n > MAX_ENS) return fail(c, LCS_ERR_ARG, "too many ensembles in one context");
   c->kind = c->ens[0].kind;
-  for (auto &e : c->ens)
+  for (auto &e : c->ens) {
     if (e.kind != c->kind)
       return fail(c, LCS_ERR_ARG, "all ensembles of a context need the same field storage");
+    c->pf_tau |= e.a.buf[0].tau != nullptr;
+    c->pf_img |= e.a.buf[0].img[0] != nullptr;
+  }
   c->total_tiles = 0;
   c->total_P = 0;
   std::vector<int> poff(n + 1, 0);
@@ -511,6 +531,7 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
     A(dalloc(c, &m.phase, 1));
     A(dalloc(c, &m.status, 1));
     A(dalloc(c, &m.tile_counter, 1));
+    A(dalloc(c, &m.staged, 1));
     A(dalloc(c, &m.bincnt, (int64_t)P * NBIN));
     A(dalloc(c, &m.off_in, (int64_t)P * NBIN));
     A(dalloc(c, &m.stay_tot, P));
@@ -543,6 +564,7 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
     };
     C2(cudaMemsetAsync(m.status, 0, sizeof(int), st));
     C2(cudaMemsetAsync(m.tile_counter, 0, sizeof(unsigned), st));
+    C2(cudaMemsetAsync(m.staged, 0, sizeof(unsigned long long), st));
     C2(cudaMemsetAsync(m.bincnt, 0, sizeof(int) * P * NBIN, st));
     C2(cudaMemsetAsync(m.stay_tot, 0, sizeof(int64_t) * P, st));
     C2(cudaMemsetAsync(m.mig_tot, 0, sizeof(int64_t) * P, st));
@@ -598,7 +620,7 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
 lcs_status lcs_step(lcs_ctx *c, int64_t nsteps) {
   lcs_status r = check_ctx(c);
   if (r != LCS_OK) return r;
-  if (nsteps < 0) return fail(c, LCS_ERR_ARG, "nsteps < 0");
+  if (nsteps < 0) return reject(c, "nsteps < 0");
   if (nsteps == 0) return LCS_OK;
   for (int64_t k = 0; k < nsteps; ++k) {
     // all ensembles of a context share the step count
@@ -649,13 +671,15 @@ lcs_status lcs_set_state(lcs_ctx *c, int ens, const double *x, const double *v,
   lcs_status r = check_ctx(c);
   if (r != LCS_OK) return r;
   if (ens < 0 || ens >= (int)c->ens.size() || !x || !v || !ids || !seg)
-    return fail(c, LCS_ERR_ARG, "lcs_set_state: bad argument");
+    return reject(c, "lcs_set_state: bad argument");
   Ens &e = c->ens[ens];
   const int P = e.a.geo.Ptot;
-  if (seg[0] != 0 || seg[P] != e.np) return fail(c, LCS_ERR_ARG, "lcs_set_state: bad segments");
-  e.tape_ok = false;  // the recorded trajectory no longer leads to this state
+  if (seg[0] != 0 || seg[P] != e.np) return reject(c, "lcs_set_state: bad segments");
   for (int s = 0; s < P; ++s)
-    if (seg[s + 1] < seg[s]) return fail(c, LCS_ERR_ARG, "lcs_set_state: bad segments");
+    if (seg[s + 1] < seg[s]) return reject(c, "lcs_set_state: bad segments");
+  if (e.a.buf[1].tau && e.np > 0 && !tau)
+    return reject(c, "lcs_set_state: tau required (per-particle tau_p)");
+  e.tape_ok = false;  // the recorded trajectory no longer leads to this state
   cudaStream_t st = c->st;
   // Place into buffer 1 with the given segments as windows; a relayout copy
   // moves it to the other buffer with a fresh layout.
@@ -669,7 +693,6 @@ lcs_status lcs_set_state(lcs_ctx *c, int ens, const double *x, const double *v,
     }
   }
   if (B1.tau && e.np > 0) {
-    if (!tau) return fail(c, LCS_ERR_ARG, "lcs_set_state: tau required (per-particle tau_p)");
     CK(cudaMemcpyAsync(B1.tau, tau, e.np * 8, cudaMemcpyDefault, st));
   }
   if (e.np > 0) CK(cudaMemcpyAsync(B1.id, ids, e.np * 4, cudaMemcpyDefault, st));
@@ -693,7 +716,7 @@ lcs_status lcs_get_state(lcs_ctx *c, int ens, double *x, double *v, double *tau,
                          uint32_t *ids, int32_t *img, int64_t *seg) {
   if (!c) return LCS_ERR_ARG;
   if (c->failed) return LCS_ERR_STATE;
-  if (ens < 0 || ens >= (int)c->ens.size()) return fail(c, LCS_ERR_ARG, "bad ensemble");
+  if (ens < 0 || ens >= (int)c->ens.size()) return reject(c, "bad ensemble");
   Ens &e = c->ens[ens];
   cudaStream_t st = c->st;
   const int P = e.a.geo.Ptot;
@@ -736,7 +759,7 @@ lcs_status lcs_get_state(lcs_ctx *c, int ens, double *x, double *v, double *tau,
 lcs_status lcs_get_field(lcs_ctx *c, int ens, double *out) {
   lcs_status r = check_ctx(c);
   if (r != LCS_OK) return r;
-  if (ens < 0 || ens >= (int)c->ens.size() || !out) return fail(c, LCS_ERR_ARG, "bad argument");
+  if (ens < 0 || ens >= (int)c->ens.size() || !out) return reject(c, "bad argument");
   Ens &e = c->ens[ens];
   const int64_t ncell = (int64_t)e.d.n * e.d.n * e.d.n;
   double *tmp = nullptr;
@@ -753,13 +776,13 @@ lcs_status lcs_backward(lcs_ctx *c, const double *gx, const double *gv, double *
                         double *gx0, double *gv0) {
   lcs_status r = check_ctx(c);
   if (r != LCS_OK) return r;
-  if (c->ens.size() != 1) return fail(c, LCS_ERR_ARG, "lcs_backward: one ensemble only");
+  if (c->ens.size() != 1) return reject(c, "lcs_backward: one ensemble only");
   Ens &e = c->ens[0];
   const int K = e.d.ckpt_every;
   if (K <= 0 || !e.d.track_images || !e.tape_ok)
-    return fail(c, LCS_ERR_ARG, "lcs_backward: needs ckpt_every > 0, track_images = 1 and no "
-                                "lcs_set_state since lcs_init");
-  if (!gx || !gv || !gU || !gx0 || !gv0) return fail(c, LCS_ERR_ARG, "lcs_backward: null pointer");
+    return reject(c, "lcs_backward: needs ckpt_every > 0, track_images = 1 and no "
+                     "lcs_set_state since lcs_init");
+  if (!gx || !gv || !gU || !gx0 || !gv0) return reject(c, "lcs_backward: null pointer");
   const int64_t np = e.np, T = e.steps;
   cudaStream_t st = c->st;
   if (!e.lam_id) {
@@ -792,7 +815,7 @@ lcs_status lcs_backward(lcs_ctx *c, const double *gx, const double *gv, double *
 lcs_status lcs_profile_steps(lcs_ctx *c, int64_t nsteps, double *ms, int64_t *count) {
   lcs_status r = check_ctx(c);
   if (r != LCS_OK) return r;
-  if (nsteps < 0 || !ms) return fail(c, LCS_ERR_ARG, "lcs_profile_steps: bad argument");
+  if (nsteps < 0 || !ms) return reject(c, "lcs_profile_steps: bad argument");
   for (int k = 0; k < LCS_PROF_N; ++k) {
     ms[k] = 0.0;
     if (count) count[k] = 0;
@@ -828,17 +851,57 @@ lcs_status lcs_profile_steps(lcs_ctx *c, int64_t nsteps, double *ms, int64_t *co
   return read_status(c);
 }
 
-lcs_status lcs_tune(lcs_ctx *c, int steps_per_trial, int *block, int *items, double *trial_ms) {
+// Step-kernel configurations: (threads per block, particles per thread, kernel mode)
+static const int kStepConfigs[LCS_TUNE_CONFIGS][3] = {
+    {256, 2, 0}, {256, 1, 0}, {128, 2, 0}, {256, 2, 1}, {128, 2, 1},
+    {256, 2, 2}, {128, 2, 2}, {256, 1, 2}};
+
+lcs_status lcs_set_step_config(lcs_ctx *c, int block, int items, int mode) {
   lcs_status r = check_ctx(c);
   if (r != LCS_OK) return r;
-  if (steps_per_trial < 1) return fail(c, LCS_ERR_ARG, "lcs_tune: steps_per_trial < 1");
-  // (threads per block, particles per thread)
-  static const int cfg[][2] = {{256, 2}, {256, 1}, {128, 2}};
+  bool known = false;
+  for (const auto &k : kStepConfigs) known |= k[0] == block && k[1] == items && k[2] == mode;
+  if (!known || (mode == LCS_STEP_STAGED_FIELD && c->kind == FK_F64))
+    return reject(c, "lcs_set_step_config: configuration not available");
+  CK(cudaStreamSynchronize(c->st));
+  c->block = block;
+  c->items = items;
+  c->mode = mode;
+  r = retile(c);
+  if (r != LCS_OK) return r;
+  drop_graphs(c);
+  return read_status(c);
+}
+
+lcs_status lcs_staged_tiles(lcs_ctx *c, int64_t *count) {
+  lcs_status r = check_ctx(c);
+  if (r != LCS_OK) return r;
+  if (!count) return reject(c, "lcs_staged_tiles: count is NULL");
+  CK(cudaStreamSynchronize(c->st));
+  int64_t tot = 0;
+  for (auto &e : c->ens) {
+    unsigned long long v = 0;
+    CK(cudaMemcpy(&v, e.a.m.staged, sizeof(v), cudaMemcpyDeviceToHost));
+    tot += (int64_t)v;
+  }
+  *count = tot;
+  return read_status(c);
+}
+
+lcs_status lcs_tune(lcs_ctx *c, int steps_per_trial, int *block, int *items, int *mode,
+                    double *trial_ms) {
+  lcs_status r = check_ctx(c);
+  if (r != LCS_OK) return r;
+  if (steps_per_trial < 1) return reject(c, "lcs_tune: steps_per_trial < 1");
+  const auto &cfg = kStepConfigs;
   double best = 1e300;
   int bi = 0;
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < LCS_TUNE_CONFIGS; ++k) {
+    if (trial_ms) trial_ms[k] = -1.0;
+    if (cfg[k][2] == LCS_STEP_STAGED_FIELD && c->kind == FK_F64) continue;  // no FP64 form
     c->block = cfg[k][0];
     c->items = cfg[k][1];
+    c->mode = cfg[k][2];
     r = retile(c);
     if (r != LCS_OK) return r;
     double ms[LCS_PROF_N];
@@ -852,11 +915,13 @@ lcs_status lcs_tune(lcs_ctx *c, int steps_per_trial, int *block, int *items, dou
   }
   c->block = cfg[bi][0];
   c->items = cfg[bi][1];
+  c->mode = cfg[bi][2];
   r = retile(c);
   if (r != LCS_OK) return r;
   drop_graphs(c);  // graphs recorded with the old configuration are rebuilt
   if (block) *block = c->block;
   if (items) *items = c->items;
+  if (mode) *mode = c->mode;
   return LCS_OK;
 }
 

@@ -28,6 +28,7 @@ constexpr int NBIN = 27;          // neighbour directions including (0,0,0)
 constexpr int BIN_STAY = 13;      // (0,0,0)
 constexpr int SLACK_MIN = 128;
 constexpr int MAX_ENS = 4096;    // ensembles per context
+constexpr int STAGE_BYTES = 65536;  // shared-memory box of the staged step kernel
 constexpr int SORT_BLOCK = 256;
 constexpr int SORT_ITEMS = 16;
 constexpr int SORT_TILE = SORT_BLOCK * SORT_ITEMS;  // 4096
@@ -49,6 +50,11 @@ struct Rec {
 
 // Field storage kinds.
 enum FieldKind { FK_F64 = 0, FK_DF = 1, FK_F32 = 2, FK_BF16 = 3 };
+
+// Bytes of one cell (three velocity components plus padding) of the field copy.
+__host__ __device__ constexpr int cell_bytes(int kind) {
+  return kind == FK_BF16 ? 8 : kind == FK_F32 ? 16 : 32;
+}
 
 struct Geom {
   int N;
@@ -78,6 +84,7 @@ struct Meta {
   int64_t *off_in;       // offset of (source, direction) in its dest [Ptot*27]
   int64_t *stay_tot;     // stayers per segment                       [Ptot]
   int64_t *mig_tot;      // migrants per segment                      [Ptot]
+  unsigned long long *staged;  // step tiles served from a shared-memory field box [1]
 };
 
 struct StepArgs {
@@ -112,6 +119,7 @@ template <int CAP>
 struct StepGroup {
   StepArgs a[CAP];
   int n;
+  int pf_tau, pf_img;  // record rows present in some ensemble (prefetch layout)
   unsigned int *counter;
 };
 static_assert(sizeof(StepGroup<GROUP_ENS>) <= 32764, "kernel parameter block too large");
@@ -236,7 +244,8 @@ cudaError_t launch_unpack(const BatchArgs &bt, int total_P, cudaStream_t st);
 cudaError_t launch_flip(const BatchArgs &bt, cudaStream_t st);
 cudaError_t launch_field_expand(const void *src, int N, FieldKind kind, double *dst,
                                 cudaStream_t st);
-int step_kernel_occupancy(FieldKind kind, int mode, int block, int items);
+int step_kernel_occupancy(FieldKind kind, int mode, int block, int items, bool pf_tau,
+                          bool pf_img);
 
 // Adjoint: checkpoint of the live particles (compacted, storage order).
 struct TapeSlot {

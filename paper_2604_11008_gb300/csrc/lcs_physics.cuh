@@ -72,6 +72,25 @@ __device__ __forceinline__ void interp64(const void *field, const Geom &g, doubl
   u = au, v = av, w = aw;
 }
 
+// Shared-memory copy of a box of field cells for the sorted gather: cells
+// [ox, ox+nx) x [oy, oy+ny) x [oz, oz+nz) in unwrapped cell coordinates
+// (i = -2 .. N+1), records laid out as in global memory, x fastest.
+// s == nullptr means no staged box.
+struct FieldBox {
+  const void *s;
+  int ox, oy, oz, nx, ny, nz;
+};
+
+// Cell offset of corner (0,0,0) of a stencil inside the box, or -1.
+__device__ __forceinline__ int box_base(const FieldBox &b, int i0, int j0, int k0) {
+  if (!b.s) return -1;
+  const int li = i0 - b.ox, lj = j0 - b.oy, lk = k0 - b.oz;
+  if ((unsigned)li >= (unsigned)(b.nx - 1) || (unsigned)lj >= (unsigned)(b.ny - 1) ||
+      (unsigned)lk >= (unsigned)(b.nz - 1))
+    return -1;
+  return (lk * b.ny + lj) * b.nx + li;
+}
+
 // Fixed-point (52 fraction bits) coordinate x N/L of the first stage: one
 // correctly rounded FP64 product, then bit operations.
 __device__ __forceinline__ long long fix_stage1(double x, double inv_dx) {
@@ -112,8 +131,9 @@ __device__ __forceinline__ df mul_un(df a, df b) {
 // weight-times-value product is split exactly (fma error), the high parts
 // are summed with two_sum and every small term goes to a compensation sum.
 __device__ __forceinline__ void interp_df(const float4 *__restrict__ f, int N,
-                                          const long long q[3], df U[3]) {
+                                          const long long q[3], df U[3], const FieldBox &box) {
   const Axis ax = axis_from_fix(q[0]), ay = axis_from_fix(q[1]), az = axis_from_fix(q[2]);
+  const int sb = box_base(box, ax.i0, ay.i0, az.i0);
   const int i0 = wrap_cell(ax.i0, N), j0 = wrap_cell(ay.i0, N), k0 = wrap_cell(az.i0, N);
   const int i1 = i0 + 1 == N ? 0 : i0 + 1, j1 = j0 + 1 == N ? 0 : j0 + 1,
             k1 = k0 + 1 == N ? 0 : k0 + 1;
@@ -132,8 +152,14 @@ __device__ __forceinline__ void interp_df(const float4 *__restrict__ f, int N,
 #pragma unroll
       for (int d = 0; d < 2; ++d) {
         const df w = mul_un(wab, wz[d]);
-        const size_t cell = (size_t)(ii[a] + jj[b] + kk[d]);
-        const float4 A = __ldg(f + 2 * cell), B = __ldg(f + 2 * cell + 1);
+        float4 A, B;
+        if (sb >= 0) {
+          const float4 *sm = (const float4 *)box.s + 2 * (sb + a + box.nx * (b + box.ny * d));
+          A = sm[0], B = sm[1];
+        } else {
+          const size_t cell = (size_t)(ii[a] + jj[b] + kk[d]);
+          A = __ldg(f + 2 * cell), B = __ldg(f + 2 * cell + 1);
+        }
         const float hv[3] = {A.x, A.y, A.z}, lv[3] = {A.w, B.x, B.y};
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -162,8 +188,9 @@ __device__ __forceinline__ void interp_df(const float4 *__restrict__ f, int N,
 // from the fixed-point coordinates rounded to FP32, FP32 accumulation.
 template <int KIND>
 __device__ __forceinline__ void interp_lo(const void *__restrict__ field, int N,
-                                          const long long q[3], df U[3]) {
+                                          const long long q[3], df U[3], const FieldBox &box) {
   const Axis ax = axis_from_fix(q[0]), ay = axis_from_fix(q[1]), az = axis_from_fix(q[2]);
+  const int sb = box_base(box, ax.i0, ay.i0, az.i0);
   const int i0 = wrap_cell(ax.i0, N), j0 = wrap_cell(ay.i0, N), k0 = wrap_cell(az.i0, N);
   const int i1 = i0 + 1 == N ? 0 : i0 + 1, j1 = j0 + 1 == N ? 0 : j0 + 1,
             k1 = k0 + 1 == N ? 0 : k0 + 1;
@@ -184,12 +211,13 @@ __device__ __forceinline__ void interp_lo(const void *__restrict__ field, int N,
       for (int d = 0; d < 2; ++d) {
         const float w = __fmul_rn(wab, wz[d]);
         const uint32_t cell = ii[a] + jj[b] + kk[d];
+        const int sc = sb + a + box.nx * (b + box.ny * d);
         float f[3];
         if (KIND == FK_F32) {
-          const float4 p = __ldg((const float4 *)field + cell);
+          const float4 p = sb >= 0 ? ((const float4 *)box.s)[sc] : __ldg((const float4 *)field + cell);
           f[0] = p.x, f[1] = p.y, f[2] = p.z;
         } else {
-          const uint2 p = __ldg((const uint2 *)field + cell);
+          const uint2 p = sb >= 0 ? ((const uint2 *)box.s)[sc] : __ldg((const uint2 *)field + cell);
           f[0] = __uint_as_float((p.x & 0xffffu) << 16);
           f[1] = __uint_as_float(p.x & 0xffff0000u);
           f[2] = __uint_as_float((p.y & 0xffffu) << 16);
@@ -204,9 +232,9 @@ __device__ __forceinline__ void interp_lo(const void *__restrict__ field, int N,
 
 template <int KIND>
 __device__ __forceinline__ void interp_any(const void *field, int N, const long long q[3],
-                                           df U[3]) {
-  if (KIND == FK_DF) interp_df((const float4 *)field, N, q, U);
-  else interp_lo<KIND>(field, N, q, U);
+                                           df U[3], const FieldBox &box) {
+  if (KIND == FK_DF) interp_df((const float4 *)field, N, q, U, box);
+  else interp_lo<KIND>(field, N, q, U, box);
 }
 
 // Heun step of Eqs. (5)-(6) (f = 1, gravity g) with float-float increments:
@@ -216,7 +244,8 @@ __device__ __forceinline__ void interp_any(const void *field, int N, const long 
 // then X' = X + dX and V' = V + dV in FP64, and the periodic wrap.
 template <int KIND>
 __device__ __forceinline__ void heun_step_df(const StepArgs &a, double x[3], double v[3],
-                                             double tau, int img[3], int &bad) {
+                                             double tau, int img[3], int &bad,
+                                             const FieldBox &box = FieldBox{}) {
   const Geom &g = a.geo;
   const df dt = {a.dfk[0], a.dfk[1]}, hdt = {a.dfk[2], a.dfk[3]}, cx = {a.dfk[4], a.dfk[5]};
   const df h = df_mul(dt, df_recip(split_d(tau)));
@@ -224,7 +253,7 @@ __device__ __forceinline__ void heun_step_df(const StepArgs &a, double x[3], dou
   df V[3], U[3], hD1[3], Vs[3];
 #pragma unroll
   for (int s = 0; s < 3; ++s) q[s] = fix_stage1(x[s], g.inv_dx);
-  interp_any<KIND>(a.field, g.N, q, U);
+  interp_any<KIND>(a.field, g.N, q, U, box);
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     const df gd = {a.dfk[6 + 2 * s], a.dfk[7 + 2 * s]};
@@ -233,7 +262,7 @@ __device__ __forceinline__ void heun_step_df(const StepArgs &a, double x[3], dou
     Vs[s] = df_add(df_add(V[s], hD1[s]), gd);
     q[s] = fix_stage2(q[s], V[s], cx);
   }
-  interp_any<KIND>(a.field, g.N, q, U);
+  interp_any<KIND>(a.field, g.N, q, U, box);
   const long long bitsL = __double_as_longlong(g.L);
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
@@ -267,7 +296,8 @@ __device__ __forceinline__ void heun_step_df(const StepArgs &a, double x[3], dou
 // ones.
 template <int KIND>
 __device__ __forceinline__ void heun_step_lo(const StepArgs &a, double x[3], double v[3],
-                                             double tau, int img[3], int &bad) {
+                                             double tau, int img[3], int &bad,
+                                             const FieldBox &box = FieldBox{}) {
   const Geom &g = a.geo;
   const float dt = a.dfk[0], cx = a.dfk[4];
   const float h = dt * __frcp_rn(split_d(tau).h);
@@ -276,7 +306,7 @@ __device__ __forceinline__ void heun_step_lo(const StepArgs &a, double x[3], dou
   float V[3], hD1[3], Vs[3];
 #pragma unroll
   for (int s = 0; s < 3; ++s) q[s] = fix_stage1(x[s], g.inv_dx);
-  interp_lo<KIND>(a.field, g.N, q, U);
+  interp_lo<KIND>(a.field, g.N, q, U, box);
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     const float gd = a.dfk[6 + 2 * s];
@@ -285,7 +315,7 @@ __device__ __forceinline__ void heun_step_lo(const StepArgs &a, double x[3], dou
     Vs[s] = V[s] + hD1[s] + gd;
     q[s] = fix_stage2_lo(q[s], V[s], cx);
   }
-  interp_lo<KIND>(a.field, g.N, q, U);
+  interp_lo<KIND>(a.field, g.N, q, U, box);
   const long long bitsL = __double_as_longlong(g.L);
 #pragma unroll
   for (int s = 0; s < 3; ++s) {

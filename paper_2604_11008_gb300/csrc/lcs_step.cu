@@ -17,6 +17,7 @@
 #include <cuda/atomic>
 
 #include "lcs_physics.cuh"
+#include "lcs_tma.cuh"
 
 namespace lcs {
 
@@ -163,6 +164,8 @@ __device__ unsigned long long lookback_warp(unsigned long long *status_arr, int 
         if (lane == 0) latch(err, LCS_ERR_TIMEOUT);
         break;
       }
+      // an error latched elsewhere (e.g. a block that gave up) ends the wait
+      if ((spins & 63) == 0 && *(volatile int *)err == LCS_ERR_TIMEOUT) break;
       __nanosleep(ns);
       ns = ns < 256 ? ns * 2 : 256;
       continue;
@@ -228,42 +231,213 @@ __device__ __forceinline__ int dest_bin(const Geom &g, int seg, const double x[3
 struct BlockShared {
   int tile;
   unsigned warp[32];
+  unsigned tot;
   unsigned long long excl;
   int hist[NBIN];
+  int blo[32][3], bhi[32][3];  // per-warp bounding boxes (staged variant)
 };
+
+// Placement of one tile of one ensemble.  Tile j of segment s covers
+// particles [j*T, (j+1)*T) of the segment (T = BLOCK*ITEMS), ITEMS
+// consecutive ones per thread.
+struct TileMeta {
+  int gtile;      // tile id across the launch's ensembles
+  int e;          // ensemble index within the launch
+  int tile;       // tile id within the ensemble
+  int seg, t0, ntile, ph;
+  int n;          // particles in the tile (0..T)
+  int o8, o4;     // position of the tile's first particle in its prefetched 8- / 4-byte rows
+  int64_t cnt;    // live particles of the segment
+  int64_t first;  // first particle of the tile within the segment
+  int64_t bA;     // window start of the segment in the input buffer
+};
+
+template <int T>
+__device__ __forceinline__ TileMeta tile_meta(const StepArgs &a, int gtile, int e, int tile) {
+  TileMeta m;
+  m.gtile = gtile;
+  m.e = e;
+  m.tile = tile;
+  m.ph = *a.m.phase;
+  m.seg = find_segment(a.m.tile_off, a.geo.Ptot, tile);
+  m.t0 = a.m.tile_off[m.seg];
+  m.ntile = a.m.tile_off[m.seg + 1] - m.t0;
+  m.cnt = a.m.cnt[m.seg];
+  m.bA = a.m.lay_base[m.ph][m.seg];
+  m.first = (int64_t)(tile - m.t0) * T;
+  const int64_t rem = m.cnt - m.first;
+  m.n = (int)(rem < 0 ? 0 : (rem > T ? T : rem));
+  const int64_t g0 = m.bA + m.first;
+  m.o8 = (int)(g0 & 1);
+  m.o4 = (int)(g0 & 3);
+  return m;
+}
+
+// Prefetched records of one tile in shared memory: rows x0 x1 x2 v0 v1 v2
+// [tau] of T+2 doubles, then id [img0 img1 img2] of T+4 words.  Each row is
+// copied by one bulk copy starting at the 16-byte boundary at or before the
+// tile's first particle (offset o8 / o4 elements), so every copy is aligned
+// and a multiple of 16 bytes; the record arrays carry 16 bytes of slack so
+// the rounded-up copies stay inside their allocations.
+template <int T>
+struct PfLayout {
+  static constexpr int S8 = (T + 2) * 8, S4 = (T + 4) * 4;
+  __host__ __device__ static constexpr int bytes(bool tau, bool img) {
+    return (6 + (tau ? 1 : 0)) * S8 + (1 + (img ? 3 : 0)) * S4;
+  }
+};
+
+template <int T>
+__device__ __forceinline__ void pf_issue(const StepArgs &a, const TileMeta &m, bool lay_tau,
+                                         unsigned char *buf, uint64_t *bar) {
+  using LY = PfLayout<T>;
+  const Rec &A = a.buf[m.ph];
+  const unsigned n8 = m.n ? (unsigned)((m.o8 + m.n + 1) & ~1) : 0u;
+  const unsigned n4 = m.n ? (unsigned)((m.o4 + m.n + 3) & ~3) : 0u;
+  const unsigned na8 = 6u + (A.tau ? 1u : 0u), na4 = 1u + (A.img[0] ? 3u : 0u);
+  mbar_arrive_expect_tx(bar, na8 * n8 * 8u + na4 * n4 * 4u);
+  if (!m.n) return;
+  const int64_t g0 = m.bA + m.first, s8 = g0 - m.o8, s4 = g0 - m.o4;
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    bulk_load(buf + s * LY::S8, A.x[s] + s8, n8 * 8u, bar);
+    bulk_load(buf + (3 + s) * LY::S8, A.v[s] + s8, n8 * 8u, bar);
+  }
+  if (A.tau) bulk_load(buf + 6 * LY::S8, A.tau + s8, n8 * 8u, bar);
+  unsigned char *b4 = buf + (lay_tau ? 7 : 6) * LY::S8;
+  bulk_load(b4, A.id + s4, n4 * 4u, bar);
+  if (A.img[0]) {
+#pragma unroll
+    for (int s = 0; s < 3; ++s) bulk_load(b4 + (1 + s) * LY::S4, A.img[s] + s4, n4 * 4u, bar);
+  }
+}
+
+template <int T>
+__device__ __forceinline__ void pf_read(const Rec &A, const TileMeta &m, bool lay_tau,
+                                        const unsigned char *buf, int li, double x[3],
+                                        double v[3], double &tau, uint32_t &id, int img[3],
+                                        double tau_c) {
+  using LY = PfLayout<T>;
+  const double *r8 = (const double *)buf + m.o8 + li;
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    x[s] = r8[s * (T + 2)];
+    v[s] = r8[(3 + s) * (T + 2)];
+  }
+  tau = A.tau ? r8[6 * (T + 2)] : tau_c;
+  const uint32_t *r4 = (const uint32_t *)(buf + (lay_tau ? 7 : 6) * LY::S8) + m.o4 + li;
+  id = r4[0];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) img[s] = A.img[0] ? (int)r4[(1 + s) * (T + 4)] : 0;
+}
 
 // One tile of one ensemble, processed by one block: integrate + wrap + flag
 // its particles, block scan of the (stay, leave) flags, look-back across the
 // segment's earlier tiles (by warp 0), then stayers to their compacted slot
-// in the output buffer and leavers to the pack buffer.  Tile j of segment s
-// covers particles [j*BLOCK*ITEMS, (j+1)*BLOCK*ITEMS) of the segment, ITEMS
-// consecutive ones per thread.
-template <int KIND, int BLOCK, int ITEMS>
-__device__ __forceinline__ void step_block_tile(const StepArgs &a, int ph, int tile,
-                                                BlockShared &sh) {
+// in the output buffer and leavers to the pack buffer.  Records come from
+// global memory, or (pf != nullptr) from the tile's prefetched rows.
+template <int KIND, int BLOCK, int ITEMS, bool STAGED>
+__device__ __forceinline__ void step_block_tile(const StepArgs &a, const TileMeta &mt,
+                                                BlockShared &sh, void *stage,
+                                                const unsigned char *pf, bool lay_tau) {
+  constexpr int T = BLOCK * ITEMS;
+  const int ph = mt.ph;
   const Rec A = a.buf[ph], B = a.buf[ph ^ 1];
-  const int P = a.geo.Ptot;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int seg = find_segment(a.m.tile_off, P, tile);
-  const int t0 = a.m.tile_off[seg];
-  const int ntile = a.m.tile_off[seg + 1] - t0;
+  const int seg = mt.seg, t0 = mt.t0, ntile = mt.ntile, tile = mt.tile;
   const int jt = tile - t0;
-  const int64_t cnt = a.m.cnt[seg];
-  const int64_t l0 = (int64_t)jt * (BLOCK * ITEMS) + (int64_t)threadIdx.x * ITEMS;
-  const int64_t bA = a.m.lay_base[ph][seg];
+  const int64_t cnt = mt.cnt;
+  const int64_t l0 = mt.first + (int64_t)threadIdx.x * ITEMS;
+  const int64_t bA = mt.bA;
   double x[ITEMS][3], v[ITEMS][3], tau[ITEMS];
   uint32_t id[ITEMS];
   int img[ITEMS][3], bin[ITEMS];
   unsigned packed = 0;
   int bad = 0;
+  auto load_item = [&](int k) {
+    if (pf)
+      pf_read<T>(A, mt, lay_tau, pf, threadIdx.x * ITEMS + k, x[k], v[k], tau[k], id[k], img[k],
+                 a.tau_const);
+    else
+      load_rec(A, bA + l0 + k, x[k], v[k], tau[k], id[k], img[k], a.tau_const);
+  };
+  FieldBox box{nullptr, 0, 0, 0, 0, 0, 0};
+  if (STAGED && KIND != FK_F64) {
+    // Shared-memory box of the tile's field cells: bounding box of the cells
+    // of all its particles (FP32 positions, so padded by 2 cells below and 3
+    // above for rounding, the stencil's +1 corner and the predictor's move),
+    // copied cooperatively when it fits in STAGE_BYTES.
+    int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+      if (l0 + k < cnt) {
+        load_item(k);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          int c = __float2int_rd(split_d(x[k][d]).h * (float)a.geo.inv_dx - 0.5f);
+          c = min(max(c, -8), a.geo.N + 8);  // non-finite positions: any box is safe
+          lo[d] = min(lo[d], c);
+          hi[d] = max(hi[d], c);
+        }
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        lo[d] = min(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+        hi[d] = max(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+      }
+      if (lane == 0) sh.blo[warp][d] = lo[d], sh.bhi[warp][d] = hi[d];
+    }
+    __syncthreads();
+    int b_lo[3], b_n[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      int l = 1 << 30, h = -(1 << 30);
+      for (int w = 0; w < BLOCK / 32; ++w) l = min(l, sh.blo[w][d]), h = max(h, sh.bhi[w][d]);
+      b_lo[d] = l - 2;
+      b_n[d] = h - l + 5;
+    }
+    const long long ncell = (long long)b_n[0] * b_n[1] * b_n[2];
+    if (b_n[0] > 0 && ncell <= STAGE_BYTES / cell_bytes(KIND)) {
+      const int N = a.geo.N;
+      // c / n for c < 2^13 as floor((c + 1/2) * (1/n)): the float error is far
+      // below the 1/(2n) margin to the next integer, so the quotient is exact
+      const float rnx = 1.0f / (float)b_n[0], rny = 1.0f / (float)b_n[1];
+      for (int c = threadIdx.x; c < ncell; c += BLOCK) {
+        const int r = (int)(((float)c + 0.5f) * rnx), lx = c - r * b_n[0];
+        const int lz = (int)(((float)r + 0.5f) * rny), ly = r - lz * b_n[1];
+        int gx = b_lo[0] + lx, gy = b_lo[1] + ly, gz = b_lo[2] + lz;
+        while (gx < 0) gx += N;
+        while (gx >= N) gx -= N;
+        while (gy < 0) gy += N;
+        while (gy >= N) gy -= N;
+        while (gz < 0) gz += N;
+        while (gz >= N) gz -= N;
+        const size_t g = (size_t)gx + (size_t)N * ((size_t)gy + (size_t)N * gz);
+        if (KIND == FK_DF) {
+          ((float4 *)stage)[2 * c] = __ldg((const float4 *)a.field + 2 * g);
+          ((float4 *)stage)[2 * c + 1] = __ldg((const float4 *)a.field + 2 * g + 1);
+        } else if (KIND == FK_F32) {
+          ((float4 *)stage)[c] = __ldg((const float4 *)a.field + g);
+        } else {
+          ((uint2 *)stage)[c] = __ldg((const uint2 *)a.field + g);
+        }
+      }
+      box = FieldBox{stage, b_lo[0], b_lo[1], b_lo[2], b_n[0], b_n[1], b_n[2]};
+      if (threadIdx.x == 0) atomicAdd(a.m.staged, 1ull);
+    }
+    __syncthreads();
+  }
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k) {
     bin[k] = -2;
     if (l0 + k < cnt) {
-      load_rec(A, bA + l0 + k, x[k], v[k], tau[k], id[k], img[k], a.tau_const);
+      if (!STAGED || KIND == FK_F64) load_item(k);
       if (KIND == FK_F64) heun_step64(a, x[k], v[k], tau[k], img[k], bad);
-      else if (KIND == FK_DF) heun_step_df<KIND>(a, x[k], v[k], tau[k], img[k], bad);
-      else heun_step_lo<KIND>(a, x[k], v[k], tau[k], img[k], bad);
+      else if (KIND == FK_DF) heun_step_df<KIND>(a, x[k], v[k], tau[k], img[k], bad, box);
+      else heun_step_lo<KIND>(a, x[k], v[k], tau[k], img[k], bad, box);
       int b = dest_bin(a.geo, seg, x[k]);
       if (b < 0) {
         bad |= 2;
@@ -297,7 +471,11 @@ __device__ __forceinline__ void step_block_tile(const StepArgs &a, int ph, int t
       if (lane >= o) wi += y;
     }
     if (lane < BLOCK / 32) sh.warp[lane] = wi - wv;
-    const unsigned tot = __shfl_sync(0xffffffffu, wi, BLOCK / 32 - 1);
+    if (lane == BLOCK / 32 - 1) sh.tot = wi;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned tot = sh.tot;
     const unsigned long long agg = pack_sm(tot >> 16, tot & 0xffffu);
     const unsigned long long ex = lookback_warp(a.m.tile_status, tile, t0, agg, a.m.status);
     if (lane == 0) {
@@ -310,11 +488,12 @@ __device__ __forceinline__ void step_block_tile(const StepArgs &a, int ph, int t
     }
   }
   __syncthreads();
+  const unsigned long long ex = sh.excl;
   if (threadIdx.x < NBIN && threadIdx.x != BIN_STAY && sh.hist[threadIdx.x])
     atomicAdd(&a.m.bincnt[seg * NBIN + threadIdx.x], sh.hist[threadIdx.x]);
   const unsigned excl = incl - packed + sh.warp[warp];
-  int64_t stay_pos = (int64_t)(sh.excl >> 31) + (excl >> 16);
-  int64_t mig_pos = (int64_t)(sh.excl & ((1ull << 31) - 1)) + (excl & 0xffffu);
+  int64_t stay_pos = (int64_t)(ex >> 31) + (excl >> 16);
+  int64_t mig_pos = (int64_t)(ex & ((1ull << 31) - 1)) + (excl & 0xffffu);
   const int64_t bB = a.m.lay_base[ph ^ 1][seg], cB = a.m.lay_cap[ph ^ 1][seg];
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k) {
@@ -337,11 +516,40 @@ __device__ __forceinline__ void step_block_tile(const StepArgs &a, int ph, int t
 
 // Persistent step kernel with block tiles: blocks take tile ids from one
 // counter in order (predecessors always belong to running blocks).
-template <int KIND, int BLOCK, int ITEMS, int CAP>
-__global__ void __launch_bounds__(BLOCK, 512 / BLOCK)
+// Resident blocks per SM asked of the compiler: the float-float and FP64
+// kernels need ~128 registers per thread; the FP32/BF16 step fits in 64,
+// which doubles the warps available to hide the gather latency.
+template <int KIND, int BLOCK>
+constexpr int step_min_blocks() {
+  return (KIND == FK_F32 || KIND == FK_BF16) ? 1024 / BLOCK : (KIND == FK_DF ? 768 / BLOCK : 512 / BLOCK);
+}
+
+// Ensemble of global tile g: largest e with off[e] <= g.
+__device__ __forceinline__ int find_ensemble(const int *off, int n, int g) {
+  int e = 0, hi = n;
+  while (hi - e > 1) {
+    const int mid = (e + hi) >> 1;
+    if (off[mid] <= g) e = mid; else hi = mid;
+  }
+  return e;
+}
+
+constexpr long long PF_WAIT_LIMIT = 1LL << 20;  // bounded wait for a tile's bulk copies
+
+// MODE 0: records read from global memory; 1: the same with the field box
+// staged in shared memory; 2: records of the next tile prefetched by bulk
+// copies (TMA) into the second of two shared-memory buffers while the
+// current tile is integrated, scanned and scattered.
+template <int KIND, int BLOCK, int ITEMS, int CAP, int MODE>
+__global__ void __launch_bounds__(BLOCK, (step_min_blocks<KIND, BLOCK>()))
     k_step_block(const __grid_constant__ StepGroup<CAP> pb) {
+  constexpr int T = BLOCK * ITEMS;
+  constexpr bool STAGED = MODE == 1;
   __shared__ BlockShared sh;
+  extern __shared__ __align__(128) unsigned char s_dyn[];
   __shared__ int s_off[CAP + 1];
+  __shared__ uint64_t s_bar[2];
+  __shared__ TileMeta s_meta[2];
   const int n = pb.n;
   if (threadIdx.x == 0) {
     int acc = 0;
@@ -351,40 +559,89 @@ __global__ void __launch_bounds__(BLOCK, 512 / BLOCK)
     }
     s_off[n] = acc;
   }
+  if (MODE != 2) {
+    __syncthreads();
+    const int total = s_off[n];
+    for (;;) {
+      if (threadIdx.x == 0) sh.tile = (int)atomicAdd(pb.counter, 1u);
+      if (threadIdx.x < NBIN) sh.hist[threadIdx.x] = 0;
+      __syncthreads();
+      const int g = sh.tile;
+      if (g >= total) break;
+      const int e = CAP == 1 ? 0 : find_ensemble(s_off, n, g);
+      const TileMeta m = tile_meta<T>(pb.a[e], g, e, g - s_off[e]);
+      step_block_tile<KIND, BLOCK, ITEMS, STAGED>(pb.a[e], m, sh, s_dyn, nullptr, false);
+      __syncthreads();
+    }
+    return;
+  }
+  const bool lay_tau = pb.pf_tau != 0;
+  const int buf_bytes = PfLayout<T>::bytes(pb.pf_tau != 0, pb.pf_img != 0);
+  const int *status0 = pb.a[0].m.status;
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    mbar_init_fence();
+  }
   __syncthreads();
   const int total = s_off[n];
-  for (;;) {
-    if (threadIdx.x == 0) sh.tile = (int)atomicAdd(pb.counter, 1u);
-    if (threadIdx.x < NBIN) sh.hist[threadIdx.x] = 0;
-    __syncthreads();
-    const int g = sh.tile;
-    if (g >= total) break;
-    if (CAP == 1) {
-      step_block_tile<KIND, BLOCK, ITEMS>(pb.a[0], *pb.a[0].m.phase, g, sh);
-    } else {
-      int e = 0, hi = n;
-      while (hi - e > 1) {
-        const int mid = (e + hi) >> 1;
-        if (s_off[mid] <= g) e = mid; else hi = mid;
-      }
-      step_block_tile<KIND, BLOCK, ITEMS>(pb.a[e], *pb.a[e].m.phase, g - s_off[e], sh);
+  auto acquire = [&](int slot) {  // thread 0: take the next tile and start its copies
+    const int g = (int)atomicAdd(pb.counter, 1u);
+    TileMeta m;
+    m.gtile = g;
+    if (g < total) {
+      const int e = CAP == 1 ? 0 : find_ensemble(s_off, n, g);
+      m = tile_meta<T>(pb.a[e], g, e, g - s_off[e]);
+      fence_proxy_async_smem();
+      pf_issue<T>(pb.a[e], m, lay_tau, s_dyn + slot * buf_bytes, &s_bar[slot]);
     }
+    s_meta[slot] = m;
+  };
+  if (threadIdx.x == 0) acquire(0);
+  if (threadIdx.x < NBIN) sh.hist[threadIdx.x] = 0;
+  __syncthreads();
+  for (int i = 0;; ++i) {
+    const int cur = i & 1;
+    const TileMeta m = s_meta[cur];
+    if (m.gtile >= total) break;
+    if (threadIdx.x == 0) acquire(cur ^ 1);
+    const long long lim = *(volatile const int *)status0 == LCS_ERR_TIMEOUT ? 1 : PF_WAIT_LIMIT;
+    if (!mbar_wait(&s_bar[cur], (unsigned)(i >> 1) & 1u, lim))
+      latch(pb.a[m.e].m.status, LCS_ERR_TIMEOUT);  // then the tile's rows may be stale
+    step_block_tile<KIND, BLOCK, ITEMS, false>(pb.a[m.e], m, sh, nullptr,
+                                               s_dyn + cur * buf_bytes, lay_tau);
+    if (threadIdx.x < NBIN) sh.hist[threadIdx.x] = 0;
     __syncthreads();
   }
 }
 
-// (threads per block, particles per thread) configurations the tuner tries
-#define LCS_STEP_CONFIGS(X, K, C) \
-  X(K, k_step_block, 0, 256, 2, C) X(K, k_step_block, 0, 256, 1, C) \
-  X(K, k_step_block, 0, 128, 2, C)
+// (kernel mode, threads per block, particles per thread) configurations the
+// tuner tries; mode 1 (staged field box) has no all-FP64 form
+#define LCS_STEP_CONFIGS(X, K, C)                                                   \
+  X(K, 0, 256, 2, C) X(K, 0, 256, 1, C) X(K, 0, 128, 2, C) X(K, 1, 256, 2, C)      \
+  X(K, 1, 128, 2, C) X(K, 2, 256, 2, C) X(K, 2, 128, 2, C) X(K, 2, 256, 1, C)
+
+// Dynamic shared memory of a configuration: the staged field box (mode 1)
+// or the two record buffers (mode 2).
+constexpr int step_dyn_smem(int kind, int mode, int tile, bool tau, bool img) {
+  return mode == 1 ? (kind != FK_F64 ? STAGE_BYTES : 0)
+                   : mode == 2 ? 2 * ((6 + (tau ? 1 : 0)) * (tile + 2) * 8 +
+                                      (1 + (img ? 3 : 0)) * (tile + 4) * 4)
+                               : 0;
+}
 
 template <int CAP>
 cudaError_t launch_step_group(const StepGroup<CAP> &pb, FieldKind kind, int mode, int block,
                               int items, int grid, cudaStream_t st) {
-#define LCS_LAUNCH(K, KER, M, B, I, C)                                      \
-  if (kind == K && mode == M && block == B && items == I) {                 \
-    KER<K, B, I, CAP><<<grid, B, 0, st>>>(pb);                              \
-    return cudaGetLastError();                                              \
+#define LCS_LAUNCH(K, M, B, I, C)                                                          \
+  if (kind == K && mode == M && block == B && items == I && !(M == 1 && K == FK_F64)) {  \
+    static_assert(PfLayout<B * I>::bytes(true, true) ==                                    \
+                      step_dyn_smem(K, 2, B * I, true, true) / 2, "layout");               \
+    auto ker = k_step_block<K, B, I, CAP, M>;                                              \
+    const int smem = step_dyn_smem(K, M, B * I, pb.pf_tau != 0, pb.pf_img != 0);           \
+    if (smem) cudaFuncSetAttribute(ker, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+    ker<<<grid, B, smem, st>>>(pb);                                                        \
+    return cudaGetLastError();                                                             \
   }
   LCS_STEP_CONFIGS(LCS_LAUNCH, FK_F64, CAP)
   LCS_STEP_CONFIGS(LCS_LAUNCH, FK_DF, CAP)
@@ -398,11 +655,16 @@ template cudaError_t launch_step_group<1>(const StepGroup<1> &, FieldKind, int, 
 template cudaError_t launch_step_group<GROUP_ENS>(const StepGroup<GROUP_ENS> &, FieldKind, int,
                                                   int, int, int, cudaStream_t);
 
-int step_kernel_occupancy(FieldKind kind, int mode, int block, int items) {
+int step_kernel_occupancy(FieldKind kind, int mode, int block, int items, bool pf_tau,
+                          bool pf_img) {
   int n = 0;
-#define LCS_OCC(K, KER, M, B, I, C)                                                  \
-  if (kind == K && mode == M && block == B && items == I)                            \
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, KER<K, B, I, C>, B, 0);
+#define LCS_OCC(K, M, B, I, C)                                                             \
+  if (kind == K && mode == M && block == B && items == I && !(M == 1 && K == FK_F64)) {  \
+    auto ker = k_step_block<K, B, I, C, M>;                                                \
+    const int smem = step_dyn_smem(K, M, B * I, pf_tau, pf_img);                           \
+    if (smem) cudaFuncSetAttribute(ker, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ker, B, smem);                       \
+  }
   LCS_STEP_CONFIGS(LCS_OCC, FK_F64, GROUP_ENS)
   LCS_STEP_CONFIGS(LCS_OCC, FK_DF, GROUP_ENS)
   LCS_STEP_CONFIGS(LCS_OCC, FK_F32, GROUP_ENS)

@@ -217,3 +217,5 @@ def test_backward_requires_a_tape(lcs):
     with pytest.raises(lcs.LcsError) as e:
         sim.backward(np.zeros((3, 50)), np.zeros((3, 50)))
     assert e.value.status == lcs.LCS_ERR_ARG
+    sim.step(1)   # a refused call latches nothing
+    sim.sync()

@@ -3,7 +3,8 @@
 All ensembles of a context advance in the same persistent kernel launches;
 each ensemble's particles see exactly the arithmetic and the stable orders of
 a run of that ensemble alone, so batched and solo states must be identical
-bit for bit.  The autotuner changes only the scan tile, never the results.
+bit for bit.  The autotuner changes only the scan tile and the kernel mode, never the
+results.
 """
 import numpy as np
 import pytest
@@ -82,9 +83,11 @@ def test_tune_keeps_results(lcs):
     sp = specs("df", "f64")
     a = lcs.Simulator(None, None, None, None, ensembles=sp)
     b = lcs.Simulator(None, None, None, None, ensembles=sp)
-    a.step(6)
-    block, items = b.tune(2)   # 3 configurations x 2 steps
-    assert (block, items) in ((256, 2), (256, 1), (128, 2))
+    a.step(16)
+    cfg = b.tune(2)   # 8 configurations x 2 steps
+    assert cfg in ((256, 2, 0), (256, 1, 0), (128, 2, 0), (256, 2, 1), (128, 2, 1),
+                   (256, 2, 2), (128, 2, 2), (256, 1, 2))
+    assert (b.tune_trials_ms > 0).all()
     for k in range(len(sp)):
         sa, sb = gpu_state(a, k), gpu_state(b, k)
         for key in ("seg", "ids", "x", "v"):
