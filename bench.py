@@ -58,6 +58,24 @@ def build_workload(name: str, device: str, n_override: int | None = None):
     return w, field, modes, dt, x, v, tau
 
 
+# ---------------------------------------------------------------- ranks
+
+def aggregate_over_ranks(ms: float, units: int, dist=None, device: str = "cpu"):
+    """Whole-job (time, units) over the ranks of an initialised process group:
+    the slowest rank's time and the sum of all ranks' particle updates (one
+    rank, or dist None: the inputs unchanged).  Barrier first, so no rank
+    reduces before every rank has stopped its clock."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms, units
+    import torch
+    dist.barrier()
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(u.item())
+
+
 # ---------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -317,12 +335,7 @@ def main():
     launches = sim.launches - l0
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    if dist:
-        dist.barrier()
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    updates = n * STEPS_PER_BENCH_STEP * K * world
+    ms, updates = aggregate_over_ranks(ms, n * STEPS_PER_BENCH_STEP * K, dist, "cuda")
     value = updates / (ms * 1e-3)
 
     # per-kernel device time (un-graphed replay of one sort period, events
@@ -361,8 +374,10 @@ def main():
                                                        ("x", "v", "tau", "ids")})
         e1.record(stream)
         torch.cuda.synchronize()
-        e_ms = e0.elapsed_time(e1)
-        e2e = {"value": n * STEPS_PER_BENCH_STEP * args.e2e_steps * world / (e_ms * 1e-3),
+        e_ms, e_units = aggregate_over_ranks(e0.elapsed_time(e1),
+                                             n * STEPS_PER_BENCH_STEP * args.e2e_steps, dist,
+                                             "cuda")
+        e2e = {"value": e_units / (e_ms * 1e-3),
                "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "wall_s": round(time.perf_counter() - t0, 3)}
 
