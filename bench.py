@@ -204,8 +204,8 @@ def batch_throughput(lcs, torch, steps=500, n_ens=48):
     spec = lambda e, dtype: dict(field=e["field"], x0=e["x0"], v0=e["v0"], dt=e["dt"],
                                  tau=e["tau"], sub=(2, 2, 2), sort_every=10, field_dtype=dtype)
     sim = lcs.Simulator(None, None, None, None, ensembles=[spec(e, "f32") for e in ens])
-    block, items, mode = sim.tune(2)  # 16 steps: 8 configurations x 2
-    timed(sim, 4)  # graph capture; the timed steps start on a sort period
+    block, items, mode = sim.tune(2)  # 22 steps: 11 configurations x 2
+    timed(sim, 8)  # graph capture; the timed steps start on a sort period
     ms_batch = timed(sim, steps)
     launches = sim.launches
     sim.close()

@@ -189,19 +189,25 @@ lcs_status lcs_profile_steps(lcs_ctx *ctx, int64_t nsteps, double *ms, int64_t *
  *                           not available with LCS_KERNEL_FP64;
  *   LCS_STEP_PREFETCH       the records of a block's next tile are brought
  *                           into shared memory by bulk asynchronous copies
- *                           while the current tile is processed. */
+ *                           while the current tile is processed;
+ *   LCS_STEP_DEFERRED       a block integrates its next tile before it
+ *                           resolves the scan prefix of the previous one,
+ *                           which waits parked in shared memory and is then
+ *                           written out with coalesced stores. */
 #define LCS_STEP_PLAIN 0
 #define LCS_STEP_STAGED_FIELD 1
 #define LCS_STEP_PREFETCH 2
+#define LCS_STEP_DEFERRED 3
 
 /* Number of step-kernel configurations lcs_tune tries. */
-#define LCS_TUNE_CONFIGS 8
+#define LCS_TUNE_CONFIGS 11
 
 /* Autotuner: time every step-kernel configuration on steps_per_trial real
  * steps of all ensembles, keep the fastest, and rebuild the step graphs with
  * it.  The configurations, in order, as (threads per block, particles per
  * thread, mode): (256,2,0) (256,1,0) (128,2,0) (256,2,1) (128,2,1)
- * (256,2,2) (128,2,2) (256,1,2).  The first two numbers fix the scan tile.
+ * (256,2,2) (128,2,2) (256,1,2) (256,2,3) (128,2,3) (256,1,3).  The first
+ * two numbers fix the scan tile.
  * Configurations of mode LCS_STEP_STAGED_FIELD are skipped for the all-FP64
  * kernel.  The trial steps advance the simulation (steps_per_trial steps per
  * tried configuration, recorded like any other step); results do not depend

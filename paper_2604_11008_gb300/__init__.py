@@ -24,8 +24,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "liblcs.so")
 
 LCS_OK, LCS_ERR_ARG, LCS_ERR_CUDA, LCS_ERR_OOM, LCS_ERR_CAPACITY = 0, 1, 2, 3, 4
 LCS_ERR_TIMEOUT, LCS_ERR_NONFINITE, LCS_ERR_DISPLACEMENT, LCS_ERR_STATE = 5, 6, 7, 8
-LCS_TUNE_CONFIGS = 8  # step-kernel configurations lcs_tune tries
-STEP_PLAIN, STEP_STAGED_FIELD, STEP_PREFETCH = 0, 1, 2  # step-kernel modes
+LCS_TUNE_CONFIGS = 11  # step-kernel configurations lcs_tune tries
+STEP_PLAIN, STEP_STAGED_FIELD, STEP_PREFETCH, STEP_DEFERRED = 0, 1, 2, 3  # step-kernel modes
 STATUS_NAMES = {0: "LCS_OK", 1: "LCS_ERR_ARG", 2: "LCS_ERR_CUDA", 3: "LCS_ERR_OOM",
                 4: "LCS_ERR_CAPACITY", 5: "LCS_ERR_TIMEOUT", 6: "LCS_ERR_NONFINITE",
                 7: "LCS_ERR_DISPLACEMENT", 8: "LCS_ERR_STATE"}

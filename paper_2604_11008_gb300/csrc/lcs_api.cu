@@ -72,7 +72,7 @@ struct lcs_ctx {
   int sms = 152;
   // batched step over all ensembles (one launch per kernel per step)
   FieldKind kind = FK_F64;
-  int mode = 0;                 // step kernel: 0 plain, 1 staged field box, 2 prefetched records
+  int mode = 0;  // step kernel: 0 plain, 1 staged field box, 2 prefetched records, 3 deferred
   bool pf_tau = false, pf_img = false;  // some ensemble has per-particle tau / images
   int block = 256, items = 2;   // threads per block, particles per thread (autotuned)
   int step_grid = 1, total_P = 0;
@@ -853,8 +853,8 @@ lcs_status lcs_profile_steps(lcs_ctx *c, int64_t nsteps, double *ms, int64_t *co
 
 // Step-kernel configurations: (threads per block, particles per thread, kernel mode)
 static const int kStepConfigs[LCS_TUNE_CONFIGS][3] = {
-    {256, 2, 0}, {256, 1, 0}, {128, 2, 0}, {256, 2, 1}, {128, 2, 1},
-    {256, 2, 2}, {128, 2, 2}, {256, 1, 2}};
+    {256, 2, 0}, {256, 1, 0}, {128, 2, 0}, {256, 2, 1}, {128, 2, 1}, {256, 2, 2},
+    {128, 2, 2}, {256, 1, 2}, {256, 2, 3}, {128, 2, 3}, {256, 1, 3}};
 
 lcs_status lcs_set_step_config(lcs_ctx *c, int block, int items, int mode) {
   lcs_status r = check_ctx(c);

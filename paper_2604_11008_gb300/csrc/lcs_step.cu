@@ -131,21 +131,26 @@ __device__ __forceinline__ unsigned long long pack_sm(unsigned long long stay,
 
 using atom_u64 = cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>;
 
+// Publish tile t's aggregate (first tile of its segment, at t0: its
+// inclusive prefix directly, the exclusive prefix being 0).
+__device__ __forceinline__ void publish_aggregate(unsigned long long *status_arr, int t, int t0,
+                                                  unsigned long long agg) {
+  atom_u64(status_arr[t]).store((t == t0 ? FLAG_PRE : FLAG_AGG) | agg,
+                                cuda::memory_order_release);
+}
+
 // Exclusive (stay, mig) prefix of tile `t` within its segment (first tile of
-// the segment at t0), computed by one whole warp: the tile's aggregate is
-// published first; then the warp reads 32 predecessors per round, stops at
-// the nearest inclusive prefix, and sums the aggregates in between (decoupled
-// look-back, Merrill & Garland 2016).  Finally the tile's own inclusive prefix
-// is published.  Every lane returns the prefix.  Bounded: on timeout the
-// error is latched and the partial sum used.
-__device__ unsigned long long lookback_warp(unsigned long long *status_arr, int t, int t0,
-                                            unsigned long long agg, int *err) {
+// the segment at t0), computed by one whole warp after the tile's aggregate
+// has been published: the warp reads 32 predecessors per round, stops at the
+// nearest inclusive prefix, and sums the aggregates in between (decoupled
+// look-back, Merrill & Garland 2016); then the tile's own inclusive prefix is
+// published.  Every lane returns the prefix.  Bounded: on timeout the error
+// is latched and the partial sum used; a timeout latched elsewhere ends the
+// wait early.
+__device__ unsigned long long resolve_prefix_warp(unsigned long long *status_arr, int t, int t0,
+                                                  unsigned long long agg, int *err) {
   const int lane = threadIdx.x & 31;
-  if (t == t0) {
-    if (lane == 0) atom_u64(status_arr[t]).store(FLAG_PRE | agg, cuda::memory_order_release);
-    return 0;
-  }
-  if (lane == 0) atom_u64(status_arr[t]).store(FLAG_AGG | agg, cuda::memory_order_release);
+  if (t == t0) return 0;
   unsigned long long excl = 0;
   int j = t - 1;  // newest predecessor not yet summed
   long long spins = 0;
@@ -180,6 +185,14 @@ __device__ unsigned long long lookback_warp(unsigned long long *status_arr, int 
   if (lane == 0)
     atom_u64(status_arr[t]).store(FLAG_PRE | (excl + agg), cuda::memory_order_release);
   return excl;
+}
+
+// Publish, then resolve (the tile waits for its own prefix at once).
+__device__ __forceinline__ unsigned long long lookback_warp(unsigned long long *status_arr, int t,
+                                                            int t0, unsigned long long agg,
+                                                            int *err) {
+  if ((threadIdx.x & 31) == 0) publish_aggregate(status_arr, t, t0, agg);
+  return resolve_prefix_warp(status_arr, t, t0, agg, err);
 }
 
 // ---------------------------------------------------------------- step kernel
@@ -514,16 +527,6 @@ __device__ __forceinline__ void step_block_tile(const StepArgs &a, const TileMet
   }
 }
 
-// Persistent step kernel with block tiles: blocks take tile ids from one
-// counter in order (predecessors always belong to running blocks).
-// Resident blocks per SM asked of the compiler: the float-float and FP64
-// kernels need ~128 registers per thread; the FP32/BF16 step fits in 64,
-// which doubles the warps available to hide the gather latency.
-template <int KIND, int BLOCK>
-constexpr int step_min_blocks() {
-  return (KIND == FK_F32 || KIND == FK_BF16) ? 1024 / BLOCK : (KIND == FK_DF ? 768 / BLOCK : 512 / BLOCK);
-}
-
 // Ensemble of global tile g: largest e with off[e] <= g.
 __device__ __forceinline__ int find_ensemble(const int *off, int n, int g) {
   int e = 0, hi = n;
@@ -532,6 +535,218 @@ __device__ __forceinline__ int find_ensemble(const int *off, int n, int g) {
     if (off[mid] <= g) e = mid; else hi = mid;
   }
   return e;
+}
+
+// Shared-memory rows of a parked tile (mode 3): x0 x1 x2 v0 v1 v2 [tau] of
+// T doubles, id [img0 img1 img2] of T words, then T destination bins.
+// Stayers sit at their tile-local rank from the front, leavers at their
+// rank from the back.
+template <int T>
+struct ParkLayout {
+  __host__ __device__ static constexpr int bytes(bool tau, bool img) {
+    return (6 + (tau ? 1 : 0)) * T * 8 + (1 + (img ? 3 : 0)) * T * 4 + T;
+  }
+};
+
+template <int T>
+__device__ __forceinline__ void park_put(unsigned char *pk, bool lay_tau, bool lay_img,
+                                         const Rec &A, int j, const double x[3],
+                                         const double v[3], double tau, uint32_t id,
+                                         const int img[3], int bin) {
+  double *r8 = (double *)pk;
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    r8[s * T + j] = x[s];
+    r8[(3 + s) * T + j] = v[s];
+  }
+  if (A.tau) r8[6 * T + j] = tau;
+  uint32_t *r4 = (uint32_t *)(pk + (lay_tau ? 7 : 6) * T * 8);
+  r4[j] = id;
+  if (A.img[0]) {
+#pragma unroll
+    for (int s = 0; s < 3; ++s) r4[(1 + s) * T + j] = (uint32_t)img[s];
+  }
+  pk[ParkLayout<T>::bytes(lay_tau, lay_img) - T + j] = (unsigned char)bin;
+}
+
+// Copy parked row j to record i of R (and its bin to bins[i] when given).
+template <int T>
+__device__ __forceinline__ void park_get(const unsigned char *pk, bool lay_tau, bool lay_img,
+                                         int j, const Rec &R, int64_t i, uint8_t *bins) {
+  const double *r8 = (const double *)pk;
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    R.x[s][i] = r8[s * T + j];
+    R.v[s][i] = r8[(3 + s) * T + j];
+  }
+  if (R.tau) R.tau[i] = r8[6 * T + j];
+  const uint32_t *r4 = (const uint32_t *)(pk + (lay_tau ? 7 : 6) * T * 8);
+  R.id[i] = r4[j];
+  if (R.img[0]) {
+#pragma unroll
+    for (int s = 0; s < 3; ++s) R.img[s][i] = (int32_t)r4[(1 + s) * T + j];
+  }
+  if (bins) bins[i] = pk[ParkLayout<T>::bytes(lay_tau, lay_img) - T + j];
+}
+
+// Load and integrate the tile's particles (ITEMS per thread, consecutive):
+// Heun step, wrap, destination bin (-2 for no particle), the per-thread
+// packed (stay << 16 | leave) count and the block's direction histogram.
+template <int KIND, int ITEMS>
+__device__ __forceinline__ unsigned integrate_items(const StepArgs &a, const TileMeta &mt,
+                                                    BlockShared &sh, double x[][3],
+                                                    double v[][3], double tau[], uint32_t id[],
+                                                    int img[][3], int bin[]) {
+  const Rec &A = a.buf[mt.ph];
+  const int64_t l0 = mt.first + (int64_t)threadIdx.x * ITEMS;
+  unsigned packed = 0;
+  int bad = 0;
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k) {
+    bin[k] = -2;
+    if (l0 + k < mt.cnt) {
+      load_rec(A, mt.bA + l0 + k, x[k], v[k], tau[k], id[k], img[k], a.tau_const);
+      if (KIND == FK_F64) heun_step64(a, x[k], v[k], tau[k], img[k], bad);
+      else if (KIND == FK_DF) heun_step_df<KIND>(a, x[k], v[k], tau[k], img[k], bad);
+      else heun_step_lo<KIND>(a, x[k], v[k], tau[k], img[k], bad);
+      int b = dest_bin(a.geo, mt.seg, x[k]);
+      if (b < 0) {
+        bad |= 2;
+        b = BIN_STAY;
+      }
+      bin[k] = b;
+      if (b == BIN_STAY) {
+        packed += 1u << 16;
+      } else {
+        packed += 1u;
+        atomicAdd(&sh.hist[b], 1);
+      }
+    }
+  }
+  if (bad & 1) latch(a.m.status, LCS_ERR_NONFINITE);
+  if (bad & 2) latch(a.m.status, LCS_ERR_DISPLACEMENT);
+  return packed;
+}
+
+// Mode 3, deferred scatter: a block integrates its next tile while its
+// previous tile waits, parked in shared memory, for the look-back; by then
+// every predecessor has long published its aggregate, so the look-back does
+// not stall the block.  The parked tile is then written out with coalesced
+// stores: its stayers form one contiguous run of the output window and its
+// leavers one contiguous run of the pack buffer.
+template <int KIND, int BLOCK, int ITEMS, int CAP>
+__device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockShared &sh,
+                                              const int *s_off, unsigned char *pk) {
+  constexpr int T = BLOCK * ITEMS;
+  __shared__ TileMeta s_park;
+  __shared__ unsigned s_park_tot;
+  const int n = pb.n, total = s_off[n];
+  const bool lay_tau = pb.pf_tau != 0, lay_img = pb.pf_img != 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  bool parked = false;
+  if (threadIdx.x < NBIN) sh.hist[threadIdx.x] = 0;
+  for (;;) {
+    if (threadIdx.x == 0) sh.tile = (int)atomicAdd(pb.counter, 1u);
+    __syncthreads();
+    const int g = sh.tile;
+    const bool fresh = g < total;
+    double x[ITEMS][3], v[ITEMS][3], tau[ITEMS];
+    uint32_t id[ITEMS];
+    int img[ITEMS][3], bin[ITEMS];
+    unsigned packed = 0;
+    TileMeta m;
+    if (fresh) {
+      const int e = CAP == 1 ? 0 : find_ensemble(s_off, n, g);
+      m = tile_meta<T>(pb.a[e], g, e, g - s_off[e]);
+      packed = integrate_items<KIND, ITEMS>(pb.a[e], m, sh, x, v, tau, id, img, bin);
+    }
+    if (parked) {
+      const TileMeta pm = s_park;
+      const StepArgs &pa = pb.a[pm.e];
+      const unsigned tot = s_park_tot;
+      if (warp == 0) {
+        const unsigned long long agg = pack_sm(tot >> 16, tot & 0xffffu);
+        const unsigned long long ex =
+            resolve_prefix_warp(pa.m.tile_status, pm.tile, pm.t0, agg, pa.m.status);
+        if (lane == 0) {
+          sh.excl = ex;
+          if (pm.tile - pm.t0 == pm.ntile - 1) {
+            const unsigned long long inc = ex + agg;
+            pa.m.stay_tot[pm.seg] = (int64_t)(inc >> 31);
+            pa.m.mig_tot[pm.seg] = (int64_t)(inc & ((1ull << 31) - 1));
+          }
+        }
+      }
+      __syncthreads();
+      const unsigned long long ex = sh.excl;
+      const int nstay = (int)(tot >> 16), nmig = (int)(tot & 0xffffu);
+      const int64_t stay0 = (int64_t)(ex >> 31), mig0 = (int64_t)(ex & ((1ull << 31) - 1));
+      const int ph = pm.ph;
+      const Rec &B = pa.buf[ph ^ 1];
+      const int64_t bB = pa.m.lay_base[ph ^ 1][pm.seg], cB = pa.m.lay_cap[ph ^ 1][pm.seg];
+      for (int j = threadIdx.x; j < nstay; j += BLOCK) {
+        if (stay0 + j < cB) park_get<T>(pk, lay_tau, lay_img, j, B, bB + stay0 + j, nullptr);
+        else latch(pa.m.status, LCS_ERR_CAPACITY);
+      }
+      for (int j = threadIdx.x; j < nmig; j += BLOCK)
+        park_get<T>(pk, lay_tau, lay_img, T - 1 - j, pa.pack, pm.bA + mig0 + j, pa.pack_bin);
+      __syncthreads();
+    }
+    if (!fresh) break;
+    // block scan of the fresh tile's (stay, leave) counts
+    unsigned incl = packed;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) sh.warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const unsigned wv = lane < BLOCK / 32 ? sh.warp[lane] : 0u;
+      unsigned wi = wv;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += y;
+      }
+      if (lane < BLOCK / 32) sh.warp[lane] = wi - wv;
+      if (lane == BLOCK / 32 - 1) {
+        sh.tot = wi;
+        const StepArgs &a = pb.a[m.e];
+        publish_aggregate(a.m.tile_status, m.tile, m.t0, pack_sm(wi >> 16, wi & 0xffffu));
+        s_park = m;
+        s_park_tot = wi;
+      }
+    }
+    __syncthreads();
+    const StepArgs &a = pb.a[m.e];
+    if (threadIdx.x < NBIN) {
+      if (threadIdx.x != BIN_STAY && sh.hist[threadIdx.x])
+        atomicAdd(&a.m.bincnt[m.seg * NBIN + threadIdx.x], sh.hist[threadIdx.x]);
+      sh.hist[threadIdx.x] = 0;
+    }
+    const unsigned excl = incl - packed + sh.warp[warp];
+    int rs = (int)(excl >> 16), rm = (int)(excl & 0xffffu);
+    const Rec &A = a.buf[m.ph];
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+      if (bin[k] == -2) continue;
+      const int j = bin[k] == BIN_STAY ? rs++ : T - 1 - rm++;
+      park_put<T>(pk, lay_tau, lay_img, A, j, x[k], v[k], tau[k], id[k], img[k], bin[k]);
+    }
+    parked = true;
+  }
+}
+
+// Persistent step kernel with block tiles: blocks take tile ids from one
+// counter in order (predecessors always belong to running blocks).
+// Resident blocks per SM asked of the compiler: the float-float and FP64
+// kernels need ~128 registers per thread; the FP32/BF16 step fits in 64,
+// which doubles the warps available to hide the gather latency.
+template <int KIND, int BLOCK>
+constexpr int step_min_blocks() {
+  return (KIND == FK_F32 || KIND == FK_BF16) ? 1024 / BLOCK : (KIND == FK_DF ? 768 / BLOCK : 512 / BLOCK);
 }
 
 constexpr long long PF_WAIT_LIMIT = 1LL << 20;  // bounded wait for a tile's bulk copies
@@ -558,6 +773,11 @@ __global__ void __launch_bounds__(BLOCK, (step_min_blocks<KIND, BLOCK>()))
       acc += pb.a[e].m.tile_off[pb.a[e].geo.Ptot];
     }
     s_off[n] = acc;
+  }
+  if (MODE == 3) {
+    __syncthreads();
+    step_deferred<KIND, BLOCK, ITEMS, CAP>(pb, sh, s_off, s_dyn);
+    return;
   }
   if (MODE != 2) {
     __syncthreads();
@@ -619,15 +839,17 @@ __global__ void __launch_bounds__(BLOCK, (step_min_blocks<KIND, BLOCK>()))
 // tuner tries; mode 1 (staged field box) has no all-FP64 form
 #define LCS_STEP_CONFIGS(X, K, C)                                                   \
   X(K, 0, 256, 2, C) X(K, 0, 256, 1, C) X(K, 0, 128, 2, C) X(K, 1, 256, 2, C)      \
-  X(K, 1, 128, 2, C) X(K, 2, 256, 2, C) X(K, 2, 128, 2, C) X(K, 2, 256, 1, C)
+  X(K, 1, 128, 2, C) X(K, 2, 256, 2, C) X(K, 2, 128, 2, C) X(K, 2, 256, 1, C)      \
+  X(K, 3, 256, 2, C) X(K, 3, 128, 2, C) X(K, 3, 256, 1, C)
 
-// Dynamic shared memory of a configuration: the staged field box (mode 1)
-// or the two record buffers (mode 2).
+// Dynamic shared memory of a configuration: the staged field box (mode 1),
+// the two record buffers (mode 2) or the parked tile (mode 3).
 constexpr int step_dyn_smem(int kind, int mode, int tile, bool tau, bool img) {
-  return mode == 1 ? (kind != FK_F64 ? STAGE_BYTES : 0)
-                   : mode == 2 ? 2 * ((6 + (tau ? 1 : 0)) * (tile + 2) * 8 +
-                                      (1 + (img ? 3 : 0)) * (tile + 4) * 4)
-                               : 0;
+  return mode == 1   ? (kind != FK_F64 ? STAGE_BYTES : 0)
+         : mode == 2 ? 2 * ((6 + (tau ? 1 : 0)) * (tile + 2) * 8 +
+                            (1 + (img ? 3 : 0)) * (tile + 4) * 4)
+         : mode == 3 ? (6 + (tau ? 1 : 0)) * tile * 8 + (1 + (img ? 3 : 0)) * tile * 4 + tile
+                     : 0;
 }
 
 template <int CAP>
@@ -637,6 +859,8 @@ cudaError_t launch_step_group(const StepGroup<CAP> &pb, FieldKind kind, int mode
   if (kind == K && mode == M && block == B && items == I && !(M == 1 && K == FK_F64)) {  \
     static_assert(PfLayout<B * I>::bytes(true, true) ==                                    \
                       step_dyn_smem(K, 2, B * I, true, true) / 2, "layout");               \
+    static_assert(ParkLayout<B * I>::bytes(true, false) ==                                 \
+                      step_dyn_smem(K, 3, B * I, true, false), "layout");                  \
     auto ker = k_step_block<K, B, I, CAP, M>;                                              \
     const int smem = step_dyn_smem(K, M, B * I, pb.pf_tau != 0, pb.pf_img != 0);           \
     if (smem) cudaFuncSetAttribute(ker, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \

@@ -83,10 +83,11 @@ def test_tune_keeps_results(lcs):
     sp = specs("df", "f64")
     a = lcs.Simulator(None, None, None, None, ensembles=sp)
     b = lcs.Simulator(None, None, None, None, ensembles=sp)
-    a.step(16)
-    cfg = b.tune(2)   # 8 configurations x 2 steps
+    a.step(22)
+    cfg = b.tune(2)   # 11 configurations x 2 steps
     assert cfg in ((256, 2, 0), (256, 1, 0), (128, 2, 0), (256, 2, 1), (128, 2, 1),
-                   (256, 2, 2), (128, 2, 2), (256, 1, 2))
+                   (256, 2, 2), (128, 2, 2), (256, 1, 2), (256, 2, 3), (128, 2, 3),
+                   (256, 1, 3))
     assert (b.tune_trials_ms > 0).all()
     for k in range(len(sp)):
         sa, sb = gpu_state(a, k), gpu_state(b, k)

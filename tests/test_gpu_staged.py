@@ -3,8 +3,10 @@
 Mode 1 copies the box of field cells around each tile's particles into shared
 memory and interpolates from there (a tile whose box does not fit reads global
 memory); mode 2 brings each block's next tile of particle records into shared
-memory with bulk asynchronous copies while the current tile is processed.
-The values read are the same either way, so every configuration must
+memory with bulk asynchronous copies while the current tile is processed;
+mode 3 integrates a block's next tile before resolving the previous tile's
+scan prefix, parking that tile in shared memory.  The values read are the
+same either way, so every configuration must
 reproduce the plain kernel's state bit for bit; the staged-tile counter shows
 which path the mode-1 tiles took.
 """
@@ -20,6 +22,7 @@ pytestmark = pytest.mark.gpu
 UNSTAGED = (256, 2, 0)
 STAGED = ((256, 2, 1), (128, 2, 1))
 PREFETCH = ((256, 2, 2), (128, 2, 2), (256, 1, 2))
+DEFERRED = ((256, 2, 3), (128, 2, 3), (256, 1, 3))
 
 
 @pytest.fixture(scope="module")
@@ -109,7 +112,7 @@ def test_staged_config_errors(lcs):
 @pytest.mark.parametrize("kernel,dtype", [("fp64", "f64"), ("df", "f64"), ("auto", "f32"),
                                           ("auto", "bf16")])
 @pytest.mark.parametrize("per_particle_tau,images", [(True, True), (False, False), (True, False)])
-def test_prefetched_records_equal_plain(lcs, kernel, dtype, per_particle_tau, images):
+def test_prefetched_and_deferred_equal_plain(lcs, kernel, dtype, per_particle_tau, images):
     # ragged segments (window starts at every alignment), migration, sorting
     case = dense_case(904, 12, 9001)
     if not per_particle_tau:
@@ -126,14 +129,15 @@ def test_prefetched_records_equal_plain(lcs, kernel, dtype, per_particle_tau, im
         return st
 
     ref = go(UNSTAGED)
-    for cfg in PREFETCH:
+    for cfg in PREFETCH + DEFERRED:
         st = go(cfg)
         for key in ("seg", "ids", "x", "v", "img", "tau"):
             assert np.array_equal(st[key], ref[key]), (cfg, key)
 
 
-def test_prefetched_batch_against_oracle(lcs):
-    """Several ensembles in one launch, mode 2, against the FP64 oracle."""
+@pytest.mark.parametrize("mode", [2, 3])
+def test_prefetched_and_deferred_batch_against_oracle(lcs, mode):
+    """Several ensembles in one launch, modes 2 and 3, against the FP64 oracle."""
     sp = []
     for k, (N, n, sub) in enumerate([(12, 3000, (2, 2, 2)), (8, 1, (1, 1, 1)),
                                      (16, 0, (2, 1, 1)), (12, 5000, (3, 1, 2))]):
@@ -142,7 +146,7 @@ def test_prefetched_batch_against_oracle(lcs):
                        tau_const=0.1, g=(0.0, 0.0, -9.8), sub=sub, sort_every=4, sort_brick=2,
                        kernel="df", track_images=True))
     batch = lcs.Simulator(None, None, None, None, ensembles=sp)
-    batch.set_step_config(256, 2, 2)
+    batch.set_step_config(256, 2, mode)
     batch.step(9)
     for k in (0, 3):
         s = sp[k]
