@@ -126,6 +126,34 @@ cudaError_t dalloc(lcs_ctx *c, T **p, int64_t n) {
   return e;
 }
 
+// For every destination subdomain d, the (source, direction) pairs whose
+// leavers arrive in d, by ascending source id (each source appears once;
+// -1 pads the row of 26).  Fixed by the subdomain grid alone.
+std::vector<int> finish_table(const int Pd[3]) {
+  const int P = Pd[0] * Pd[1] * Pd[2];
+  std::vector<int> tab((size_t)P * (NBIN - 1), -1);
+  for (int d = 0; d < P; ++d) {
+    const int pd[3] = {d % Pd[0], (d / Pd[0]) % Pd[1], d / (Pd[0] * Pd[1])};
+    std::vector<std::pair<int, int>> in;
+    for (int b = 0; b < NBIN; ++b) {
+      if (b == BIN_STAY) continue;
+      const int dir[3] = {b % 3 - 1, (b / 3) % 3 - 1, b / 9 - 1};
+      int ps[3], ok = 1;
+      for (int q = 0; q < 3; ++q) {
+        ps[q] = ((pd[q] - dir[q]) % Pd[q] + Pd[q]) % Pd[q];
+        if (dir_comp(ps[q], pd[q], Pd[q]) != dir[q]) ok = 0;
+      }
+      if (!ok) continue;
+      const int src = ps[0] + Pd[0] * (ps[1] + Pd[1] * ps[2]);
+      if (src != d) in.push_back({src, b});
+    }
+    std::sort(in.begin(), in.end());
+    for (size_t j = 0; j < in.size(); ++j)
+      tab[(size_t)d * (NBIN - 1) + j] = in[j].first * NBIN + in[j].second;
+  }
+  return tab;
+}
+
 // Record arrays get 4 elements (>= 16 bytes) of slack: the step kernel's bulk
 // copies round a tile's rows out to 16-byte boundaries.
 lcs_status alloc_rec(lcs_ctx *c, Rec &r, int64_t cap, bool has_tau, bool has_img) {
@@ -532,6 +560,7 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
     A(dalloc(c, &m.status, 1));
     A(dalloc(c, &m.tile_counter, 1));
     A(dalloc(c, &m.staged, 1));
+    A(dalloc(c, &m.fin_tab, (int64_t)P * (NBIN - 1)));
     A(dalloc(c, &m.bincnt, (int64_t)P * NBIN));
     A(dalloc(c, &m.off_in, (int64_t)P * NBIN));
     A(dalloc(c, &m.stay_tot, P));
@@ -565,6 +594,10 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
     C2(cudaMemsetAsync(m.status, 0, sizeof(int), st));
     C2(cudaMemsetAsync(m.tile_counter, 0, sizeof(unsigned), st));
     C2(cudaMemsetAsync(m.staged, 0, sizeof(unsigned long long), st));
+    {
+      const std::vector<int> tab = finish_table(e.a.geo.P);
+      C2(cudaMemcpy(m.fin_tab, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice));
+    }
     C2(cudaMemsetAsync(m.bincnt, 0, sizeof(int) * P * NBIN, st));
     C2(cudaMemsetAsync(m.stay_tot, 0, sizeof(int64_t) * P, st));
     C2(cudaMemsetAsync(m.mig_tot, 0, sizeof(int64_t) * P, st));

@@ -85,6 +85,8 @@ struct Meta {
   int64_t *stay_tot;     // stayers per segment                       [Ptot]
   int64_t *mig_tot;      // migrants per segment                      [Ptot]
   unsigned long long *staged;  // step tiles served from a shared-memory field box [1]
+  int *fin_tab;          // arrivals of each destination: source*27 + direction,
+                         // by ascending source, -1 padded             [Ptot*26]
 };
 
 struct StepArgs {
@@ -142,7 +144,7 @@ __device__ __forceinline__ int wrap_cell(int i, int N) {
 
 // Normalised direction component from subdomain coordinate a to b.
 // Returns -1, 0, +1, or 2 when b is not a neighbour of a.
-__device__ __forceinline__ int dir_comp(int a, int b, int P) {
+__host__ __device__ __forceinline__ int dir_comp(int a, int b, int P) {
   if (P == 1) return 0;
   int d = b - a;
   if (d < 0) d += P;

@@ -131,12 +131,15 @@ __device__ __forceinline__ unsigned long long pack_sm(unsigned long long stay,
 
 using atom_u64 = cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>;
 
+// Tile status words carry flag and value in one 64-bit word, so a reader
+// that sees the flag sees its value: relaxed atomics suffice (no fences).
+//
 // Publish tile t's aggregate (first tile of its segment, at t0: its
 // inclusive prefix directly, the exclusive prefix being 0).
 __device__ __forceinline__ void publish_aggregate(unsigned long long *status_arr, int t, int t0,
                                                   unsigned long long agg) {
   atom_u64(status_arr[t]).store((t == t0 ? FLAG_PRE : FLAG_AGG) | agg,
-                                cuda::memory_order_release);
+                                cuda::memory_order_relaxed);
 }
 
 // Exclusive (stay, mig) prefix of tile `t` within its segment (first tile of
@@ -158,7 +161,7 @@ __device__ unsigned long long resolve_prefix_warp(unsigned long long *status_arr
   while (true) {
     const int idx = j - lane;
     unsigned long long v = FLAG_PRE;  // before the segment start: prefix 0
-    if (idx >= t0) v = atom_u64(status_arr[idx]).load(cuda::memory_order_acquire);
+    if (idx >= t0) v = atom_u64(status_arr[idx]).load(cuda::memory_order_relaxed);
     const unsigned long long f = v & FLAG_MASK;
     const unsigned pre = __ballot_sync(0xffffffffu, f == FLAG_PRE);
     const unsigned inv = __ballot_sync(0xffffffffu, f == 0);
@@ -183,7 +186,7 @@ __device__ unsigned long long resolve_prefix_warp(unsigned long long *status_arr
     j -= 32;
   }
   if (lane == 0)
-    atom_u64(status_arr[t]).store(FLAG_PRE | (excl + agg), cuda::memory_order_release);
+    atom_u64(status_arr[t]).store(FLAG_PRE | (excl + agg), cuda::memory_order_relaxed);
   return excl;
 }
 
@@ -902,45 +905,34 @@ int step_kernel_occupancy(FieldKind kind, int mode, int block, int items, bool p
 // Per destination d: arrival offsets of every (source, direction) pair in
 // source order after the stayers, the new count, and the next layout.
 __device__ __forceinline__ void finish_body(const StepArgs &a) {
-  const Geom &g = a.geo;
-  const int P = g.Ptot;
+  const int P = a.geo.Ptot;
   const int ph = *a.m.phase;
   const int64_t *capB = a.m.lay_cap[ph ^ 1];
-  for (int d = threadIdx.x; d < P; d += blockDim.x) {
-    const int pd[3] = {d % g.P[0], (d / g.P[0]) % g.P[1], d / (g.P[0] * g.P[1])};
-    int src[NBIN - 1], bn[NBIN - 1], n = 0;
-    for (int b = 0; b < NBIN; ++b) {
-      if (b == BIN_STAY) continue;
-      const int dir[3] = {b % 3 - 1, (b / 3) % 3 - 1, b / 9 - 1};
-      int ps[3], ok = 1;
+  const int lane = threadIdx.x & 31;
+  // one warp per destination: lane j takes the j-th arriving (source,
+  // direction) pair of the destination's table, in source order
+  for (int d = threadIdx.x >> 5; d < P; d += blockDim.x >> 5) {
+    const int e = lane < NBIN - 1 ? a.m.fin_tab[d * (NBIN - 1) + lane] : -1;
+    const long long c = e >= 0 ? (long long)a.m.bincnt[e] : 0;
+    long long incl = c;
 #pragma unroll
-      for (int s = 0; s < 3; ++s) {
-        ps[s] = ((pd[s] - dir[s]) % g.P[s] + g.P[s]) % g.P[s];
-        if (dir_comp(ps[s], pd[s], g.P[s]) != dir[s]) ok = 0;
-      }
-      if (!ok) continue;
-      const int s_id = ps[0] + g.P[0] * (ps[1] + g.P[1] * ps[2]);
-      if (s_id == d) continue;
-      // insertion by source id (each source appears once)
-      int j = n++;
-      while (j > 0 && src[j - 1] > s_id) {
-        src[j] = src[j - 1];
-        bn[j] = bn[j - 1];
-        --j;
-      }
-      src[j] = s_id;
-      bn[j] = b;
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
     }
-    int64_t off = a.m.stay_tot[d];
-    for (int j = 0; j < n; ++j) {
-      const int e = src[j] * NBIN + bn[j];
-      a.m.off_in[e] = off;
-      off += a.m.bincnt[e];
+    const int64_t stay = a.m.stay_tot[d];
+    if (e >= 0) {
+      a.m.off_in[e] = stay + incl - c;
       a.m.bincnt[e] = 0;
     }
-    a.m.stay_tot[d] = 0;
-    if (off > capB[d]) latch(a.m.status, LCS_ERR_CAPACITY);
-    a.m.cnt[d] = off;
+    const long long arrived = __shfl_sync(0xffffffffu, incl, 31);
+    __syncwarp();
+    if (lane == 0) {
+      const int64_t tot = stay + arrived;
+      a.m.stay_tot[d] = 0;
+      if (tot > capB[d]) latch(a.m.status, LCS_ERR_CAPACITY);
+      a.m.cnt[d] = tot;
+    }
   }
   __syncthreads();
   layout_from_counts(P, a.step_tile, a.m.cnt, a.m.cstart, a.m.tile_off, a.m.stile_off,
