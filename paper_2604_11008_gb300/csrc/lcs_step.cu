@@ -227,8 +227,7 @@ __device__ __forceinline__ void store_rec(const Rec &R, int64_t i, const double 
 
 // Destination direction bin (0..26, 13 = stay) of a particle at x from
 // segment `seg`; -1 if the destination is not a neighbour.
-__device__ __forceinline__ int dest_bin(const Geom &g, int seg, const double x[3]) {
-  const int ps[3] = {seg % g.P[0], (seg / g.P[0]) % g.P[1], seg / (g.P[0] * g.P[1])};
+__device__ __forceinline__ int dest_bin(const Geom &g, const int ps[3], const double x[3]) {
   int bin = 0, mul = 1;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
@@ -261,6 +260,7 @@ struct TileMeta {
   int e;          // ensemble index within the launch
   int tile;       // tile id within the ensemble
   int seg, t0, ntile, ph;
+  int ps[3];      // subdomain coordinates of the segment
   int n;          // particles in the tile (0..T)
   int o8, o4;     // position of the tile's first particle in its prefetched 8- / 4-byte rows
   int64_t cnt;    // live particles of the segment
@@ -276,6 +276,9 @@ __device__ __forceinline__ TileMeta tile_meta(const StepArgs &a, int gtile, int 
   m.tile = tile;
   m.ph = *a.m.phase;
   m.seg = find_segment(a.m.tile_off, a.geo.Ptot, tile);
+  m.ps[0] = m.seg % a.geo.P[0];
+  m.ps[1] = (m.seg / a.geo.P[0]) % a.geo.P[1];
+  m.ps[2] = m.seg / (a.geo.P[0] * a.geo.P[1]);
   m.t0 = a.m.tile_off[m.seg];
   m.ntile = a.m.tile_off[m.seg + 1] - m.t0;
   m.cnt = a.m.cnt[m.seg];
@@ -454,7 +457,9 @@ __device__ __forceinline__ void step_block_tile(const StepArgs &a, const TileMet
       if (KIND == FK_F64) heun_step64(a, x[k], v[k], tau[k], img[k], bad);
       else if (KIND == FK_DF) heun_step_df<KIND>(a, x[k], v[k], tau[k], img[k], bad, box);
       else heun_step_lo<KIND>(a, x[k], v[k], tau[k], img[k], bad, box);
-      int b = dest_bin(a.geo, seg, x[k]);
+      const int ps[3] = {seg % a.geo.P[0], (seg / a.geo.P[0]) % a.geo.P[1],
+                         seg / (a.geo.P[0] * a.geo.P[1])};
+      int b = dest_bin(a.geo, ps, x[k]);
       if (b < 0) {
         bad |= 2;
         b = BIN_STAY;
@@ -612,7 +617,7 @@ __device__ __forceinline__ unsigned integrate_items(const StepArgs &a, const Til
       if (KIND == FK_F64) heun_step64(a, x[k], v[k], tau[k], img[k], bad);
       else if (KIND == FK_DF) heun_step_df<KIND>(a, x[k], v[k], tau[k], img[k], bad);
       else heun_step_lo<KIND>(a, x[k], v[k], tau[k], img[k], bad);
-      int b = dest_bin(a.geo, mt.seg, x[k]);
+      int b = dest_bin(a.geo, mt.ps, x[k]);
       if (b < 0) {
         bad |= 2;
         b = BIN_STAY;
@@ -744,12 +749,12 @@ __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockSha
 
 // Persistent step kernel with block tiles: blocks take tile ids from one
 // counter in order (predecessors always belong to running blocks).
-// Resident blocks per SM asked of the compiler: the float-float and FP64
-// kernels need ~128 registers per thread; the FP32/BF16 step fits in 64,
-// which doubles the warps available to hide the gather latency.
-template <int KIND, int BLOCK>
+// Resident threads per SM asked of the compiler (so registers per thread,
+// measured): 512 for the all-FP64 kernel (128 registers), 768 for the
+// float-float kernel with two particles per thread (80), 1024 otherwise (64).
+template <int KIND, int BLOCK, int ITEMS>
 constexpr int step_min_blocks() {
-  return (KIND == FK_F32 || KIND == FK_BF16) ? 1024 / BLOCK : (KIND == FK_DF ? 768 / BLOCK : 512 / BLOCK);
+  return KIND == FK_F64 ? 512 / BLOCK : (KIND == FK_DF && ITEMS == 2 ? 768 : 1024) / BLOCK;
 }
 
 constexpr long long PF_WAIT_LIMIT = 1LL << 20;  // bounded wait for a tile's bulk copies
@@ -759,7 +764,7 @@ constexpr long long PF_WAIT_LIMIT = 1LL << 20;  // bounded wait for a tile's bul
 // copies (TMA) into the second of two shared-memory buffers while the
 // current tile is integrated, scanned and scattered.
 template <int KIND, int BLOCK, int ITEMS, int CAP, int MODE>
-__global__ void __launch_bounds__(BLOCK, (step_min_blocks<KIND, BLOCK>()))
+__global__ void __launch_bounds__(BLOCK, (step_min_blocks<KIND, BLOCK, ITEMS>()))
     k_step_block(const __grid_constant__ StepGroup<CAP> pb) {
   constexpr int T = BLOCK * ITEMS;
   constexpr bool STAGED = MODE == 1;
