@@ -50,7 +50,7 @@ def _load():
             i64, i32, dbl = C.c_int64, C.c_int, C.c_double
             lib.orc_interp_many.argtypes = [P, i32, dbl, i64, P, P, P, P, P, P]
             lib.orc_advance.argtypes = [P, i32, dbl, dbl, i64, P, P, P, P, P, P, P, dbl, dbl, P,
-                                        i32, P, P]
+                                        i32, P, P, i32, dbl, dbl]
             lib.orc_advance.restype = i32
             lib.orc_keys.argtypes = [i32, dbl, P, i32, i64, P, P, P, P, P]
             lib.orc_keys.restype = i32
@@ -111,7 +111,12 @@ def interp_transpose(field, L, x, mu):
     return gf, jt
 
 
-def advance(field, L, x, v, tau, tau_const, dt, g, nsteps, img=None, cellhash=None):
+# Drag law: (0,) Stokes (f = 1); (1, nu, density_ratio) the factor of Eq. (7).
+STOKES = (0, 0.0, 0.0)
+
+
+def advance(field, L, x, v, tau, tau_const, dt, g, nsteps, img=None, cellhash=None,
+            drag=STOKES):
     """Heun steps of Eqs. (5)-(6) with wrap, in place on x, v (3, n) float64 C arrays."""
     lib = _load()
     field = _c(field, np.float64)
@@ -122,7 +127,9 @@ def advance(field, L, x, v, tau, tau_const, dt, g, nsteps, img=None, cellhash=No
     gg = _c(g, np.float64)
     return lib.orc_advance(_p(field), N, float(L), inv_dx(N, L), n, _p(x[0]), _p(x[1]),
                            _p(x[2]), _p(v[0]), _p(v[1]), _p(v[2]), _p(tau), float(tau_const),
-                           float(dt), _p(gg), int(nsteps), _p(img), _p(cellhash))
+                           float(dt), _p(gg), int(nsteps), _p(img), _p(cellhash),
+                           int(drag[0]), float(drag[1]) if drag[0] else 0.0,
+                           float(drag[2]) if drag[0] else 0.0)
 
 
 def keys(N, L, P, brick, x):
@@ -256,10 +263,10 @@ def initial_state(N, L, P, x, v, tau, ids=None, track_img=False):
     return st
 
 
-def step(st: State, field, L, P, tau_const, dt, g, brick, do_sort: bool):
+def step(st: State, field, L, P, tau_const, dt, g, brick, do_sort: bool, drag=STOKES):
     """One step of the path: advance + wrap, migrate, and (if do_sort) the cell sort."""
     N = field.shape[-1]
-    status = advance(field, L, st.x, st.v, st.tau, tau_const, dt, g, 1, img=st.img)
+    status = advance(field, L, st.x, st.v, st.tau, tau_const, dt, g, 1, img=st.img, drag=drag)
     dest, key = keys(N, L, P, brick, st.x)
     perm, seg_out, _ = migrate(int(np.prod(P)), st.seg, dest)
     st.permute(perm)
@@ -271,11 +278,12 @@ def step(st: State, field, L, P, tau_const, dt, g, brick, do_sort: bool):
     return status
 
 
-def run(st: State, field, L, P, tau_const, dt, g, nsteps, sort_every=0, brick=8, step0=0):
+def run(st: State, field, L, P, tau_const, dt, g, nsteps, sort_every=0, brick=8, step0=0,
+        drag=STOKES):
     """nsteps steps; the sort runs after steps whose 1-based index is a multiple of sort_every."""
     status = ORC_OK
     for k in range(step0, step0 + nsteps):
         s = step(st, field, L, P, tau_const, dt, g, brick,
-                 sort_every > 0 and (k + 1) % sort_every == 0)
+                 sort_every > 0 and (k + 1) % sort_every == 0, drag=drag)
         status = status or s
     return status

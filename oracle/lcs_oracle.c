@@ -9,7 +9,8 @@
  *   orc_interp        trilinear interpolation from the eight surrounding
  *                     cell-centre values (Sec. 2.2, last paragraph)
  *   orc_advance       particle ODE dX/dt = V, dV/dt = -(f/tau_p)(V - U(X))
- *                     (Eqs. 5-6) with f = 1 (Stokes drag) plus an optional
+ *                     (Eqs. 5-6) with f = 1 (Stokes drag) or the nonlinear
+ *                     drag factor of Eq. (7), plus an optional
  *                     constant gravity g, advanced with the two-stage
  *                     second-order Runge-Kutta method of Sec. 2.2 read as
  *                     Heun's method, then periodic wrap into [0, L)
@@ -118,11 +119,26 @@ static int wrap_coord(double *x, double L) {
   return img;
 }
 
-/* Advance n particles by nsteps Heun steps of Eqs. (5)-(6) with f = 1:
- *   A1 = (U(X) - V)/tau + g,   X* = X + dt V,   V* = V + dt A1,
- *   A2 = (U(X*) - V*)/tau + g,
+/* Drag factor f of Eq. (7) for a particle with relaxation time tp and
+ * velocity relative to the fluid vrel = V - U(X), in a fluid of kinematic
+ * viscosity nu, particle-to-fluid density ratio rr (Sec. 2.2):
+ *   radius r from tau_p = (2/9) rr r^2 / nu,
+ *   Re_p = 2 r |V - U| / nu,
+ *   f = 1 + 0.15 Re_p^0.687. */
+static double drag_factor(double tp, double nu, double rr, const double vrel[3]) {
+  const double r = sqrt(9.0 * nu * tp / (2.0 * rr));
+  const double speed = sqrt(vrel[0] * vrel[0] + vrel[1] * vrel[1] + vrel[2] * vrel[2]);
+  const double re = 2.0 * r * speed / nu;
+  return 1.0 + 0.15 * pow(re, 0.687);
+}
+
+/* Advance n particles by nsteps Heun steps of Eqs. (5)-(6):
+ *   A1 = f1 (U(X) - V)/tau + g,   X* = X + dt V,   V* = V + dt A1,
+ *   A2 = f2 (U(X*) - V*)/tau + g,
  *   X' = X + dt/2 (V + V*),    V' = V + dt/2 (A1 + A2),
- * then wrap X' into [0, L).  tau may be NULL (then tau_const for all).
+ * then wrap X' into [0, L).  drag = 0: f1 = f2 = 1 (Stokes drag); drag = 1:
+ * f1, f2 from Eq. (7) with the relative velocity of their stage (nu, rr as
+ * in drag_factor).  tau may be NULL (then tau_const for all).
  * img (3*n int32, SoA) counts the periodic images crossed (may be NULL).
  * cellhash (n uint64, may be NULL) folds in the floor index of every gather,
  * so that two runs which visit different interpolation cells can be told
@@ -131,10 +147,11 @@ static int wrap_coord(double *x, double L) {
 int orc_advance(const double *field, int N, double L, double inv_dx, int64_t n, double *x,
                 double *y, double *z, double *vx, double *vy, double *vz, const double *tau,
                 double tau_const, double dt, const double *g, int nsteps, int32_t *img,
-                uint64_t *cellhash) {
+                uint64_t *cellhash, int drag, double nu, double rr) {
   int status = ORC_OK;
   double *X[3] = {x, y, z};
   double *V[3] = {vx, vy, vz};
+  if (drag != 0 && (drag != 1 || !(nu > 0.0) || !(rr > 0.0))) return ORC_ERR_ARG;
   for (int step = 0; step < nsteps; ++step) {
     for (int64_t p = 0; p < n; ++p) {
       const double tp = tau ? tau[p] : tau_const;
@@ -145,15 +162,24 @@ int orc_advance(const double *field, int N, double L, double inv_dx, int64_t n, 
       }
       orc_interp(field, N, inv_dx, x0[0], x0[1], x0[2], u1);
       if (cellhash) cellhash[p] = cell_hash(cellhash[p], inv_dx, x0);
+      double f1 = 1.0, f2 = 1.0;
+      if (drag) {
+        const double rel[3] = {v0[0] - u1[0], v0[1] - u1[1], v0[2] - u1[2]};
+        f1 = drag_factor(tp, nu, rr, rel);
+      }
       for (int s = 0; s < 3; ++s) {
-        a1[s] = (u1[s] - v0[s]) / tp + g[s];
+        a1[s] = f1 * (u1[s] - v0[s]) / tp + g[s];
         xs[s] = x0[s] + dt * v0[s];
         vs[s] = v0[s] + dt * a1[s];
       }
       orc_interp(field, N, inv_dx, xs[0], xs[1], xs[2], u2);
       if (cellhash) cellhash[p] = cell_hash(cellhash[p], inv_dx, xs);
+      if (drag) {
+        const double rel[3] = {vs[0] - u2[0], vs[1] - u2[1], vs[2] - u2[2]};
+        f2 = drag_factor(tp, nu, rr, rel);
+      }
       for (int s = 0; s < 3; ++s) {
-        a2[s] = (u2[s] - vs[s]) / tp + g[s];
+        a2[s] = f2 * (u2[s] - vs[s]) / tp + g[s];
         double xn = x0[s] + 0.5 * dt * (v0[s] + vs[s]);
         double vn = v0[s] + 0.5 * dt * (a1[s] + a2[s]);
         if (fabs(xn - x0[s]) >= 0.5 * L) status = ORC_ERR_DISPLACEMENT;
@@ -415,7 +441,8 @@ int orc_adjoint(const double *field, int N, double L, double inv_dx, int64_t n,
     double *src = traj + (size_t)k * per, *dst = traj + (size_t)(k + 1) * per;
     memcpy(dst, src, per * sizeof(double));
     int st = orc_advance(field, N, L, inv_dx, n, dst, dst + n, dst + 2 * n, dst + 3 * n,
-                         dst + 4 * n, dst + 5 * n, tau, tau_const, dt, g, 1, NULL, NULL);
+                         dst + 4 * n, dst + 5 * n, tau, tau_const, dt, g, 1, NULL, NULL, 0,
+                         0.0, 0.0);
     if (st != ORC_OK) status = st;
   }
   for (int k = nsteps - 1; k >= 0; --k) {

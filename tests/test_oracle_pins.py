@@ -182,6 +182,60 @@ def test_heun_converges_second_order_to_exponential_relaxation():
     assert 3.6 < errs[0] / errs[1] < 4.4 and 3.6 < errs[1] / errs[2] < 4.4
 
 
+def _nonlinear_relaxation(w0, tau, nu, rr, t):
+    """Exact speed relative to a uniform fluid under the drag factor of Eq. (7):
+    dw/dt = -(1 + c w^a) w / tau with a = 0.687, c = 0.15 (2r/nu)^a and
+    tau = (2/9) rr r^2 / nu.  Separating variables, y = w^a obeys
+    y / (1 + c y) = K exp(-a t / tau) with K = y0 / (1 + c y0)."""
+    a = 0.687
+    r = math.sqrt(9.0 * nu * tau / (2.0 * rr))
+    c = 0.15 * (2.0 * r / nu) ** a
+    y0 = w0 ** a
+    k = y0 / (1.0 + c * y0) * math.exp(-a * t / tau)
+    return (k / (1.0 - c * k)) ** (1.0 / a)
+
+
+def test_nonlinear_drag_converges_second_order_to_exact_relaxation():
+    """Uniform flow, no gravity, relative speeds giving Re_p from about 0.5 to 5:
+    the oracle's Heun steps with the drag of Eq. (7) approach the exact speed and
+    displacement (the latter by quadrature) at second order."""
+    from scipy.integrate import quad
+    N, nu, rr, T = 4, 1e-3, 843.0, 0.4
+    U0 = np.array([0.3, -0.2, 0.1])
+    field = uniform_field(N, U0)
+    cases = [(0.5, 0.05), (2.0, 0.05), (5.0, 0.2), (3.0, 0.1)]   # (w0, tau)
+    e = np.array([[1.0, 0.0, 0.0], [0.0, 0.6, 0.8], [0.48, 0.6, 0.64], [0.0, 0.0, 1.0]]).T
+    e = np.ascontiguousarray(e / np.linalg.norm(e, axis=0))
+    w0 = np.array([c[0] for c in cases])
+    tau = np.array([c[1] for c in cases])
+    w_ref = np.array([_nonlinear_relaxation(w, tp, nu, rr, T) for w, tp in cases])
+    d_ref = np.array([quad(lambda t, w=w, tp=tp: _nonlinear_relaxation(w, tp, nu, rr, t), 0, T,
+                           epsabs=1e-14, epsrel=1e-13)[0] for w, tp in cases])
+    errs = []
+    for steps in (40, 80, 160, 320):
+        x = np.full((3, len(cases)), 1.0)
+        v = np.ascontiguousarray(U0[:, None] + w0[None, :] * e)
+        img = np.zeros(x.shape, np.int32)
+        st = oracle.advance(field, L, x, v, tau, 0.0, T / steps, np.zeros(3), steps, img=img,
+                            drag=(1, nu, rr))
+        assert st == oracle.ORC_OK
+        wv = v - U0[:, None]
+        xu = x + L * img - 1.0 - U0[:, None] * T
+        errs.append(max(np.max(np.abs(wv - w_ref * e)), np.max(np.abs(xu - d_ref * e))))
+    ratios = [errs[i] / errs[i + 1] for i in range(3)]
+    assert all(3.6 < q < 4.4 for q in ratios), (errs, ratios)
+    assert errs[-1] < 1e-5
+
+
+def test_nonlinear_drag_rejects_bad_parameters():
+    field = uniform_field(4, np.zeros(3))
+    x = np.full((3, 2), 1.0)
+    v = np.zeros((3, 2))
+    for drag in ((1, 0.0, 843.0), (1, 1e-3, -1.0), (2, 1e-3, 843.0)):
+        st = oracle.advance(field, L, x, v, None, 0.1, 0.01, np.zeros(3), 1, drag=drag)
+        assert st == oracle.ORC_ERR_ARG
+
+
 def test_heun_stage_structure_brute_force():
     """One step on a random field equals the Heun formulas evaluated with the
     independent scipy interpolator (catches a wrong stage, sign or weight)."""
