@@ -76,6 +76,13 @@ typedef enum {
                             float-float arithmetic, integration in FP64 */
 } lcs_kernel;
 
+typedef enum {
+  LCS_DRAG_STOKES = 0,   /* f = 1 in Eq. (6) */
+  LCS_DRAG_NONLINEAR = 1 /* f = 1 + 0.15 Re_p^0.687, Re_p = 2 r |V - U| / nu, with the
+                            radius r from tau_p = (2/9)(rho_p/rho) r^2 / nu (Sec. 2.2,
+                            Eq. 7); forward only (no lcs_backward) */
+} lcs_drag;
+
 /* One ensemble: a field, its particles and its parameters. */
 typedef struct {
   int n;                  /* grid points per axis N (the grid is N^3), >= 2 */
@@ -96,6 +103,9 @@ typedef struct {
   int sort_brick;         /* brick edge B of the cell order (0: 8; 1: x-fastest) */
   int track_images;       /* 1: keep per-axis periodic image counts */
   int ckpt_every;         /* > 0: tape checkpoints every k steps for lcs_backward */
+  lcs_drag drag;          /* drag law (LCS_DRAG_STOKES when zero-initialised) */
+  double nu;              /* kinematic viscosity, > 0 (LCS_DRAG_NONLINEAR only) */
+  double density_ratio;   /* rho_p / rho, > 0; 0 selects 843 (water, Sec. 2.2) */
 } lcs_desc;
 
 /* Create a context for n_ens ensembles (1 <= n_ens <= 1024, all with the same

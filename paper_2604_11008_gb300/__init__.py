@@ -38,6 +38,7 @@ EXPORTS = ("lcs_init", "lcs_step", "lcs_migrate", "lcs_sort", "lcs_set_state", "
            "lcs_launch_count", "lcs_partition", "lcs_profile_steps", "lcs_partition_noalloc",
            "lcs_tune", "lcs_set_step_config", "lcs_staged_tiles")
 PARTITION_NOALLOC_MAX_N = 1 << 20
+DRAGS = {"stokes": 0, "nonlinear": 1}  # lcs_drag: f = 1, or the factor of Eq. (7)
 PROF_CLASSES = ("step", "finish", "unpack", "flip", "sort")
 
 
@@ -53,7 +54,8 @@ class Desc(C.Structure):
                 ("x0", C.c_void_p), ("v0", C.c_void_p), ("tau", C.c_void_p),
                 ("tau_const", C.c_double), ("ids", C.c_void_p), ("dt", C.c_double),
                 ("g", C.c_double * 3), ("sort_every", C.c_int), ("sort_brick", C.c_int),
-                ("track_images", C.c_int), ("ckpt_every", C.c_int)]
+                ("track_images", C.c_int), ("ckpt_every", C.c_int), ("drag", C.c_int),
+                ("nu", C.c_double), ("density_ratio", C.c_double)]
 
 
 _lib = None
@@ -129,14 +131,15 @@ class Simulator:
     def __init__(self, field, x0, v0, dt, tau=None, tau_const=0.0, g=(0.0, 0.0, 0.0),
                  sub=(1, 1, 1), box=2 * math.pi, field_dtype="f64", kernel="auto", ids=None,
                  sort_every=0, sort_brick=0, track_images=False, ckpt_every=0, stream=None,
-                 ensembles=None):
+                 ensembles=None, drag="stokes", nu=0.0, density_ratio=0.0):
         import torch
         self._keep = []
         self._stream = stream
         specs = ensembles if ensembles is not None else [dict(
             field=field, x0=x0, v0=v0, dt=dt, tau=tau, tau_const=tau_const, g=g, sub=sub,
             box=box, field_dtype=field_dtype, kernel=kernel, ids=ids, sort_every=sort_every,
-            sort_brick=sort_brick, track_images=track_images, ckpt_every=ckpt_every)]
+            sort_brick=sort_brick, track_images=track_images, ckpt_every=ckpt_every,
+            drag=drag, nu=nu, density_ratio=density_ratio)]
         descs = (Desc * len(specs))()
         self.meta = []
         for k, sp in enumerate(specs):
@@ -163,6 +166,9 @@ class Simulator:
             d.sort_brick = int(sp.get("sort_brick", 0))
             d.track_images = int(bool(sp.get("track_images", False)))
             d.ckpt_every = int(sp.get("ckpt_every", 0))
+            d.drag = DRAGS[sp.get("drag", "stokes")]
+            d.nu = float(sp.get("nu", 0.0))
+            d.density_ratio = float(sp.get("density_ratio", 0.0))
             self.meta.append(dict(n=d.n, np=d.np, P=int(np.prod(d.sub[:])), has_tau=t is not None,
                                   tau_const=d.tau_const, box=d.box))
         self._ctx = C.c_void_p()

@@ -209,7 +209,7 @@ lcs_status enqueue_sort(lcs_ctx *c, Ens &e, cudaStream_t st) {
   return LCS_OK;
 }
 
-// The step kernel of every group of ensembles (one launch per 52 ensembles).
+// The step kernel of every group of ensembles (one launch per GROUP_ENS ensembles).
 lcs_status launch_steps(lcs_ctx *c, cudaStream_t st) {
   static thread_local StepGroup<GROUP_ENS> big;
   for (size_t gi = 0; gi < c->groups.size(); ++gi) {
@@ -240,7 +240,7 @@ lcs_status launch_steps(lcs_ctx *c, cudaStream_t st) {
 }
 
 // One step of every ensemble: 1 memset + (step groups + 3) launches, whatever
-// the number of ensembles (one step group per 52 ensembles).
+// the number of ensembles (one step group per GROUP_ENS ensembles).
 lcs_status enqueue_step(lcs_ctx *c, cudaStream_t st) {
   CK(cudaMemsetAsync(c->tile_status, 0, sizeof(unsigned long long) * c->total_tiles, st));
   lcs_status rs = launch_steps(c, st);
@@ -484,6 +484,16 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
       r = fail(c, LCS_ERR_ARG, "invalid lcs_desc for ensemble " + std::to_string(k));
       break;
     }
+    if (d.drag != LCS_DRAG_STOKES &&
+        (d.drag != LCS_DRAG_NONLINEAR || !(d.nu > 0) || !(d.density_ratio >= 0) ||
+         !std::isfinite(d.nu) || !std::isfinite(d.density_ratio))) {
+      r = fail(c, LCS_ERR_ARG, "invalid drag parameters for ensemble " + std::to_string(k));
+      break;
+    }
+    if (d.drag != LCS_DRAG_STOKES && d.ckpt_every > 0) {
+      r = fail(c, LCS_ERR_ARG, "lcs_backward supports the Stokes drag only (ckpt_every > 0)");
+      break;
+    }
     switch (d.field_dtype) {
       case LCS_F64:
         e.kind = d.field_kernel == LCS_KERNEL_FP64 ? FK_F64 : FK_DF;
@@ -522,6 +532,8 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
     e.max_stiles = (int)(e.np / SORT_TILE + P + 2);
     e.a.dt = d.dt;
     e.a.half_dt = 0.5 * d.dt;
+    e.a.drag = d.drag == LCS_DRAG_NONLINEAR ? 1 : 0;
+    e.a.drag_c = e.a.drag ? 18.0 / (d.nu * (d.density_ratio > 0 ? d.density_ratio : 843.0)) : 0.0;
     e.a.tau_const = d.tau ? 0.0 : d.tau_const;
     for (int s = 0; s < 3; ++s) e.a.g[s] = d.g[s];
     {

@@ -103,6 +103,8 @@ struct StepArgs {
   // float-pair splits (hi, lo) of dt, dt/2, dt*N/L and dt*g for the DF step
   float dfk[12];
   int step_tile;     // particles per step tile (block or warp lanes x items per lane)
+  int drag;          // 0: Stokes (f = 1); 1: drag factor of Eq. (7)
+  double drag_c;     // 18 / (nu rho_p/rho): Re_p^2 = drag_c tau_p |V - U|^2
 };
 
 // The ensembles of one context, as the batched kernels see them.
@@ -116,7 +118,7 @@ struct BatchArgs {
 
 // A group of at most CAP ensembles advanced by one step-kernel launch; the
 // whole struct is the kernel's parameter block (<= 32 KB for CAP = GROUP_ENS).
-constexpr int GROUP_ENS = 52;
+constexpr int GROUP_ENS = 48;
 template <int CAP>
 struct StepGroup {
   StepArgs a[CAP];

@@ -237,10 +237,31 @@ __device__ __forceinline__ void interp_any(const void *field, int N, const long 
   else interp_lo<KIND>(field, N, q, U, box);
 }
 
-// Heun step of Eqs. (5)-(6) (f = 1, gravity g) with float-float increments:
-//   h = dt/tau, D1 = U(X) - V, V* = V + h D1 + dt g, X* = X + dt V,
-//   D2 = U(X*) - V*, dV = (h D1 + h D2)/2 + dt g,
-//   dX = dt V + (dt/2)(h D1 + dt g)          [= dt (V + V*)/2]
+// Drag factor of Eq. (7): f = 1 + 0.15 Re_p^0.687 with Re_p^2 = c tau |D|^2,
+// c = 18 / (nu rho_p/rho) (the radius from tau_p = (2/9)(rho_p/rho) r^2/nu,
+// Sec. 2.2), D = U - V, so f = 1 + 0.15 (c tau |D|^2)^(0.687/2).  The float-
+// float kernel evaluates it in FP64 with CUDA's pow (about 1 ulp), the
+// FP32/BF16 kernels in FP32 with powf.
+static __device__ __noinline__ df drag_factor_df(double c, double tau, const df D[3]) {
+  double d2 = 0.0;
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const double d = df_to_double(D[s]);
+    d2 = fma(d, d, d2);
+  }
+  return split_d(1.0 + 0.15 * pow(c * tau * d2, 0.3435));
+}
+
+static __device__ __noinline__ float drag_factor_f32(float c, float tau, const float D[3]) {
+  const float d2 = fmaf(D[0], D[0], fmaf(D[1], D[1], D[2] * D[2]));
+  return 1.0f + 0.15f * powf(c * tau * d2, 0.3435f);
+}
+
+// Heun step of Eqs. (5)-(6) (gravity g) with float-float increments:
+//   h = dt/tau, D1 = U(X) - V, h1 = f(D1) h, V* = V + h1 D1 + dt g,
+//   X* = X + dt V, D2 = U(X*) - V*, h2 = f(D2) h,
+//   dV = (h1 D1 + h2 D2)/2 + dt g, dX = dt V + (dt/2)(h1 D1 + dt g)
+//   [= dt (V + V*)/2], with f = 1 (Stokes) or the factor of Eq. (7)
 // then X' = X + dX and V' = V + dV in FP64, and the periodic wrap.
 template <int KIND>
 __device__ __forceinline__ void heun_step_df(const StepArgs &a, double x[3], double v[3],
@@ -254,20 +275,29 @@ __device__ __forceinline__ void heun_step_df(const StepArgs &a, double x[3], dou
 #pragma unroll
   for (int s = 0; s < 3; ++s) q[s] = fix_stage1(x[s], g.inv_dx);
   interp_any<KIND>(a.field, g.N, q, U, box);
+  df D[3];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    V[s] = split_d(v[s]);
+    D[s] = df_add(U[s], df_neg(V[s]));
+  }
+  const df h1 = a.drag ? df_mul(h, drag_factor_df(a.drag_c, tau, D)) : h;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     const df gd = {a.dfk[6 + 2 * s], a.dfk[7 + 2 * s]};
-    V[s] = split_d(v[s]);
-    hD1[s] = df_mul(h, df_add(U[s], df_neg(V[s])));
+    hD1[s] = df_mul(h1, D[s]);
     Vs[s] = df_add(df_add(V[s], hD1[s]), gd);
     q[s] = fix_stage2(q[s], V[s], cx);
   }
   interp_any<KIND>(a.field, g.N, q, U, box);
+#pragma unroll
+  for (int s = 0; s < 3; ++s) D[s] = df_add(U[s], df_neg(Vs[s]));
+  const df h2 = a.drag ? df_mul(h, drag_factor_df(a.drag_c, tau, D)) : h;
   const long long bitsL = __double_as_longlong(g.L);
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     const df gd = {a.dfk[6 + 2 * s], a.dfk[7 + 2 * s]};
-    const df hD2 = df_mul(h, df_add(U[s], df_neg(Vs[s])));
+    const df hD2 = df_mul(h2, D[s]);
     const df dV = df_add(df_scale2(df_add(hD1[s], hD2), 0.5f), gd);
     const df dX = df_add(df_mul(dt, V[s]), df_mul(hdt, df_add(hD1[s], gd)));
     if (!(fabsf(dX.h) < (float)(0.5 * g.L))) bad |= 2;
@@ -307,20 +337,29 @@ __device__ __forceinline__ void heun_step_lo(const StepArgs &a, double x[3], dou
 #pragma unroll
   for (int s = 0; s < 3; ++s) q[s] = fix_stage1(x[s], g.inv_dx);
   interp_lo<KIND>(a.field, g.N, q, U, box);
+  float D[3];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    V[s] = split_d(v[s]).h;
+    D[s] = U[s].h - V[s];
+  }
+  const float h1 = a.drag ? h * drag_factor_f32((float)a.drag_c, split_d(tau).h, D) : h;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     const float gd = a.dfk[6 + 2 * s];
-    V[s] = split_d(v[s]).h;
-    hD1[s] = h * (U[s].h - V[s]);
+    hD1[s] = h1 * D[s];
     Vs[s] = V[s] + hD1[s] + gd;
     q[s] = fix_stage2_lo(q[s], V[s], cx);
   }
   interp_lo<KIND>(a.field, g.N, q, U, box);
+#pragma unroll
+  for (int s = 0; s < 3; ++s) D[s] = U[s].h - Vs[s];
+  const float h2 = a.drag ? h * drag_factor_f32((float)a.drag_c, split_d(tau).h, D) : h;
   const long long bitsL = __double_as_longlong(g.L);
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     const float gd = a.dfk[6 + 2 * s];
-    const float hD2 = h * (U[s].h - Vs[s]);
+    const float hD2 = h2 * D[s];
     const float dV = 0.5f * (hD1[s] + hD2) + gd;
     const float dX = dt * (V[s] + 0.5f * (hD1[s] + gd));
     if (!(fabsf(dX) < (float)(0.5 * g.L))) bad |= 2;
@@ -342,23 +381,35 @@ __device__ __forceinline__ void heun_step_lo(const StepArgs &a, double x[3], dou
   }
 }
 
-// One Heun step of Eqs. (5)-(6) (f = 1, gravity g) with periodic wrap, in FP64.
+// Drag factor of Eq. (7) in FP64 (see drag_factor_df).
+static __device__ __noinline__ double drag_factor64(double c, double tau, const double u[3],
+                                                const double v[3]) {
+  double d2 = 0.0;
+#pragma unroll
+  for (int s = 0; s < 3; ++s) d2 = fma(u[s] - v[s], u[s] - v[s], d2);
+  return 1.0 + 0.15 * pow(c * tau * d2, 0.3435);
+}
+
+// One Heun step of Eqs. (5)-(6) (gravity g; f = 1 or Eq. 7) with periodic
+// wrap, in FP64.
 __device__ __forceinline__ void heun_step64(const StepArgs &a, double x[3], double v[3],
                                           double tau, int img[3], int &bad) {
   const Geom &g = a.geo;
   const double itau = 1.0 / tau;
   double u1[3], a1[3], xs[3], vs[3], u2[3];
   interp64(a.field, g, x[0], x[1], x[2], u1[0], u1[1], u1[2]);
+  const double f1 = a.drag ? drag_factor64(a.drag_c, tau, u1, v) * itau : itau;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
-    a1[s] = (u1[s] - v[s]) * itau + a.g[s];
+    a1[s] = (u1[s] - v[s]) * f1 + a.g[s];
     xs[s] = predictor64(x[s], v[s], a.dt);
     vs[s] = v[s] + a.dt * a1[s];
   }
   interp64(a.field, g, xs[0], xs[1], xs[2], u2[0], u2[1], u2[2]);
+  const double f2 = a.drag ? drag_factor64(a.drag_c, tau, u2, vs) * itau : itau;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
-    const double a2 = (u2[s] - vs[s]) * itau + a.g[s];
+    const double a2 = (u2[s] - vs[s]) * f2 + a.g[s];
     double xn = x[s] + a.half_dt * (v[s] + vs[s]);
     const double vn = v[s] + a.half_dt * (a1[s] + a2);
     if (!(fabs(xn - x[s]) < 0.5 * g.L)) bad |= fabs(xn) <= 1e300 ? 2 : 1;
