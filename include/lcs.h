@@ -29,6 +29,13 @@
  *   - Particle i of a subdomain p = (px, py, pz) has its containing cell
  *     c_s = min(floor(x_s * N/L), N-1) in [px*N/Px, (px+1)*N/Px) etc., and
  *     p is numbered px + Px*(py + Py*pz).
+ *   - The library keeps positions in fixed point in cell units (52 fraction
+ *     bits: the FP64 product x_s * N/L given to lcs_init / lcs_set_state is
+ *     held exactly, and its integer part is the cell above) and velocities as
+ *     float pairs (48 significant bits).  lcs_get_state returns them rounded
+ *     to FP64: a position read back is within one unit in the last place of
+ *     the value set, and the cell of a position read back can differ from
+ *     the library's only when it lies within that rounding of a cell face.
  *   - Every call returns an lcs_status; nothing is thrown across the ABI.
  *     Errors detected inside kernels are latched in a device status word
  *     and reported by the next synchronising call (lcs_sync, lcs_get_state,

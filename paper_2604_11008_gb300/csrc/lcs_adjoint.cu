@@ -54,25 +54,36 @@ __global__ void k_tape_store(StepArgs a, TapeSlot t, int64_t np) {
 }
 
 // Re-run `len` steps from a checkpoint with the forward's own arithmetic,
-// storing the state at the start of every step: states[(j*6 + c)*np + i].
+// storing the state at the start of every step: states[(j*6 + c)*np + i]
+// (c < 3: fixed-point positions, c >= 3: velocity float pairs, as 64-bit
+// words).
+__device__ __forceinline__ unsigned long long bits_of_df(df v) {
+  return ((unsigned long long)__float_as_uint(v.l) << 32) | __float_as_uint(v.h);
+}
+__device__ __forceinline__ df df_of_bits(unsigned long long b) {
+  return {__uint_as_float((unsigned)b), __uint_as_float((unsigned)(b >> 32))};
+}
+
 template <int KIND>
-__global__ void k_recompute(StepArgs a, TapeSlot t, double *states, int len, int64_t np) {
+__global__ void k_recompute(StepArgs a, TapeSlot t, unsigned long long *states, int len,
+                            int64_t np) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= np) return;
-  double x[3], v[3];
+  long long x[3];
+  df v[3];
   int img[3] = {0, 0, 0};
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     x[s] = t.x[s * np + i];
-    v[s] = t.v[s * np + i];
+    v[s] = df_from2(t.v[s * np + i]);
   }
   const double tau = t.tau ? t.tau[i] : a.tau_const;
   for (int j = 0; j < len; ++j) {
-    double *st = states + (int64_t)j * 6 * np;
+    unsigned long long *st = states + (int64_t)j * 6 * np;
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
-      st[s * np + i] = x[s];
-      st[(3 + s) * np + i] = v[s];
+      st[s * np + i] = (unsigned long long)x[s];
+      st[(3 + s) * np + i] = bits_of_df(v[s]);
     }
     int bad = 0;
     if (KIND == FK_F64) heun_step64(a, x, v, tau, img, bad);
@@ -270,7 +281,7 @@ __device__ __forceinline__ void scatter_agg(double *gU, int64_t ncell, const ASt
 
 struct AdjArgs {
   StepArgs a;
-  const double *state;  // [6][np] state at the start of this step
+  const unsigned long long *state;  // [6][np] state at the start of this step (k_recompute)
   const double *tau;    // [np] or nullptr
   double *lam;          // [6][np] lamX, lamV in the same storage order (in/out)
   double *gU;           // [3][N^3]
@@ -284,11 +295,13 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs p) {
   const bool valid = i < p.np;
   const int64_t np = p.np, ii = valid ? i : 0;
   const int N = a.geo.N;
-  double x[3], v[3], lx[3], lv[3];
+  long long q1[3];
+  df v[3];
+  double lx[3], lv[3];
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
-    x[s] = p.state[s * np + ii];
-    v[s] = p.state[(3 + s) * np + ii];
+    q1[s] = (long long)p.state[s * np + ii];
+    v[s] = df_of_bits(p.state[(3 + s) * np + ii]);
     lx[s] = p.lam[s * np + ii];
     lv[s] = p.lam[(3 + s) * np + ii];
   }
@@ -297,20 +310,21 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs p) {
   // the forward's stage coordinates
   AStage S1, S2;
   if (KIND == FK_F64) {
-    double xs[3];
+    double x[3], xs[3];
 #pragma unroll
-    for (int s = 0; s < 3; ++s) xs[s] = predictor64(x[s], v[s], a.dt);
+    for (int s = 0; s < 3; ++s) {
+      x[s] = pos_of_fix(q1[s], a.geo);
+      xs[s] = predictor64(x[s], vel_of_df(v[s]), a.dt);
+    }
     astage_from_pos64(x, a.geo.inv_dx, N, S1);
     astage_from_pos64(xs, a.geo.inv_dx, N, S2);
   } else {
     const df cx = {a.dfk[4], a.dfk[5]};
-    long long q1[3], q2[3];
+    long long q2[3];
 #pragma unroll
-    for (int s = 0; s < 3; ++s) {
-      q1[s] = fix_stage1(x[s], a.geo.inv_dx);
-      q2[s] = KIND == FK_DF ? fix_stage2(q1[s], split_d(v[s]), cx)
-                            : fix_stage2_lo(q1[s], split_d(v[s]).h, a.dfk[4]);
-    }
+    for (int s = 0; s < 3; ++s)
+      q2[s] = KIND == FK_DF ? fix_stage2(q1[s], v[s], cx)
+                            : fix_stage2_lo(q1[s], v[s].h, a.dfk[4]);
     astage_from_fix(q1, N, S1);
     astage_from_fix(q2, N, S2);
   }
@@ -356,7 +370,7 @@ cudaError_t launch_tape_store(const StepArgs &a, const TapeSlot &t, int64_t np, 
 }
 
 cudaError_t launch_recompute(const StepArgs &a, FieldKind kind, const TapeSlot &t,
-                             double *states, int len, int64_t np, cudaStream_t st) {
+                             unsigned long long *states, int len, int64_t np, cudaStream_t st) {
   const int grid = (int)std::max<int64_t>(1, (np + 127) / 128);
   switch (kind) {
     case FK_F64: k_recompute<FK_F64><<<grid, 128, 0, st>>>(a, t, states, len, np); break;
@@ -374,7 +388,7 @@ cudaError_t launch_lam_permute(const uint32_t *id, const double *src, double *ds
   return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint(const StepArgs &a, FieldKind kind, const double *state,
+cudaError_t launch_adjoint(const StepArgs &a, FieldKind kind, const unsigned long long *state,
                            const double *tau, double *lam, double *gU, int64_t np,
                            cudaStream_t st) {
   AdjArgs p{a, state, tau, lam, gU, np};

@@ -26,6 +26,8 @@ __global__ void k_set_phase(StepArgs a);
 __global__ void k_input_meta(StepArgs a, const int64_t *seg_dev);
 __global__ void k_iota(uint32_t *p, const int64_t *cstart, int P);
 __global__ void k_compact(StepArgs a, Rec out);
+__global__ void k_import(Rec R, int64_t n, Geom g, int *status);
+__global__ void k_export(Rec R, int64_t n, Geom g);
 __global__ void k_partition_in(const uint32_t *keys, int64_t n, uint32_t nbins, uint32_t *k,
                                uint32_t *p, int32_t *status);
 __global__ void k_partition_tables(int64_t n, int64_t *cs1, int *to1, int32_t *status);
@@ -54,7 +56,8 @@ struct Ens {
   // adjoint tape: checkpoint k holds the state after k*ckpt_every steps
   std::vector<TapeSlot> tape;
   bool tape_ok = false;
-  double *states = nullptr, *lam_id = nullptr, *lam_s = nullptr;
+  unsigned long long *states = nullptr;  // recomputed states of one segment (k_recompute)
+  double *lam_id = nullptr, *lam_s = nullptr;
 };
 
 }  // namespace
@@ -509,6 +512,8 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
     g.N = d.n;
     g.L = d.box;
     g.inv_dx = (double)d.n / d.box;
+    g.fix_dx = d.box / (double)d.n / 4503599627370496.0;  // L / N / 2^52
+    g.qL = (int64_t)d.n << 52;
     g.Ptot = P;
     for (int s = 0; s < 3; ++s) {
       g.P[s] = d.sub[s];
@@ -622,6 +627,8 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
       if (B1.img[s]) C2(cudaMemsetAsync(B1.img[s], 0, e.np * 4, st));
     }
     if (B1.tau && e.np > 0) C2(cudaMemcpyAsync(B1.tau, d.tau, e.np * 8, cudaMemcpyDefault, st));
+    if (e.np > 0)  // FP64 positions and velocities -> fixed point and float pairs
+      k_import<<<grid_for(e.np, 256, c->sms * 8), 256, 0, st>>>(B1, e.np, e.a.geo, m.status);
     std::vector<int64_t> seg(P + 1, e.np);
     seg[0] = 0;
     int64_t *seg_dev = nullptr;
@@ -741,6 +748,10 @@ lcs_status lcs_set_state(lcs_ctx *c, int ens, const double *x, const double *v,
     CK(cudaMemcpyAsync(B1.tau, tau, e.np * 8, cudaMemcpyDefault, st));
   }
   if (e.np > 0) CK(cudaMemcpyAsync(B1.id, ids, e.np * 4, cudaMemcpyDefault, st));
+  if (e.np > 0) {
+    k_import<<<grid_for(e.np, 256, c->sms * 8), 256, 0, st>>>(B1, e.np, e.a.geo, e.a.m.status);
+    c->launches += 1;
+  }
   int64_t *seg_dev = nullptr;
   CK(cudaMallocAsync((void **)&seg_dev, sizeof(int64_t) * (P + 1), st));
   CK(cudaMemcpyAsync(seg_dev, seg, sizeof(int64_t) * (P + 1), cudaMemcpyHostToDevice, st));
@@ -767,7 +778,8 @@ lcs_status lcs_get_state(lcs_ctx *c, int ens, double *x, double *v, double *tau,
   const int P = e.a.geo.Ptot;
   Rec tmp = e.a.pack;
   k_compact<<<grid_for(e.np, 256, c->sms * 8), 256, 0, st>>>(e.a, tmp);
-  c->launches += 1;
+  k_export<<<grid_for(e.np, 256, c->sms * 8), 256, 0, st>>>(tmp, e.np, e.a.geo);
+  c->launches += 2;
   CK(cudaGetLastError());
   for (int s = 0; s < 3 && e.np > 0; ++s) {
     if (x) CK(cudaMemcpyAsync(x + s * e.np, tmp.x[s], e.np * 8, cudaMemcpyDefault, st));

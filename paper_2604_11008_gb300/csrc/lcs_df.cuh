@@ -94,6 +94,9 @@ __device__ __forceinline__ double df_to_double(df a) {
   return __dadd_rn(f2d_bits(a.h), f2d_bits(a.l));
 }
 
+__device__ __forceinline__ df df_from2(float2 a) { return {a.x, a.y}; }
+__device__ __forceinline__ float2 df_to2(df a) { return make_float2(a.h, a.l); }
+
 // Fixed point with 52 fraction bits of a float (truncated), as int64.
 // Valid for |f| < 2^10.
 __device__ __forceinline__ long long f_to_fix52(float f) {

@@ -39,10 +39,14 @@ constexpr long long SPIN_LIMIT = 1LL << 26;         // bounded look-back wait
 // First error wins; later errors are dropped.
 __device__ __forceinline__ void latch(int *status, int code) { atomicCAS(status, 0, code); }
 
-// Particle record buffer (structure of arrays, capacity C).
+// Particle record buffer (structure of arrays, capacity C).  Positions are
+// kept in fixed point in grid-cell units with 52 fraction bits,
+// q = RN(x N/L) 2^52 with 0 <= q < N 2^52 (the cell of a particle is q >> 52,
+// the floor of the FP64 product x N/L); velocities as unevaluated float
+// pairs (hi, lo), 48 significant bits.  The C ABI converts at its edges.
 struct Rec {
-  double *x[3];
-  double *v[3];
+  int64_t *x[3];    // fixed-point positions
+  float2 *v[3];     // velocity float pairs
   double *tau;      // nullptr when tau is a constant
   uint32_t *id;
   int32_t *img[3];  // nullptr entries when images are not tracked
@@ -64,6 +68,8 @@ struct Geom {
   int Ptot;
   double L;
   double inv_dx;   // N / L, one correctly rounded division on the host
+  double fix_dx;   // L / N / 2^52: FP64 position of a fixed-point coordinate
+  int64_t qL;      // N 2^52: the box side in fixed point
 };
 
 // Per-ensemble device metadata arrays.
@@ -253,15 +259,17 @@ int step_kernel_occupancy(FieldKind kind, int mode, int block, int items, bool p
 
 // Adjoint: checkpoint of the live particles (compacted, storage order).
 struct TapeSlot {
-  double *x, *v, *tau;  // [3][np], [3][np], [np] or nullptr
-  uint32_t *id;         // [np]
+  int64_t *x;   // [3][np] fixed-point positions
+  float2 *v;    // [3][np] velocity float pairs
+  double *tau;  // [np] or nullptr
+  uint32_t *id; // [np]
 };
 cudaError_t launch_tape_store(const StepArgs &a, const TapeSlot &t, int64_t np, cudaStream_t st);
 cudaError_t launch_recompute(const StepArgs &a, FieldKind kind, const TapeSlot &t,
-                             double *states, int len, int64_t np, cudaStream_t st);
+                             unsigned long long *states, int len, int64_t np, cudaStream_t st);
 cudaError_t launch_lam_permute(const uint32_t *id, const double *src, double *dst, int64_t np,
                                int to_storage, int *status, cudaStream_t st);
-cudaError_t launch_adjoint(const StepArgs &a, FieldKind kind, const double *state,
+cudaError_t launch_adjoint(const StepArgs &a, FieldKind kind, const unsigned long long *state,
                            const double *tau, double *lam, double *gU, int64_t np,
                            cudaStream_t st);
 

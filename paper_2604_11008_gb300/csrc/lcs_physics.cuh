@@ -257,128 +257,123 @@ static __device__ __noinline__ float drag_factor_f32(float c, float tau, const f
   return 1.0f + 0.15f * powf(c * tau * d2, 0.3435f);
 }
 
-// Heun step of Eqs. (5)-(6) (gravity g) with float-float increments:
+// Wrap a fixed-point coordinate into [0, N 2^52) (Sec. 2.1): one image per
+// step; img counts the images crossed.
+__device__ __forceinline__ long long wrap_fix(long long q, long long qL, int &img) {
+  if (q < 0) {
+    q += qL;
+    img -= 1;
+  } else if (q >= qL) {
+    q -= qL;
+    img += 1;
+  }
+  return q;
+}
+
+// Heun step of Eqs. (5)-(6) (gravity g) with float-float increments, on the
+// fixed-point position q (cell units, 52 fraction bits) and the float-pair
+// velocity V:
 //   h = dt/tau, D1 = U(X) - V, h1 = f(D1) h, V* = V + h1 D1 + dt g,
 //   X* = X + dt V, D2 = U(X*) - V*, h2 = f(D2) h,
 //   dV = (h1 D1 + h2 D2)/2 + dt g, dX = dt V + (dt/2)(h1 D1 + dt g)
-//   [= dt (V + V*)/2], with f = 1 (Stokes) or the factor of Eq. (7)
-// then X' = X + dX and V' = V + dV in FP64, and the periodic wrap.
+//   [= dt (V + V*)/2], with f = 1 (Stokes) or the factor of Eq. (7);
+// then q' = q + (N/L) dX in fixed point (exact addition), V' = V + dV in
+// float-float, and the periodic wrap.  No FP64 instruction on the Stokes path.
 template <int KIND>
-__device__ __forceinline__ void heun_step_df(const StepArgs &a, double x[3], double v[3],
+__device__ __forceinline__ void heun_step_df(const StepArgs &a, long long q[3], df V[3],
                                              double tau, int img[3], int &bad,
                                              const FieldBox &box = FieldBox{}) {
   const Geom &g = a.geo;
-  const df dt = {a.dfk[0], a.dfk[1]}, hdt = {a.dfk[2], a.dfk[3]}, cx = {a.dfk[4], a.dfk[5]};
+  const df dt = {a.dfk[0], a.dfk[1]}, cx = {a.dfk[4], a.dfk[5]};
+  const df hcx = df_scale2(cx, 0.5f);  // (dt/2) N/L
   const df h = df_mul(dt, df_recip(split_d(tau)));
-  long long q[3];
-  df V[3], U[3], hD1[3], Vs[3];
-#pragma unroll
-  for (int s = 0; s < 3; ++s) q[s] = fix_stage1(x[s], g.inv_dx);
+  long long q2[3];
+  df U[3], hD1[3], Vs[3], D[3];
   interp_any<KIND>(a.field, g.N, q, U, box);
-  df D[3];
 #pragma unroll
-  for (int s = 0; s < 3; ++s) {
-    V[s] = split_d(v[s]);
-    D[s] = df_add(U[s], df_neg(V[s]));
-  }
+  for (int s = 0; s < 3; ++s) D[s] = df_add(U[s], df_neg(V[s]));
   const df h1 = a.drag ? df_mul(h, drag_factor_df(a.drag_c, tau, D)) : h;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     const df gd = {a.dfk[6 + 2 * s], a.dfk[7 + 2 * s]};
     hD1[s] = df_mul(h1, D[s]);
     Vs[s] = df_add(df_add(V[s], hD1[s]), gd);
-    q[s] = fix_stage2(q[s], V[s], cx);
+    q2[s] = fix_stage2(q[s], V[s], cx);
   }
-  interp_any<KIND>(a.field, g.N, q, U, box);
+  interp_any<KIND>(a.field, g.N, q2, U, box);
 #pragma unroll
   for (int s = 0; s < 3; ++s) D[s] = df_add(U[s], df_neg(Vs[s]));
   const df h2 = a.drag ? df_mul(h, drag_factor_df(a.drag_c, tau, D)) : h;
-  const long long bitsL = __double_as_longlong(g.L);
+  const float half_box = 0.5f * (float)g.N;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     const df gd = {a.dfk[6 + 2 * s], a.dfk[7 + 2 * s]};
     const df hD2 = df_mul(h2, D[s]);
     const df dV = df_add(df_scale2(df_add(hD1[s], hD2), 0.5f), gd);
-    const df dX = df_add(df_mul(dt, V[s]), df_mul(hdt, df_add(hD1[s], gd)));
-    if (!(fabsf(dX.h) < (float)(0.5 * g.L))) bad |= 2;
-    double xn = __dadd_rn(x[s], df_to_double(dX));
-    const double vn = __dadd_rn(v[s], df_to_double(dV));
-    const long long bx = __double_as_longlong(xn);
-    if (((bx >> 52) & 0x7ff) == 0x7ff || ((__double_as_longlong(vn) >> 52) & 0x7ff) == 0x7ff)
-      bad |= 1;
-    if (bx < 0) {
-      xn = __dadd_rn(xn, g.L);
-      img[s] -= 1;
-    } else if (bx >= bitsL) {
-      xn = __dsub_rn(xn, g.L);
-      img[s] += 1;
-    }
-    if (__double_as_longlong(xn) == bitsL) xn = 0.0;
-    x[s] = xn;
-    v[s] = vn;
+    // displacement in cell units: (dt N/L) V + (dt/2 N/L)(h1 D1 + dt g)
+    const df dXc = df_add(df_mul(cx, V[s]), df_mul(hcx, df_add(hD1[s], gd)));
+    const df vn = df_add(V[s], dV);
+    if (!(fabsf(dXc.h) < half_box)) bad |= isfinite(dXc.h) ? 2 : 1;
+    if (!isfinite(vn.h)) bad |= 1;
+    q[s] = wrap_fix(q[s] + f_to_fix52(dXc.h) + f_to_fix52(dXc.l), g.qL, img[s]);
+    V[s] = vn;
   }
 }
 
 // Heun step of Eqs. (5)-(6) for FP32 / BF16 field storage: the same
 // formulas as heun_step_df with the increments in FP32 (the field itself
-// carries 2^-24 or 2^-8 relative error), accumulated into the FP64 state
-// X' = X + dX, V' = V + dV; the cell coordinates stay the exact fixed-point
-// ones.
+// carries 2^-24 or 2^-8 relative error), accumulated exactly into the
+// fixed-point position and in float-float into the velocity.
 template <int KIND>
-__device__ __forceinline__ void heun_step_lo(const StepArgs &a, double x[3], double v[3],
+__device__ __forceinline__ void heun_step_lo(const StepArgs &a, long long q[3], df V[3],
                                              double tau, int img[3], int &bad,
                                              const FieldBox &box = FieldBox{}) {
   const Geom &g = a.geo;
   const float dt = a.dfk[0], cx = a.dfk[4];
-  const float h = dt * __frcp_rn(split_d(tau).h);
-  long long q[3];
+  const float taus = split_d(tau).h;
+  const float h = dt * __frcp_rn(taus);
+  long long q2[3];
   df U[3];
-  float V[3], hD1[3], Vs[3];
-#pragma unroll
-  for (int s = 0; s < 3; ++s) q[s] = fix_stage1(x[s], g.inv_dx);
+  float hD1[3], Vs[3], D[3];
   interp_lo<KIND>(a.field, g.N, q, U, box);
-  float D[3];
 #pragma unroll
-  for (int s = 0; s < 3; ++s) {
-    V[s] = split_d(v[s]).h;
-    D[s] = U[s].h - V[s];
-  }
-  const float h1 = a.drag ? h * drag_factor_f32((float)a.drag_c, split_d(tau).h, D) : h;
+  for (int s = 0; s < 3; ++s) D[s] = U[s].h - V[s].h;
+  const float h1 = a.drag ? h * drag_factor_f32((float)a.drag_c, taus, D) : h;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     const float gd = a.dfk[6 + 2 * s];
     hD1[s] = h1 * D[s];
-    Vs[s] = V[s] + hD1[s] + gd;
-    q[s] = fix_stage2_lo(q[s], V[s], cx);
+    Vs[s] = V[s].h + hD1[s] + gd;
+    q2[s] = fix_stage2_lo(q[s], V[s].h, cx);
   }
-  interp_lo<KIND>(a.field, g.N, q, U, box);
+  interp_lo<KIND>(a.field, g.N, q2, U, box);
 #pragma unroll
   for (int s = 0; s < 3; ++s) D[s] = U[s].h - Vs[s];
-  const float h2 = a.drag ? h * drag_factor_f32((float)a.drag_c, split_d(tau).h, D) : h;
-  const long long bitsL = __double_as_longlong(g.L);
+  const float h2 = a.drag ? h * drag_factor_f32((float)a.drag_c, taus, D) : h;
+  const float half_box = 0.5f * (float)g.N;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     const float gd = a.dfk[6 + 2 * s];
     const float hD2 = h2 * D[s];
     const float dV = 0.5f * (hD1[s] + hD2) + gd;
-    const float dX = dt * (V[s] + 0.5f * (hD1[s] + gd));
-    if (!(fabsf(dX) < (float)(0.5 * g.L))) bad |= 2;
-    double xn = __dadd_rn(x[s], f2d_bits(dX));
-    const double vn = __dadd_rn(v[s], f2d_bits(dV));
-    const long long bx = __double_as_longlong(xn);
-    if (((bx >> 52) & 0x7ff) == 0x7ff || ((__double_as_longlong(vn) >> 52) & 0x7ff) == 0x7ff)
-      bad |= 1;
-    if (bx < 0) {
-      xn = __dadd_rn(xn, g.L);
-      img[s] -= 1;
-    } else if (bx >= bitsL) {
-      xn = __dsub_rn(xn, g.L);
-      img[s] += 1;
-    }
-    if (__double_as_longlong(xn) == bitsL) xn = 0.0;
-    x[s] = xn;
-    v[s] = vn;
+    const float dXc = cx * (V[s].h + 0.5f * (hD1[s] + gd));  // cell units
+    const df vn = df_add(V[s], df{dV, 0.f});
+    if (!(fabsf(dXc) < half_box)) bad |= isfinite(dXc) ? 2 : 1;
+    if (!isfinite(vn.h)) bad |= 1;
+    q[s] = wrap_fix(q[s] + f_to_fix52(dXc), g.qL, img[s]);
+    V[s] = vn;
   }
+}
+
+// FP64 position of a fixed-point coordinate and velocity of a float pair
+// (the all-FP64 kernel and its adjoint read the state through these).
+__device__ __forceinline__ double pos_of_fix(long long q, const Geom &g) {
+  return __dmul_rn(__ll2double_rn(q), g.fix_dx);
+}
+__device__ __forceinline__ double vel_of_df(df v) { return __dadd_rn((double)v.h, (double)v.l); }
+__device__ __forceinline__ df df_of_double(double v) {
+  const float h = __double2float_rn(v);
+  return {h, __double2float_rn(__dsub_rn(v, (double)h))};
 }
 
 // Drag factor of Eq. (7) in FP64 (see drag_factor_df).
@@ -390,13 +385,20 @@ static __device__ __noinline__ double drag_factor64(double c, double tau, const 
   return 1.0 + 0.15 * pow(c * tau * d2, 0.3435);
 }
 
-// One Heun step of Eqs. (5)-(6) (gravity g; f = 1 or Eq. 7) with periodic
-// wrap, in FP64.
-__device__ __forceinline__ void heun_step64(const StepArgs &a, double x[3], double v[3],
+// One Heun step of Eqs. (5)-(6) (gravity g; f = 1 or Eq. 7) in FP64
+// arithmetic: the state is read as FP64 position and velocity, advanced with
+// FP64 operations only, and stored back (position rounded to the fixed-point
+// grid of 2^-52 cells, velocity to a float pair), then wrapped.
+__device__ __forceinline__ void heun_step64(const StepArgs &a, long long q[3], df V[3],
                                           double tau, int img[3], int &bad) {
   const Geom &g = a.geo;
   const double itau = 1.0 / tau;
-  double u1[3], a1[3], xs[3], vs[3], u2[3];
+  double x[3], v[3], u1[3], a1[3], xs[3], vs[3], u2[3];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    x[s] = pos_of_fix(q[s], g);
+    v[s] = vel_of_df(V[s]);
+  }
   interp64(a.field, g, x[0], x[1], x[2], u1[0], u1[1], u1[2]);
   const double f1 = a.drag ? drag_factor64(a.drag_c, tau, u1, v) * itau : itau;
 #pragma unroll
@@ -410,20 +412,12 @@ __device__ __forceinline__ void heun_step64(const StepArgs &a, double x[3], doub
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     const double a2 = (u2[s] - vs[s]) * f2 + a.g[s];
-    double xn = x[s] + a.half_dt * (v[s] + vs[s]);
+    const double xn = x[s] + a.half_dt * (v[s] + vs[s]);
     const double vn = v[s] + a.half_dt * (a1[s] + a2);
     if (!(fabs(xn - x[s]) < 0.5 * g.L)) bad |= fabs(xn) <= 1e300 ? 2 : 1;
     if (!isfinite(vn)) bad |= 1;
-    if (xn >= g.L) {
-      xn -= g.L;
-      img[s] += 1;
-    } else if (xn < 0.0) {
-      xn += g.L;
-      img[s] -= 1;
-    }
-    if (xn == g.L) xn = 0.0;
-    x[s] = xn;
-    v[s] = vn;
+    q[s] = wrap_fix(d_to_fix52(__dmul_rn(xn, g.inv_dx)), g.qL, img[s]);
+    V[s] = df_of_double(vn);
   }
 }
 

@@ -9,6 +9,7 @@
 // prefix-scan-gives-the-slot idea as the particle pack of Sec. 2.3.3 -- and
 // a stable scatter that ranks equal digits inside a tile with warp match
 // masks, in input order.
+#include "lcs_df.cuh"
 #include "lcs_internal.cuh"
 
 namespace lcs {
@@ -233,8 +234,9 @@ __device__ __forceinline__ int find_segment64(const int64_t *off, int P, int64_t
   return lo;
 }
 
-__device__ __forceinline__ int cell_of(const Geom &g, double x) {
-  const int c = (int)floor(__dmul_rn(x, g.inv_dx));
+// Containing cell of a fixed-point coordinate (its integer part).
+__device__ __forceinline__ int cell_of(const Geom &g, long long q) {
+  const int c = (int)(q >> 52);
   return min(max(c, 0), g.N - 1);
 }
 
@@ -280,9 +282,9 @@ __global__ void k_keys_dest(StepArgs a, uint32_t *key, uint32_t *pay) {
     int p[3];
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
-      const double x = A.x[s][slot];
-      if (!(x >= 0.0 && x < a.geo.L)) latch(a.m.status, LCS_ERR_ARG);
-      p[s] = cell_of(a.geo, x) / a.geo.W[s];
+      const long long q = A.x[s][slot];
+      if (!(q >= 0 && q < a.geo.qL)) latch(a.m.status, LCS_ERR_ARG);
+      p[s] = cell_of(a.geo, q) / a.geo.W[s];
     }
     const uint32_t d = (uint32_t)(p[0] + a.geo.P[0] * (p[1] + a.geo.P[1] * p[2]));
     key[i] = 2u * d + (d != (uint32_t)seg ? 1u : 0u);
@@ -383,6 +385,56 @@ __global__ void k_compact(StepArgs a, Rec out) {
        i += (int64_t)gridDim.x * blockDim.x) {
     const int seg = find_segment64(a.m.cstart, P, i);
     copy_rec(A, base[seg] + (i - a.m.cstart[seg]), out, i);
+  }
+}
+
+// The C ABI's FP64 state <-> the records' fixed-point positions and
+// float-pair velocities, in place on the first n records of R (the FP64
+// values occupy the same 8-byte slots).
+//   import: q = RN(x N/L) 2^52 exactly (the product has at most 53 bits, of
+//           which at least 42 are fraction bits for N <= 1024); a position
+//           outside [0, L) or non-finite latches LCS_ERR_ARG; a product that
+//           rounds up to N maps to the last fixed-point value below N, so
+//           that the cell is min(floor(x N/L), N-1) as before;
+//           v -> (RN32(v), RN32(v - hi)) (a non-finite velocity is reported
+//           as LCS_ERR_NONFINITE by the next step).
+//   export: x = RN(RN(q) L/N 2^-52), kept below L; v = hi + lo exactly.
+__device__ __forceinline__ unsigned long long import_pos(double x, const Geom &g, int *status) {
+  if (!(x >= 0.0 && x < g.L)) {
+    latch(status, LCS_ERR_ARG);
+    return 0ull;
+  }
+  long long q = d_to_fix52(__dmul_rn(x, g.inv_dx));
+  if (q >= g.qL) q = g.qL - 1;
+  return (unsigned long long)q;
+}
+
+__global__ void k_import(Rec R, int64_t n, Geom g, int *status) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      const double x = __longlong_as_double((long long)R.x[s][i]);
+      R.x[s][i] = (int64_t)import_pos(x, g, status);
+      const double v = __longlong_as_double(*(const long long *)&R.v[s][i]);
+      const float h = __double2float_rn(v);  // non-finite values surface in the next step
+      R.v[s][i] = make_float2(h, __double2float_rn(v - (double)h));
+    }
+  }
+}
+
+__global__ void k_export(Rec R, int64_t n, Geom g) {
+  const double below_L = __longlong_as_double(__double_as_longlong(g.L) - 1);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      double x = __dmul_rn(__ll2double_rn((long long)R.x[s][i]), g.fix_dx);
+      if (x >= g.L) x = below_L;
+      R.x[s][i] = __double_as_longlong(x);
+      const float2 p = R.v[s][i];
+      *(double *)&R.v[s][i] = (double)p.x + (double)p.y;
+    }
   }
 }
 

@@ -200,25 +200,25 @@ __device__ __forceinline__ unsigned long long lookback_warp(unsigned long long *
 
 // ---------------------------------------------------------------- step kernel
 
-__device__ __forceinline__ void load_rec(const Rec &R, int64_t i, double x[3], double v[3],
+__device__ __forceinline__ void load_rec(const Rec &R, int64_t i, long long x[3], df v[3],
                                          double &tau, uint32_t &id, int img[3], double tau_c) {
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     x[s] = R.x[s][i];
-    v[s] = R.v[s][i];
+    v[s] = df_from2(R.v[s][i]);
     img[s] = R.img[s] ? R.img[s][i] : 0;
   }
   tau = R.tau ? R.tau[i] : tau_c;
   id = R.id[i];
 }
 
-__device__ __forceinline__ void store_rec(const Rec &R, int64_t i, const double x[3],
-                                          const double v[3], double tau, uint32_t id,
+__device__ __forceinline__ void store_rec(const Rec &R, int64_t i, const long long x[3],
+                                          const df v[3], double tau, uint32_t id,
                                           const int img[3]) {
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     R.x[s][i] = x[s];
-    R.v[s][i] = v[s];
+    R.v[s][i] = df_to2(v[s]);
     if (R.img[s]) R.img[s][i] = img[s];
   }
   if (R.tau) R.tau[i] = tau;
@@ -227,13 +227,12 @@ __device__ __forceinline__ void store_rec(const Rec &R, int64_t i, const double 
 
 // Destination direction bin (0..26, 13 = stay) of a particle at x from
 // segment `seg`; -1 if the destination is not a neighbour.
-__device__ __forceinline__ int dest_bin(const Geom &g, const int ps[3], const double x[3]) {
+__device__ __forceinline__ int dest_bin(const Geom &g, const int ps[3], const long long x[3]) {
   int bin = 0, mul = 1;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
-    // floor of the correctly rounded product x N/L (x >= 0 after the wrap),
-    // taken from its fixed-point form without the FP64 floor
-    int c = (int)(d_to_fix52(__dmul_rn(x[s], g.inv_dx)) >> 52);
+    // the containing cell: integer part of the fixed-point coordinate
+    int c = (int)(x[s] >> 52);
     c = min(max(c, 0), g.N - 1);
     const int dc = dir_comp(ps[s], (int)__umulhi((unsigned)c, g.Wrcp[s]), g.P[s]);
     if (dc == 2) return -1;
@@ -333,17 +332,17 @@ __device__ __forceinline__ void pf_issue(const StepArgs &a, const TileMeta &m, b
 
 template <int T>
 __device__ __forceinline__ void pf_read(const Rec &A, const TileMeta &m, bool lay_tau,
-                                        const unsigned char *buf, int li, double x[3],
-                                        double v[3], double &tau, uint32_t &id, int img[3],
+                                        const unsigned char *buf, int li, long long x[3],
+                                        df v[3], double &tau, uint32_t &id, int img[3],
                                         double tau_c) {
   using LY = PfLayout<T>;
-  const double *r8 = (const double *)buf + m.o8 + li;
+  const long long *r8 = (const long long *)buf + m.o8 + li;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     x[s] = r8[s * (T + 2)];
-    v[s] = r8[(3 + s) * (T + 2)];
+    v[s] = df_from2(((const float2 *)r8)[(3 + s) * (T + 2)]);
   }
-  tau = A.tau ? r8[6 * (T + 2)] : tau_c;
+  tau = A.tau ? __longlong_as_double(r8[6 * (T + 2)]) : tau_c;
   const uint32_t *r4 = (const uint32_t *)(buf + (lay_tau ? 7 : 6) * LY::S8) + m.o4 + li;
   id = r4[0];
 #pragma unroll
@@ -368,7 +367,9 @@ __device__ __forceinline__ void step_block_tile(const StepArgs &a, const TileMet
   const int64_t cnt = mt.cnt;
   const int64_t l0 = mt.first + (int64_t)threadIdx.x * ITEMS;
   const int64_t bA = mt.bA;
-  double x[ITEMS][3], v[ITEMS][3], tau[ITEMS];
+  long long x[ITEMS][3];
+  df v[ITEMS][3];
+  double tau[ITEMS];
   uint32_t id[ITEMS];
   int img[ITEMS][3], bin[ITEMS];
   unsigned packed = 0;
@@ -382,10 +383,10 @@ __device__ __forceinline__ void step_block_tile(const StepArgs &a, const TileMet
   };
   FieldBox box{nullptr, 0, 0, 0, 0, 0, 0};
   if (STAGED && KIND != FK_F64) {
-    // Shared-memory box of the tile's field cells: bounding box of the cells
-    // of all its particles (FP32 positions, so padded by 2 cells below and 3
-    // above for rounding, the stencil's +1 corner and the predictor's move),
-    // copied cooperatively when it fits in STAGE_BYTES.
+    // Shared-memory box of the tile's field cells: bounding box of the
+    // stencil base cells of all its particles, padded by 2 cells below and 3
+    // above for the stencil's +1 corner and the predictor's move, copied
+    // cooperatively when it fits in STAGE_BYTES.
     int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
@@ -393,8 +394,8 @@ __device__ __forceinline__ void step_block_tile(const StepArgs &a, const TileMet
         load_item(k);
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          int c = __float2int_rd(split_d(x[k][d]).h * (float)a.geo.inv_dx - 0.5f);
-          c = min(max(c, -8), a.geo.N + 8);  // non-finite positions: any box is safe
+          int c = (int)((x[k][d] - (1ll << 51)) >> 52);  // stencil base cell
+          c = min(max(c, -8), a.geo.N + 8);
           lo[d] = min(lo[d], c);
           hi[d] = max(hi[d], c);
         }
@@ -558,16 +559,16 @@ struct ParkLayout {
 
 template <int T>
 __device__ __forceinline__ void park_put(unsigned char *pk, bool lay_tau, bool lay_img,
-                                         const Rec &A, int j, const double x[3],
-                                         const double v[3], double tau, uint32_t id,
+                                         const Rec &A, int j, const long long x[3],
+                                         const df v[3], double tau, uint32_t id,
                                          const int img[3], int bin) {
-  double *r8 = (double *)pk;
+  long long *r8 = (long long *)pk;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     r8[s * T + j] = x[s];
-    r8[(3 + s) * T + j] = v[s];
+    ((float2 *)r8)[(3 + s) * T + j] = df_to2(v[s]);
   }
-  if (A.tau) r8[6 * T + j] = tau;
+  if (A.tau) r8[6 * T + j] = __double_as_longlong(tau);
   uint32_t *r4 = (uint32_t *)(pk + (lay_tau ? 7 : 6) * T * 8);
   r4[j] = id;
   if (A.img[0]) {
@@ -581,13 +582,13 @@ __device__ __forceinline__ void park_put(unsigned char *pk, bool lay_tau, bool l
 template <int T>
 __device__ __forceinline__ void park_get(const unsigned char *pk, bool lay_tau, bool lay_img,
                                          int j, const Rec &R, int64_t i, uint8_t *bins) {
-  const double *r8 = (const double *)pk;
+  const long long *r8 = (const long long *)pk;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     R.x[s][i] = r8[s * T + j];
-    R.v[s][i] = r8[(3 + s) * T + j];
+    R.v[s][i] = ((const float2 *)r8)[(3 + s) * T + j];
   }
-  if (R.tau) R.tau[i] = r8[6 * T + j];
+  if (R.tau) R.tau[i] = __longlong_as_double(r8[6 * T + j]);
   const uint32_t *r4 = (const uint32_t *)(pk + (lay_tau ? 7 : 6) * T * 8);
   R.id[i] = r4[j];
   if (R.img[0]) {
@@ -602,8 +603,8 @@ __device__ __forceinline__ void park_get(const unsigned char *pk, bool lay_tau, 
 // packed (stay << 16 | leave) count and the block's direction histogram.
 template <int KIND, int ITEMS>
 __device__ __forceinline__ unsigned integrate_items(const StepArgs &a, const TileMeta &mt,
-                                                    BlockShared &sh, double x[][3],
-                                                    double v[][3], double tau[], uint32_t id[],
+                                                    BlockShared &sh, long long x[][3],
+                                                    df v[][3], double tau[], uint32_t id[],
                                                     int img[][3], int bin[]) {
   const Rec &A = a.buf[mt.ph];
   const int64_t l0 = mt.first + (int64_t)threadIdx.x * ITEMS;
@@ -658,7 +659,9 @@ __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockSha
     __syncthreads();
     const int g = sh.tile;
     const bool fresh = g < total;
-    double x[ITEMS][3], v[ITEMS][3], tau[ITEMS];
+    long long x[ITEMS][3];
+  df v[ITEMS][3];
+  double tau[ITEMS];
     uint32_t id[ITEMS];
     int img[ITEMS][3], bin[ITEMS];
     unsigned packed = 0;
