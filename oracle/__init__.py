@@ -50,7 +50,7 @@ def _load():
             i64, i32, dbl = C.c_int64, C.c_int, C.c_double
             lib.orc_interp_many.argtypes = [P, i32, dbl, i64, P, P, P, P, P, P]
             lib.orc_advance.argtypes = [P, i32, dbl, dbl, i64, P, P, P, P, P, P, P, dbl, dbl, P,
-                                        i32, P, P, i32, dbl, dbl]
+                                        i32, P, P, i32, dbl, dbl, P, dbl, dbl, dbl]
             lib.orc_advance.restype = i32
             lib.orc_keys.argtypes = [i32, dbl, P, i32, i64, P, P, P, P, P]
             lib.orc_keys.restype = i32
@@ -116,8 +116,10 @@ STOKES = (0, 0.0, 0.0)
 
 
 def advance(field, L, x, v, tau, tau_const, dt, g, nsteps, img=None, cellhash=None,
-            drag=STOKES):
-    """Heun steps of Eqs. (5)-(6) with wrap, in place on x, v (3, n) float64 C arrays."""
+            drag=STOKES, field_b=None, times=(0.0, 0.0, 1.0)):
+    """Heun steps of Eqs. (5)-(6) with wrap, in place on x, v (3, n) float64 C arrays.
+    With field_b, the field is linear in time between `field` at t_a and
+    field_b at t_b; times = (t_start, t_a, t_b)."""
     lib = _load()
     field = _c(field, np.float64)
     N = field.shape[-1]
@@ -125,11 +127,13 @@ def advance(field, L, x, v, tau, tau_const, dt, g, nsteps, img=None, cellhash=No
     n = x.shape[1]
     tau = None if tau is None else _c(tau, np.float64)
     gg = _c(g, np.float64)
+    fb = None if field_b is None else _c(field_b, np.float64)
     return lib.orc_advance(_p(field), N, float(L), inv_dx(N, L), n, _p(x[0]), _p(x[1]),
                            _p(x[2]), _p(v[0]), _p(v[1]), _p(v[2]), _p(tau), float(tau_const),
                            float(dt), _p(gg), int(nsteps), _p(img), _p(cellhash),
                            int(drag[0]), float(drag[1]) if drag[0] else 0.0,
-                           float(drag[2]) if drag[0] else 0.0)
+                           float(drag[2]) if drag[0] else 0.0, _p(fb), float(times[0]),
+                           float(times[1]), float(times[2]))
 
 
 def keys(N, L, P, brick, x):
@@ -263,10 +267,12 @@ def initial_state(N, L, P, x, v, tau, ids=None, track_img=False):
     return st
 
 
-def step(st: State, field, L, P, tau_const, dt, g, brick, do_sort: bool, drag=STOKES):
+def step(st: State, field, L, P, tau_const, dt, g, brick, do_sort: bool, drag=STOKES,
+         field_b=None, times=(0.0, 0.0, 1.0)):
     """One step of the path: advance + wrap, migrate, and (if do_sort) the cell sort."""
     N = field.shape[-1]
-    status = advance(field, L, st.x, st.v, st.tau, tau_const, dt, g, 1, img=st.img, drag=drag)
+    status = advance(field, L, st.x, st.v, st.tau, tau_const, dt, g, 1, img=st.img, drag=drag,
+                     field_b=field_b, times=times)
     dest, key = keys(N, L, P, brick, st.x)
     perm, seg_out, _ = migrate(int(np.prod(P)), st.seg, dest)
     st.permute(perm)
@@ -279,11 +285,14 @@ def step(st: State, field, L, P, tau_const, dt, g, brick, do_sort: bool, drag=ST
 
 
 def run(st: State, field, L, P, tau_const, dt, g, nsteps, sort_every=0, brick=8, step0=0,
-        drag=STOKES):
-    """nsteps steps; the sort runs after steps whose 1-based index is a multiple of sort_every."""
+        drag=STOKES, field_b=None, t_start=0.0, t_field=(0.0, 1.0)):
+    """nsteps steps; the sort runs after steps whose 1-based index is a multiple of sort_every.
+    With field_b the field is linear in time between `field` at t_field[0] and
+    field_b at t_field[1]; step k (counted from step0) starts at t_start + k dt."""
     status = ORC_OK
     for k in range(step0, step0 + nsteps):
         s = step(st, field, L, P, tau_const, dt, g, brick,
-                 sort_every > 0 and (k + 1) % sort_every == 0, drag=drag)
+                 sort_every > 0 and (k + 1) % sort_every == 0, drag=drag, field_b=field_b,
+                 times=(t_start + k * dt, t_field[0], t_field[1]))
         status = status or s
     return status

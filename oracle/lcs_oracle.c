@@ -8,10 +8,11 @@
  *
  *   orc_interp        trilinear interpolation from the eight surrounding
  *                     cell-centre values (Sec. 2.2, last paragraph)
- *   orc_advance       particle ODE dX/dt = V, dV/dt = -(f/tau_p)(V - U(X))
+ *   orc_advance       particle ODE dX/dt = V, dV/dt = -(f/tau_p)(V - U(X, t))
  *                     (Eqs. 5-6) with f = 1 (Stokes drag) or the nonlinear
  *                     drag factor of Eq. (7), plus an optional
- *                     constant gravity g, advanced with the two-stage
+ *                     constant gravity g, in a frozen field or one linear in
+ *                     time between two snapshots, advanced with the two-stage
  *                     second-order Runge-Kutta method of Sec. 2.2 read as
  *                     Heun's method, then periodic wrap into [0, L)
  *                     (periodic cube of side L, Sec. 2.1)
@@ -132,13 +133,30 @@ static double drag_factor(double tp, double nu, double rr, const double vrel[3])
   return 1.0 + 0.15 * pow(re, 0.687);
 }
 
+/* Fluid velocity at position p and time fraction theta between two field
+ * snapshots (the coupling to an evolving Eulerian field, U(X, t) of Eq. 6):
+ * U = (1 - theta) U_a(p) + theta U_b(p), linear in time; U_a alone when
+ * fb is NULL (frozen field). */
+static void fluid_velocity(const double *fa, const double *fb, double theta, int N,
+                           double inv_dx, const double p[3], double u[3]) {
+  orc_interp(fa, N, inv_dx, p[0], p[1], p[2], u);
+  if (!fb) return;
+  double ub[3];
+  orc_interp(fb, N, inv_dx, p[0], p[1], p[2], ub);
+  for (int s = 0; s < 3; ++s) u[s] = (1.0 - theta) * u[s] + theta * ub[s];
+}
+
 /* Advance n particles by nsteps Heun steps of Eqs. (5)-(6):
  *   A1 = f1 (U(X) - V)/tau + g,   X* = X + dt V,   V* = V + dt A1,
  *   A2 = f2 (U(X*) - V*)/tau + g,
  *   X' = X + dt/2 (V + V*),    V' = V + dt/2 (A1 + A2),
  * then wrap X' into [0, L).  drag = 0: f1 = f2 = 1 (Stokes drag); drag = 1:
  * f1, f2 from Eq. (7) with the relative velocity of their stage (nu, rr as
- * in drag_factor).  tau may be NULL (then tau_const for all).
+ * in drag_factor).  With a second snapshot field_b (time t_b; field at
+ * t_a), step k of the call starts at t = t_start + k dt and its two stages
+ * see the field at t and t + dt:
+ *   U1 = U(X, t),  U2 = U(X*, t + dt),  theta(t) = (t - t_a) / (t_b - t_a)
+ * (field_b NULL: the frozen field).  tau may be NULL (then tau_const for all).
  * img (3*n int32, SoA) counts the periodic images crossed (may be NULL).
  * cellhash (n uint64, may be NULL) folds in the floor index of every gather,
  * so that two runs which visit different interpolation cells can be told
@@ -147,12 +165,17 @@ static double drag_factor(double tp, double nu, double rr, const double vrel[3])
 int orc_advance(const double *field, int N, double L, double inv_dx, int64_t n, double *x,
                 double *y, double *z, double *vx, double *vy, double *vz, const double *tau,
                 double tau_const, double dt, const double *g, int nsteps, int32_t *img,
-                uint64_t *cellhash, int drag, double nu, double rr) {
+                uint64_t *cellhash, int drag, double nu, double rr, const double *field_b,
+                double t_start, double t_a, double t_b) {
   int status = ORC_OK;
   double *X[3] = {x, y, z};
   double *V[3] = {vx, vy, vz};
   if (drag != 0 && (drag != 1 || !(nu > 0.0) || !(rr > 0.0))) return ORC_ERR_ARG;
+  if (field_b && !(t_b > t_a)) return ORC_ERR_ARG;
   for (int step = 0; step < nsteps; ++step) {
+    const double t = t_start + step * dt;
+    const double th1 = field_b ? (t - t_a) / (t_b - t_a) : 0.0;
+    const double th2 = field_b ? (t + dt - t_a) / (t_b - t_a) : 0.0;
     for (int64_t p = 0; p < n; ++p) {
       const double tp = tau ? tau[p] : tau_const;
       double x0[3], v0[3], u1[3], a1[3], xs[3], vs[3], u2[3], a2[3];
@@ -160,7 +183,7 @@ int orc_advance(const double *field, int N, double L, double inv_dx, int64_t n, 
         x0[s] = X[s][p];
         v0[s] = V[s][p];
       }
-      orc_interp(field, N, inv_dx, x0[0], x0[1], x0[2], u1);
+      fluid_velocity(field, field_b, th1, N, inv_dx, x0, u1);
       if (cellhash) cellhash[p] = cell_hash(cellhash[p], inv_dx, x0);
       double f1 = 1.0, f2 = 1.0;
       if (drag) {
@@ -172,7 +195,7 @@ int orc_advance(const double *field, int N, double L, double inv_dx, int64_t n, 
         xs[s] = x0[s] + dt * v0[s];
         vs[s] = v0[s] + dt * a1[s];
       }
-      orc_interp(field, N, inv_dx, xs[0], xs[1], xs[2], u2);
+      fluid_velocity(field, field_b, th2, N, inv_dx, xs, u2);
       if (cellhash) cellhash[p] = cell_hash(cellhash[p], inv_dx, xs);
       if (drag) {
         const double rel[3] = {vs[0] - u2[0], vs[1] - u2[1], vs[2] - u2[2]};
@@ -442,7 +465,7 @@ int orc_adjoint(const double *field, int N, double L, double inv_dx, int64_t n,
     memcpy(dst, src, per * sizeof(double));
     int st = orc_advance(field, N, L, inv_dx, n, dst, dst + n, dst + 2 * n, dst + 3 * n,
                          dst + 4 * n, dst + 5 * n, tau, tau_const, dt, g, 1, NULL, NULL, 0,
-                         0.0, 0.0);
+                         0.0, 0.0, NULL, 0.0, 0.0, 0.0);
     if (st != ORC_OK) status = st;
   }
   for (int k = nsteps - 1; k >= 0; --k) {

@@ -236,6 +236,56 @@ def test_nonlinear_drag_rejects_bad_parameters():
         assert st == oracle.ORC_ERR_ARG
 
 
+def test_evolving_field_converges_second_order_to_exact_solution():
+    """Two uniform snapshots U_a at t_a and U_b at t_b: the fluid velocity is
+    U(t) = c0 + c1 t, and dV/dt = (U(t) - V)/tau + g has the exact solution
+    V = c0 + c1 t + tau g - tau c1 + (V0 - c0 - tau g + tau c1) e^{-t/tau}
+    (and X by integration).  Heun with the stage times t and t + dt converges
+    at second order; evaluating the second stage at the wrong time would
+    leave a first-order error."""
+    N, T = 4, 0.5
+    Ua, Ub = np.array([0.4, -0.3, 0.2]), np.array([-0.6, 0.5, 1.1])
+    ta, tb, t0 = -0.2, 0.8, 0.1
+    fa, fb = uniform_field(N, Ua), uniform_field(N, Ub)
+    gvec = np.array([0.0, 0.3, -1.0])
+    c1 = (Ub - Ua) / (tb - ta)
+    rng = np.random.default_rng(17)
+    n = 6
+    x0 = rng.random((3, n)) * L
+    v0 = rng.standard_normal((3, n))
+    tau = np.array([0.05, 0.1, 0.2, 0.3, 0.5, 1.0])
+
+    def exact(t):  # time measured from t0
+        c0 = Ua + (t0 - ta) * c1                 # U at the start time
+        vinf0 = c0[:, None] + tau * gvec[:, None] - tau * c1[:, None]
+        a = v0 - vinf0
+        e = np.exp(-t / tau)
+        v = vinf0 + c1[:, None] * t + a * e
+        x = x0 + vinf0 * t + 0.5 * c1[:, None] * t * t + tau * a * (1 - e)
+        return x, v
+
+    xr, vr = exact(T)
+    errs = []
+    for steps in (50, 100, 200, 400):
+        x, v = x0.copy(), v0.copy()
+        img = np.zeros((3, n), np.int32)
+        st = oracle.advance(fa, L, x, v, tau, 0.0, T / steps, gvec, steps, img=img, field_b=fb,
+                            times=(t0, ta, tb))
+        assert st == oracle.ORC_OK
+        errs.append(max(np.max(np.abs(x + L * img - xr)), np.max(np.abs(v - vr))))
+    ratios = [errs[i] / errs[i + 1] for i in range(3)]
+    assert all(3.6 < q < 4.4 for q in ratios), (errs, ratios)
+
+
+def test_evolving_field_with_equal_snapshots_is_the_frozen_field():
+    field, _, x, v, tau = synth.small_case(18, 8, 8, 2.0, 50, 0.1)
+    xa, va, xb, vb = x.copy(), v.copy(), x.copy(), v.copy()
+    oracle.advance(field, L, xa, va, tau, 0.0, 0.01, np.zeros(3), 20)
+    oracle.advance(field, L, xb, vb, tau, 0.0, 0.01, np.zeros(3), 20, field_b=field,
+                   times=(0.3, 0.0, 1.0))
+    assert np.abs(xa - xb).max() < 1e-14 and np.abs(va - vb).max() < 1e-14
+
+
 def test_heun_stage_structure_brute_force():
     """One step on a random field equals the Heun formulas evaluated with the
     independent scipy interpolator (catches a wrong stage, sign or weight)."""
