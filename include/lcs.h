@@ -113,6 +113,15 @@ typedef struct {
   lcs_drag drag;          /* drag law (LCS_DRAG_STOKES when zero-initialised) */
   double nu;              /* kinematic viscosity, > 0 (LCS_DRAG_NONLINEAR only) */
   double density_ratio;   /* rho_p / rho, > 0; 0 selects 843 (water, Sec. 2.2) */
+  /* Evolving field: with field_next != NULL the fluid velocity is linear in
+   * time between `field` (time t_field[0]) and field_next (time t_field[1]):
+   * U(X, t) = (1 - th) U_0(X) + th U_1(X), th = (t - t_field[0]) /
+   * (t_field[1] - t_field[0]); step n (from 0) starts at t = t_start + n dt
+   * and its Heun stages see t and t + dt.  lcs_set_field pushes the next
+   * snapshot.  NULL: the frozen field.  Forward only (no lcs_backward). */
+  const double *field_next; /* device [3][N][N][N] or NULL; read during the call only */
+  double t_start;         /* time of the initial state */
+  double t_field[2];      /* times of field and field_next, t_field[1] > t_field[0] */
 } lcs_desc;
 
 /* Create a context for n_ens ensembles (1 <= n_ens <= 1024, all with the same
@@ -168,6 +177,13 @@ lcs_status lcs_get_state(lcs_ctx *ctx, int ens, double *x, double *v, double *ta
  * the storage precision), expanded to FP64 [3][N][N][N] ("any" pointer).
  * Synchronising. */
 lcs_status lcs_get_field(lcs_ctx *ctx, int ens, double *out);
+
+/* Evolving field: the second snapshot of ensemble `ens` becomes the first,
+ * `field` (device [3][N][N][N] FP64, read during the call) at time t becomes
+ * the second (t must exceed the current second snapshot's time); the step
+ * graphs are rebuilt.  LCS_ERR_ARG for an ensemble created with a frozen
+ * field.  Synchronising. */
+lcs_status lcs_set_field(lcs_ctx *ctx, int ens, const double *field, double t);
 
 /* Gradients of a scalar loss of the final state of ensemble 0 with respect
  * to the field and the initial state, by the hand-written adjoint of the

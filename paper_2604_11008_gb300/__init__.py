@@ -36,7 +36,7 @@ KERNELS = {"auto": 0, "fp64": 1, "df": 2}
 EXPORTS = ("lcs_init", "lcs_step", "lcs_migrate", "lcs_sort", "lcs_set_state", "lcs_get_state",
            "lcs_get_field", "lcs_backward", "lcs_sync", "lcs_last_error", "lcs_destroy",
            "lcs_launch_count", "lcs_partition", "lcs_profile_steps", "lcs_partition_noalloc",
-           "lcs_tune", "lcs_set_step_config", "lcs_staged_tiles")
+           "lcs_tune", "lcs_set_step_config", "lcs_staged_tiles", "lcs_set_field")
 PARTITION_NOALLOC_MAX_N = 1 << 20
 DRAGS = {"stokes": 0, "nonlinear": 1}  # lcs_drag: f = 1, or the factor of Eq. (7)
 PROF_CLASSES = ("step", "finish", "unpack", "flip", "sort")
@@ -55,7 +55,8 @@ class Desc(C.Structure):
                 ("tau_const", C.c_double), ("ids", C.c_void_p), ("dt", C.c_double),
                 ("g", C.c_double * 3), ("sort_every", C.c_int), ("sort_brick", C.c_int),
                 ("track_images", C.c_int), ("ckpt_every", C.c_int), ("drag", C.c_int),
-                ("nu", C.c_double), ("density_ratio", C.c_double)]
+                ("nu", C.c_double), ("density_ratio", C.c_double), ("field_next", C.c_void_p),
+                ("t_start", C.c_double), ("t_field", C.c_double * 2)]
 
 
 _lib = None
@@ -91,10 +92,11 @@ def lib():
         L.lcs_tune.argtypes = [P, i32, P, P, P, P]
         L.lcs_set_step_config.argtypes = [P, i32, i32, i32]
         L.lcs_staged_tiles.argtypes = [P, P]
+        L.lcs_set_field.argtypes = [P, i32, P, C.c_double]
         for name in ("lcs_init", "lcs_step", "lcs_migrate", "lcs_sort", "lcs_set_state",
                      "lcs_get_state", "lcs_get_field", "lcs_backward", "lcs_sync",
                      "lcs_partition", "lcs_profile_steps", "lcs_partition_noalloc", "lcs_tune",
-                     "lcs_set_step_config", "lcs_staged_tiles"):
+                     "lcs_set_step_config", "lcs_staged_tiles", "lcs_set_field"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -131,7 +133,8 @@ class Simulator:
     def __init__(self, field, x0, v0, dt, tau=None, tau_const=0.0, g=(0.0, 0.0, 0.0),
                  sub=(1, 1, 1), box=2 * math.pi, field_dtype="f64", kernel="auto", ids=None,
                  sort_every=0, sort_brick=0, track_images=False, ckpt_every=0, stream=None,
-                 ensembles=None, drag="stokes", nu=0.0, density_ratio=0.0):
+                 ensembles=None, drag="stokes", nu=0.0, density_ratio=0.0, field_next=None,
+                 t_start=0.0, t_field=(0.0, 1.0)):
         import torch
         self._keep = []
         self._stream = stream
@@ -139,7 +142,8 @@ class Simulator:
             field=field, x0=x0, v0=v0, dt=dt, tau=tau, tau_const=tau_const, g=g, sub=sub,
             box=box, field_dtype=field_dtype, kernel=kernel, ids=ids, sort_every=sort_every,
             sort_brick=sort_brick, track_images=track_images, ckpt_every=ckpt_every,
-            drag=drag, nu=nu, density_ratio=density_ratio)]
+            drag=drag, nu=nu, density_ratio=density_ratio, field_next=field_next,
+            t_start=t_start, t_field=t_field)]
         descs = (Desc * len(specs))()
         self.meta = []
         for k, sp in enumerate(specs):
@@ -148,7 +152,8 @@ class Simulator:
             v = _dev(sp["v0"], torch.float64)
             t = None if sp.get("tau") is None else _dev(sp["tau"], torch.float64)
             i = None if sp.get("ids") is None else _dev(sp["ids"], torch.int32)
-            self._keep += [f, x, v, t, i]
+            fn = None if sp.get("field_next") is None else _dev(sp["field_next"], torch.float64)
+            self._keep += [f, x, v, t, i, fn]
             d = descs[k]
             d.n = int(f.shape[-1])
             d.box = float(sp.get("box", 2 * math.pi))
@@ -169,6 +174,9 @@ class Simulator:
             d.drag = DRAGS[sp.get("drag", "stokes")]
             d.nu = float(sp.get("nu", 0.0))
             d.density_ratio = float(sp.get("density_ratio", 0.0))
+            d.field_next = fn.data_ptr() if fn is not None else None
+            d.t_start = float(sp.get("t_start", 0.0))
+            d.t_field[:] = [float(a) for a in sp.get("t_field", (0.0, 1.0))]
             self.meta.append(dict(n=d.n, np=d.np, P=int(np.prod(d.sub[:])), has_tau=t is not None,
                                   tau_const=d.tau_const, box=d.box))
         self._ctx = C.c_void_p()
@@ -234,6 +242,13 @@ class Simulator:
                                    C.byref(md), _ptr(ms)))
         self.tune_trials_ms = ms
         return b.value, it.value, md.value
+
+    def set_field(self, field, t: float, ens: int = 0):
+        """Evolving field: push the snapshot at time t (the current second
+        snapshot becomes the first)."""
+        import torch
+        f = _dev(field, torch.float64)
+        self._check(lib().lcs_set_field(self._ctx, int(ens), f.data_ptr(), float(t)))
 
     def set_step_config(self, block: int, items: int, mode: int = STEP_PLAIN):
         """Pin one of the step-kernel configurations lcs_tune chooses among."""

@@ -48,6 +48,8 @@ struct Ens {
   int brick = 8, nb[3] = {1, 1, 1}, key_bits = 0, mig_bits = 1;
   int max_tiles = 0, max_stiles = 0, step_grid = 1;
   void *field = nullptr;
+  void *field_b = nullptr;  // second snapshot (evolving field) or nullptr
+  double t_a = 0.0, t_b = 1.0;
   StepArgs a{};
   SortArgs s{};
   int64_t *cs1 = nullptr;
@@ -77,7 +79,8 @@ struct lcs_ctx {
   FieldKind kind = FK_F64;
   int mode = 0;  // step kernel: 0 plain, 1 staged field box, 2 prefetched records, 3 deferred
   bool pf_tau = false, pf_img = false;  // some ensemble has per-particle tau / images
-  int block = 256, items = 2;   // threads per block, particles per thread (autotuned)
+  bool evolve = false;  // some ensemble has an evolving field (mode-3 kernels only)
+  int block = 256, items = 2;   // threads per block, particles per thread (set in setup_batch)
   int step_grid = 1, total_P = 0;
   int64_t total_tiles = 0;      // sum of the ensembles' look-back array sizes
   unsigned long long *tile_status = nullptr;
@@ -218,7 +221,8 @@ lcs_status launch_steps(lcs_ctx *c, cudaStream_t st) {
   for (size_t gi = 0; gi < c->groups.size(); ++gi) {
     const int first = c->groups[gi].first, cnt = c->groups[gi].second;
     const int occ = std::max(
-        1, step_kernel_occupancy(c->kind, c->mode, c->block, c->items, c->pf_tau, c->pf_img));
+        1, step_kernel_occupancy(c->kind, c->mode, c->block, c->items, c->evolve, c->pf_tau,
+                                 c->pf_img));
     const int grid = (int)std::max<int64_t>(
         1, std::min<int64_t>(c->group_tiles[gi], (int64_t)occ * c->sms));
     if (cnt == 1) {
@@ -228,14 +232,15 @@ lcs_status launch_steps(lcs_ctx *c, cudaStream_t st) {
       one.pf_tau = c->pf_tau;
       one.pf_img = c->pf_img;
       one.counter = c->d_counter + gi;
-      CK(launch_step_group<1>(one, c->kind, c->mode, c->block, c->items, grid, st));
+      CK(launch_step_group<1>(one, c->kind, c->mode, c->block, c->items, c->evolve, grid, st));
     } else {
       for (int k = 0; k < cnt; ++k) big.a[k] = c->ens[first + k].a;
       big.n = cnt;
       big.pf_tau = c->pf_tau;
       big.pf_img = c->pf_img;
       big.counter = c->d_counter + gi;
-      CK(launch_step_group<GROUP_ENS>(big, c->kind, c->mode, c->block, c->items, grid, st));
+      CK(launch_step_group<GROUP_ENS>(big, c->kind, c->mode, c->block, c->items, c->evolve, grid,
+                                      st));
     }
     c->launches += 1;
   }
@@ -420,7 +425,13 @@ lcs_status setup_batch(lcs_ctx *c) {
       return fail(c, LCS_ERR_ARG, "all ensembles of a context need the same field storage");
     c->pf_tau |= e.a.buf[0].tau != nullptr;
     c->pf_img |= e.a.buf[0].img[0] != nullptr;
+    c->evolve |= e.field_b != nullptr;
   }
+  // default step kernel (lcs_tune / lcs_set_step_config change it): the
+  // deferred scatter, one particle per thread for the FP64-field kernels
+  c->mode = LCS_STEP_DEFERRED;
+  c->block = 256;
+  c->items = (c->kind == FK_DF || c->kind == FK_F64) ? 1 : 2;
   c->total_tiles = 0;
   c->total_P = 0;
   std::vector<int> poff(n + 1, 0);
@@ -495,6 +506,15 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
     }
     if (d.drag != LCS_DRAG_STOKES && d.ckpt_every > 0) {
       r = fail(c, LCS_ERR_ARG, "lcs_backward supports the Stokes drag only (ckpt_every > 0)");
+      break;
+    }
+    if (d.field_next && (!(d.t_field[1] > d.t_field[0]) || !std::isfinite(d.t_field[0]) ||
+                         !std::isfinite(d.t_field[1]) || !std::isfinite(d.t_start))) {
+      r = fail(c, LCS_ERR_ARG, "evolving field: needs t_field[1] > t_field[0], finite times");
+      break;
+    }
+    if (d.field_next && d.ckpt_every > 0) {
+      r = fail(c, LCS_ERR_ARG, "lcs_backward supports a frozen field only (ckpt_every > 0)");
       break;
     }
     switch (d.field_dtype) {
@@ -594,8 +614,17 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
     const int64_t ncell = (int64_t)d.n * d.n * d.n;
     const int64_t fbytes = e.kind == FK_BF16 ? 8 : e.kind == FK_F32 ? 16 : 32;
     A(dalloc(c, (char **)&e.field, ncell * fbytes));
+    if (d.field_next) A(dalloc(c, (char **)&e.field_b, ncell * fbytes));
+    A(dalloc(c, &m.nstep, 1));
     if (r != LCS_OK) break;
     e.a.field = e.field;
+    e.a.field_b = e.field_b;
+    e.t_a = d.t_field[0];
+    e.t_b = d.t_field[1];
+    if (e.field_b) {
+      e.a.th0 = (d.t_start - e.t_a) / (e.t_b - e.t_a);
+      e.a.dth = d.dt / (e.t_b - e.t_a);
+    }
     e.a.max_tiles = e.max_tiles;
     e.a.cap = e.cap;
     e.s.nseg = P;
@@ -619,6 +648,8 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
     C2(cudaMemsetAsync(m.stay_tot, 0, sizeof(int64_t) * P, st));
     C2(cudaMemsetAsync(m.mig_tot, 0, sizeof(int64_t) * P, st));
     C2(launch_field_convert(d.field, d.n, e.kind, e.field, st));
+    if (e.field_b) C2(launch_field_convert(d.field_next, d.n, e.kind, e.field_b, st));
+    C2(cudaMemsetAsync(m.nstep, 0, sizeof(int64_t), st));
     // particles -> buffer 1 compacted as one input segment, then migrate
     Rec &B1 = e.a.buf[1];
     for (int s = 0; s < 3 && e.np > 0; ++s) {
@@ -829,6 +860,31 @@ lcs_status lcs_get_field(lcs_ctx *c, int ens, double *out) {
   return LCS_OK;
 }
 
+lcs_status lcs_set_field(lcs_ctx *c, int ens, const double *field, double t) {
+  lcs_status r = check_ctx(c);
+  if (r != LCS_OK) return r;
+  if (ens < 0 || ens >= (int)c->ens.size() || !field)
+    return reject(c, "lcs_set_field: bad argument");
+  Ens &e = c->ens[ens];
+  if (!e.field_b) return reject(c, "lcs_set_field: ensemble was created with a frozen field");
+  if (!(t > e.t_b) || !std::isfinite(t)) return reject(c, "lcs_set_field: t must exceed t_b");
+  CK(cudaStreamSynchronize(c->st));
+  std::swap(e.field, e.field_b);  // the newer snapshot becomes the first
+  CK(launch_field_convert(field, e.d.n, e.kind, e.field_b, c->st));
+  c->launches += 1;
+  e.t_a = e.t_b;
+  e.t_b = t;
+  e.a.field = e.field;
+  e.a.field_b = e.field_b;
+  e.a.th0 = (e.d.t_start - e.t_a) / (e.t_b - e.t_a);
+  e.a.dth = e.d.dt / (e.t_b - e.t_a);
+  r = upload_args(c);
+  if (r != LCS_OK) return r;
+  drop_graphs(c);  // the graphs carry the snapshot pointers and times
+  CK(cudaStreamSynchronize(c->st));
+  return read_status(c);
+}
+
 lcs_status lcs_backward(lcs_ctx *c, const double *gx, const double *gv, double *gU,
                         double *gx0, double *gv0) {
   lcs_status r = check_ctx(c);
@@ -918,7 +974,8 @@ lcs_status lcs_set_step_config(lcs_ctx *c, int block, int items, int mode) {
   if (r != LCS_OK) return r;
   bool known = false;
   for (const auto &k : kStepConfigs) known |= k[0] == block && k[1] == items && k[2] == mode;
-  if (!known || (mode == LCS_STEP_STAGED_FIELD && c->kind == FK_F64))
+  if (!known || (mode == LCS_STEP_STAGED_FIELD && c->kind == FK_F64) ||
+      (c->evolve && mode != LCS_STEP_DEFERRED))
     return reject(c, "lcs_set_step_config: configuration not available");
   CK(cudaStreamSynchronize(c->st));
   c->block = block;
@@ -956,6 +1013,7 @@ lcs_status lcs_tune(lcs_ctx *c, int steps_per_trial, int *block, int *items, int
   for (int k = 0; k < LCS_TUNE_CONFIGS; ++k) {
     if (trial_ms) trial_ms[k] = -1.0;
     if (cfg[k][2] == LCS_STEP_STAGED_FIELD && c->kind == FK_F64) continue;  // no FP64 form
+    if (c->evolve && cfg[k][2] != LCS_STEP_DEFERRED) continue;  // no evolving-field form
     c->block = cfg[k][0];
     c->items = cfg[k][1];
     c->mode = cfg[k][2];

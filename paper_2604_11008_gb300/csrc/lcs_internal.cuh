@@ -91,6 +91,7 @@ struct Meta {
   int64_t *stay_tot;     // stayers per segment                       [Ptot]
   int64_t *mig_tot;      // migrants per segment                      [Ptot]
   unsigned long long *staged;  // step tiles served from a shared-memory field box [1]
+  int64_t *nstep;        // steps taken since lcs_init                  [1]
   int *fin_tab;          // arrivals of each destination: source*27 + direction,
                          // by ascending source, -1 padded             [Ptot*26]
 };
@@ -111,6 +112,10 @@ struct StepArgs {
   int step_tile;     // particles per step tile (block or warp lanes x items per lane)
   int drag;          // 0: Stokes (f = 1); 1: drag factor of Eq. (7)
   double drag_c;     // 18 / (nu rho_p/rho): Re_p^2 = drag_c tau_p |V - U|^2
+  // evolving field: second snapshot (nullptr: frozen) and the time fraction
+  // of step n's first stage, th = th0 + n dth (second stage th + dth)
+  const void *field_b;
+  double th0, dth;
 };
 
 // The ensembles of one context, as the batched kernels see them.
@@ -246,16 +251,17 @@ __device__ __forceinline__ void layout_from_counts(int P, int step_tile, const i
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_field_convert(const double *src, int N, FieldKind kind, void *dst,
                                  cudaStream_t st);
+// evolve: the evolving-field instantiation (mode 3 only)
 template <int CAP>
 cudaError_t launch_step_group(const StepGroup<CAP> &pb, FieldKind kind, int mode, int block,
-                              int items, int grid, cudaStream_t st);
+                              int items, bool evolve, int grid, cudaStream_t st);
 cudaError_t launch_finish(const BatchArgs &bt, cudaStream_t st);
 cudaError_t launch_unpack(const BatchArgs &bt, int total_P, cudaStream_t st);
 cudaError_t launch_flip(const BatchArgs &bt, cudaStream_t st);
 cudaError_t launch_field_expand(const void *src, int N, FieldKind kind, double *dst,
                                 cudaStream_t st);
-int step_kernel_occupancy(FieldKind kind, int mode, int block, int items, bool pf_tau,
-                          bool pf_img);
+int step_kernel_occupancy(FieldKind kind, int mode, int block, int items, bool evolve,
+                          bool pf_tau, bool pf_img);
 
 // Adjoint: checkpoint of the live particles (compacted, storage order).
 struct TapeSlot {

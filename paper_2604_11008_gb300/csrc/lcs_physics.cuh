@@ -257,6 +257,18 @@ static __device__ __noinline__ float drag_factor_f32(float c, float tau, const f
   return 1.0f + 0.15f * powf(c * tau * d2, 0.3435f);
 }
 
+// Time fractions of a step's two stages between the field snapshots
+// (evolving field only): U = U_a + th (U_b - U_a).
+struct StageTimes {
+  double th1, th2;
+};
+
+__device__ __forceinline__ StageTimes stage_times(const StepArgs &a) {
+  if (!a.field_b) return {0.0, 0.0};
+  const double th1 = fma((double)*a.m.nstep, a.dth, a.th0);
+  return {th1, th1 + a.dth};
+}
+
 // Wrap a fixed-point coordinate into [0, N 2^52) (Sec. 2.1): one image per
 // step; img counts the images crossed.
 __device__ __forceinline__ long long wrap_fix(long long q, long long qL, int &img) {
@@ -270,6 +282,27 @@ __device__ __forceinline__ long long wrap_fix(long long q, long long qL, int &im
   return q;
 }
 
+// U <- U + th (U_b - U) with U_b interpolated from the second snapshot
+// (float-float; FP32 for FP32/BF16 storage, whose U carries no low part).
+template <int KIND>
+__device__ __forceinline__ void lerp_field_df(const StepArgs &a, const long long q[3], double th,
+                                           df U[3]) {
+  df Ub[3];
+  interp_any<KIND>(a.field_b, a.geo.N, q, Ub, FieldBox{});
+  const df t = split_d(th);
+#pragma unroll
+  for (int s = 0; s < 3; ++s) U[s] = df_add(U[s], df_mul(t, df_add(Ub[s], df_neg(U[s]))));
+}
+
+template <int KIND>
+__device__ __forceinline__ void lerp_field_lo(const StepArgs &a, const long long q[3], float th,
+                                           df U[3]) {
+  df Ub[3];
+  interp_lo<KIND>(a.field_b, a.geo.N, q, Ub, FieldBox{});
+#pragma unroll
+  for (int s = 0; s < 3; ++s) U[s].h = fmaf(th, Ub[s].h - U[s].h, U[s].h);
+}
+
 // Heun step of Eqs. (5)-(6) (gravity g) with float-float increments, on the
 // fixed-point position q (cell units, 52 fraction bits) and the float-pair
 // velocity V:
@@ -279,10 +312,11 @@ __device__ __forceinline__ long long wrap_fix(long long q, long long qL, int &im
 //   [= dt (V + V*)/2], with f = 1 (Stokes) or the factor of Eq. (7);
 // then q' = q + (N/L) dX in fixed point (exact addition), V' = V + dV in
 // float-float, and the periodic wrap.  No FP64 instruction on the Stokes path.
-template <int KIND>
+template <int KIND, bool EVOLVE = false>
 __device__ __forceinline__ void heun_step_df(const StepArgs &a, long long q[3], df V[3],
                                              double tau, int img[3], int &bad,
-                                             const FieldBox &box = FieldBox{}) {
+                                             const FieldBox &box = FieldBox{},
+                                             StageTimes tt = StageTimes{0.0, 0.0}) {
   const Geom &g = a.geo;
   const df dt = {a.dfk[0], a.dfk[1]}, cx = {a.dfk[4], a.dfk[5]};
   const df hcx = df_scale2(cx, 0.5f);  // (dt/2) N/L
@@ -290,6 +324,7 @@ __device__ __forceinline__ void heun_step_df(const StepArgs &a, long long q[3], 
   long long q2[3];
   df U[3], hD1[3], Vs[3], D[3];
   interp_any<KIND>(a.field, g.N, q, U, box);
+  if (EVOLVE && a.field_b) lerp_field_df<KIND>(a, q, tt.th1, U);
 #pragma unroll
   for (int s = 0; s < 3; ++s) D[s] = df_add(U[s], df_neg(V[s]));
   const df h1 = a.drag ? df_mul(h, drag_factor_df(a.drag_c, tau, D)) : h;
@@ -301,6 +336,7 @@ __device__ __forceinline__ void heun_step_df(const StepArgs &a, long long q[3], 
     q2[s] = fix_stage2(q[s], V[s], cx);
   }
   interp_any<KIND>(a.field, g.N, q2, U, box);
+  if (EVOLVE && a.field_b) lerp_field_df<KIND>(a, q2, tt.th2, U);
 #pragma unroll
   for (int s = 0; s < 3; ++s) D[s] = df_add(U[s], df_neg(Vs[s]));
   const df h2 = a.drag ? df_mul(h, drag_factor_df(a.drag_c, tau, D)) : h;
@@ -324,10 +360,11 @@ __device__ __forceinline__ void heun_step_df(const StepArgs &a, long long q[3], 
 // formulas as heun_step_df with the increments in FP32 (the field itself
 // carries 2^-24 or 2^-8 relative error), accumulated exactly into the
 // fixed-point position and in float-float into the velocity.
-template <int KIND>
+template <int KIND, bool EVOLVE = false>
 __device__ __forceinline__ void heun_step_lo(const StepArgs &a, long long q[3], df V[3],
                                              double tau, int img[3], int &bad,
-                                             const FieldBox &box = FieldBox{}) {
+                                             const FieldBox &box = FieldBox{},
+                                             StageTimes tt = StageTimes{0.0, 0.0}) {
   const Geom &g = a.geo;
   const float dt = a.dfk[0], cx = a.dfk[4];
   const float taus = split_d(tau).h;
@@ -336,6 +373,7 @@ __device__ __forceinline__ void heun_step_lo(const StepArgs &a, long long q[3], 
   df U[3];
   float hD1[3], Vs[3], D[3];
   interp_lo<KIND>(a.field, g.N, q, U, box);
+  if (EVOLVE && a.field_b) lerp_field_lo<KIND>(a, q, (float)tt.th1, U);
 #pragma unroll
   for (int s = 0; s < 3; ++s) D[s] = U[s].h - V[s].h;
   const float h1 = a.drag ? h * drag_factor_f32((float)a.drag_c, taus, D) : h;
@@ -347,6 +385,7 @@ __device__ __forceinline__ void heun_step_lo(const StepArgs &a, long long q[3], 
     q2[s] = fix_stage2_lo(q[s], V[s].h, cx);
   }
   interp_lo<KIND>(a.field, g.N, q2, U, box);
+  if (EVOLVE && a.field_b) lerp_field_lo<KIND>(a, q2, (float)tt.th2, U);
 #pragma unroll
   for (int s = 0; s < 3; ++s) D[s] = U[s].h - Vs[s];
   const float h2 = a.drag ? h * drag_factor_f32((float)a.drag_c, taus, D) : h;
@@ -376,6 +415,15 @@ __device__ __forceinline__ df df_of_double(double v) {
   return {h, __double2float_rn(__dsub_rn(v, (double)h))};
 }
 
+// u <- u + th (u_b - u) in FP64 (evolving field).
+__device__ __forceinline__ void lerp_field64(const StepArgs &a, const double x[3], double th,
+                                                 double u[3]) {
+  double ub[3];
+  interp64(a.field_b, a.geo, x[0], x[1], x[2], ub[0], ub[1], ub[2]);
+#pragma unroll
+  for (int s = 0; s < 3; ++s) u[s] = fma(th, ub[s] - u[s], u[s]);
+}
+
 // Drag factor of Eq. (7) in FP64 (see drag_factor_df).
 static __device__ __noinline__ double drag_factor64(double c, double tau, const double u[3],
                                                 const double v[3]) {
@@ -389,8 +437,10 @@ static __device__ __noinline__ double drag_factor64(double c, double tau, const 
 // arithmetic: the state is read as FP64 position and velocity, advanced with
 // FP64 operations only, and stored back (position rounded to the fixed-point
 // grid of 2^-52 cells, velocity to a float pair), then wrapped.
+template <bool EVOLVE = false>
 __device__ __forceinline__ void heun_step64(const StepArgs &a, long long q[3], df V[3],
-                                          double tau, int img[3], int &bad) {
+                                          double tau, int img[3], int &bad,
+                                          StageTimes tt = StageTimes{0.0, 0.0}) {
   const Geom &g = a.geo;
   const double itau = 1.0 / tau;
   double x[3], v[3], u1[3], a1[3], xs[3], vs[3], u2[3];
@@ -400,6 +450,7 @@ __device__ __forceinline__ void heun_step64(const StepArgs &a, long long q[3], d
     v[s] = vel_of_df(V[s]);
   }
   interp64(a.field, g, x[0], x[1], x[2], u1[0], u1[1], u1[2]);
+  if (EVOLVE && a.field_b) lerp_field64(a, x, tt.th1, u1);
   const double f1 = a.drag ? drag_factor64(a.drag_c, tau, u1, v) * itau : itau;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
@@ -408,6 +459,7 @@ __device__ __forceinline__ void heun_step64(const StepArgs &a, long long q[3], d
     vs[s] = v[s] + a.dt * a1[s];
   }
   interp64(a.field, g, xs[0], xs[1], xs[2], u2[0], u2[1], u2[2]);
+  if (EVOLVE && a.field_b) lerp_field64(a, xs, tt.th2, u2);
   const double f2 = a.drag ? drag_factor64(a.drag_c, tau, u2, vs) * itau : itau;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
