@@ -296,21 +296,25 @@ def precision_throughput(lcs, torch, steps=20):
     return out
 
 
-# ---------------------------------------------------------------- nonlinear drag
+# ---------------------------------------------------------------- model variants
 
-def drag_throughput(lcs, torch, w, field, dt, x, v, tau, steps=20, nu=2e-3):
+def variants_throughput(lcs, torch, w, field, dt, x, v, tau, steps=20, nu=2e-3):
     """The bench workload with the drag factor of Eq. (7) (kinematic viscosity
-    nu, density ratio 843): particle-updates/s for the FP64 field (float-float
-    kernel, FP64 pow) and the FP32 field (powf), against Stokes drag."""
+    nu, density ratio 843) and with a field evolving linearly in time between
+    two snapshots (the second a phase-shifted copy of the first), against the
+    frozen field with Stokes drag: particle-updates/s for the FP64 field
+    (float-float kernel) and the FP32 field, deferred-scatter kernel."""
     st = torch.cuda.current_stream()
-    out = {"workload": f"{w.name}, drag factor of Eq. (7), nu {nu}, rho_p/rho 843",
-           "steps": steps, "unit": UNIT}
+    out = {"workload": f"{w.name}; drag of Eq. (7) with nu {nu}, rho_p/rho 843; evolving "
+                       f"field between two snapshots", "steps": steps, "unit": UNIT}
+    field2 = torch.roll(field, shifts=7, dims=-1)
     for dtype in ("f64", "f32"):
-        for drag in ("stokes", "nonlinear"):
+        for variant in ("stokes", "nonlinear_drag", "evolving_field"):
+            kw = dict(drag="nonlinear", nu=nu) if variant == "nonlinear_drag" else {}
+            if variant == "evolving_field":
+                kw = dict(field_next=field2, t_start=0.0, t_field=(0.0, 100.0 * dt))
             sim = lcs.Simulator(field, x, v, dt, tau=tau, tau_const=w.tau_const, g=w.g,
-                                sub=w.sub, field_dtype=dtype, sort_every=w.sort_every,
-                                drag=drag, nu=nu)
-            sim.set_step_config(256, 1, 3)
+                                sub=w.sub, field_dtype=dtype, sort_every=w.sort_every, **kw)
             sim.step(10)
             sim.sync()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -318,11 +322,12 @@ def drag_throughput(lcs, torch, w, field, dt, x, v, tau, steps=20, nu=2e-3):
             sim.step(steps)
             e1.record(st)
             sim.sync()
-            out[f"{dtype}_{drag}"] = x.shape[1] * steps / (e0.elapsed_time(e1) * 1e-3)
+            out[f"{dtype}_{variant}"] = x.shape[1] * steps / (e0.elapsed_time(e1) * 1e-3)
             sim.close()
-    for dtype in ("f64", "f32"):
-        out[f"{dtype}_nonlinear_over_stokes"] = round(out[f"{dtype}_nonlinear"] /
-                                                      out[f"{dtype}_stokes"], 3)
+        for variant in ("nonlinear_drag", "evolving_field"):
+            out[f"{dtype}_{variant}_over_stokes"] = round(out[f"{dtype}_{variant}"] /
+                                                          out[f"{dtype}_stokes"], 3)
+    del field2
     return out
 
 
@@ -338,8 +343,8 @@ def main():
     ap.add_argument("--kernel", default="auto", choices=["auto", "fp64", "df"])
     ap.add_argument("--field", default="f64", choices=["f64", "f32", "bf16"])
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--drag", type=int, default=1,
-                    help="also time the nonlinear drag factor of Eq. (7)")
+    ap.add_argument("--variants", type=int, default=1,
+                    help="also time the nonlinear drag of Eq. (7) and an evolving field")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1 << 20)
     ap.add_argument("--precision", type=int, default=1,
@@ -461,9 +466,9 @@ def main():
     precision = None
     if rank == 0 and args.precision:
         precision = precision_throughput(lcs, torch)
-    drag = None
-    if rank == 0 and args.drag:
-        drag = drag_throughput(lcs, torch, w, field, dt, x, v, tau)
+    variants = None
+    if rank == 0 and args.variants:
+        variants = variants_throughput(lcs, torch, w, field, dt, x, v, tau)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -492,7 +497,7 @@ def main():
                           "l2": "inputs larger than L2 (state ~1 GB, field 0.54 GB)",
                           "parallelism": f"replicas{world}"},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "adjoint": adjoint, "batch": batch,
-               "precision": precision, "nonlinear_drag": drag,
+               "precision": precision, "model_variants": variants,
                "gpu_launches": int(launches), "clocks": clk,
                "kernel_profile_ms": {k: round(v_[0], 4) for k, v_ in prof.items()}}
         print(json.dumps(out))
