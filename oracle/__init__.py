@@ -66,6 +66,8 @@ def _load():
             lib.orc_interp_transpose_many.argtypes = [P, i32, dbl, i64, P, P, P, P, P, P]
             lib.orc_round_f32.argtypes = [i64, P, P]
             lib.orc_round_bf16.argtypes = [i64, P, P]
+            lib.orc_pair_hist.argtypes = [i64, P, P, P, dbl, dbl, i32, P]
+            lib.orc_pair_hist.restype = None
             _lib = lib
     return _lib
 
@@ -176,6 +178,16 @@ def sort(P: int, seg, key):
     if st != ORC_OK:
         raise MemoryError("orc_sort")
     return perm
+
+
+def pair_hist(x, L, r_max, nbins):
+    """Counts (nbins,) of pair separations r < r_max (minimum image), all pairs."""
+    lib = _load()
+    x = _c(x, np.float64)
+    counts = np.zeros(nbins, np.int64)
+    lib.orc_pair_hist(x.shape[1], _p(x[0]), _p(x[1]), _p(x[2]), float(L), float(r_max),
+                      int(nbins), _p(counts))
+    return counts
 
 
 def loss(L, x, img, target, mask=None):

@@ -29,6 +29,10 @@
  *   orc_adjoint       reverse-mode derivative of orc_advance, written out
  *                     from the forward definitions above
  *   orc_round_f32/bf16  round-to-nearest-even of FP64 values to FP32 / BF16
+ *   orc_pair_hist     histogram of pair separations (minimum image in the
+ *                     periodic box), the counts behind the radial
+ *                     distribution function g(r) of Sec. 3 (particle-phase
+ *                     validation), by brute force over all pairs
  *
  * Layouts: field [3][N][N][N] float64 with cell (i,j,k) at i + N*(j + N*k),
  * x fastest; particle data structure-of-arrays float64.
@@ -532,4 +536,29 @@ void orc_round_bf16(int64_t n, const double *in, double *out) {
     if (fabs(r) > 3.3895313892515355e38) r = copysign(INFINITY, x);
     out[i] = r;
   }
+}
+
+/* Histogram of the separations of all unordered particle pairs i < j in the
+ * periodic cube of side L (minimum image per axis: a difference d > L/2 is
+ * replaced by d - L, d < -L/2 by d + L), for separations r < r_max, in nbins
+ * equal bins: bin = floor(r * (nbins / r_max)) (clamped to nbins - 1).
+ * r^2 = (dx dx + dy dy) + dz dz, r = sqrt(r^2); counts (nbins) are added to. */
+void orc_pair_hist(int64_t n, const double *x, const double *y, const double *z, double L,
+                   double r_max, int nbins, int64_t *counts) {
+  const double inv_w = (double)nbins / r_max;
+  const double half = 0.5 * L;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = i + 1; j < n; ++j) {
+      double d[3] = {x[i] - x[j], y[i] - y[j], z[i] - z[j]};
+      for (int s = 0; s < 3; ++s) {
+        if (d[s] > half) d[s] -= L;
+        else if (d[s] < -half) d[s] += L;
+      }
+      const double r = sqrt((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]);
+      if (r < r_max) {
+        int b = (int)(r * inv_w);
+        if (b > nbins - 1) b = nbins - 1;
+        counts[b] += 1;
+      }
+    }
 }

@@ -286,6 +286,37 @@ def test_evolving_field_with_equal_snapshots_is_the_frozen_field():
     assert np.abs(xa - xb).max() < 1e-14 and np.abs(va - vb).max() < 1e-14
 
 
+def test_pair_histogram_of_a_cubic_lattice():
+    """m^3 points of a simple cubic lattice filling the periodic box (spacing
+    a = L/m): every point has 6 neighbours at a, 12 at a sqrt(2), 8 at
+    a sqrt(3) and 6 at 2a, so the unordered pair counts are 3n, 6n, 4n, 3n
+    (m >= 5 keeps 2a below L/2; the minimum image joins the faces)."""
+    m = 6
+    a = L / m
+    g = np.arange(m) * a + 0.1 * a
+    x = np.stack([c.ravel() for c in np.meshgrid(g, g, g, indexing="ij")])
+    n = m ** 3
+    r_max, nbins = 2.21 * a, 13         # bins of 0.17 a: 1, 1.414, 1.732, 2 lie inside bins
+    c = oracle.pair_hist(x, L, r_max, nbins)
+    want = np.zeros(nbins, np.int64)
+    for k, mult in ((1.0, 3), (math.sqrt(2), 6), (math.sqrt(3), 4), (2.0, 3)):
+        want[int(k / 0.17)] += mult * n
+    assert np.array_equal(c, want), (c, want)
+
+
+def test_pair_histogram_of_uniform_points_gives_g_near_one():
+    """Uniform random points: counts / (n(n-1)/2 * shell volume / L^3) ~ 1."""
+    rng = np.random.default_rng(9)
+    n = 4000
+    x = rng.random((3, n)) * L
+    r_max, nbins = 0.6, 6
+    c = oracle.pair_hist(x, L, r_max, nbins)
+    edges = np.linspace(0, r_max, nbins + 1)
+    shell = 4.0 / 3.0 * math.pi * (edges[1:] ** 3 - edges[:-1] ** 3)
+    g = c / (n * (n - 1) / 2 * shell / L ** 3)
+    assert np.all(np.abs(g[1:] - 1) < 0.15) and abs(g[0] - 1) < 0.6, g
+
+
 def test_heun_stage_structure_brute_force():
     """One step on a random field equals the Heun formulas evaluated with the
     independent scipy interpolator (catches a wrong stage, sign or weight)."""
