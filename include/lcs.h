@@ -178,6 +178,17 @@ lcs_status lcs_get_state(lcs_ctx *ctx, int ens, double *x, double *v, double *ta
  * Synchronising. */
 lcs_status lcs_get_field(lcs_ctx *ctx, int ens, double *out);
 
+/* Particle statistics: counts[b] (host, nbins <= 4096) = number of unordered
+ * pairs of particles of ensemble `ens` whose separation r (minimum image in
+ * the periodic box, positions as lcs_get_state returns them,
+ * r = sqrt((dx dx + dy dy) + dz dz) in FP64) is below r_max, with
+ * b = min(floor(r * (nbins / r_max)), nbins - 1): the counts behind the
+ * radial distribution function g(r) (particle-phase validation of Sec. 3),
+ * g_b = counts[b] / (np (np - 1) / 2 * shell volume_b / L^3).  Requires N >= 3
+ * and 0 < r_max <= L/N (pairs then lie in neighbouring cells).  Scratch is
+ * allocated with cudaMallocAsync on the context's stream.  Synchronising. */
+lcs_status lcs_pair_histogram(lcs_ctx *ctx, int ens, double r_max, int nbins, int64_t *counts);
+
 /* Evolving field: the second snapshot of ensemble `ens` becomes the first,
  * `field` (device [3][N][N][N] FP64, read during the call) at time t becomes
  * the second (t must exceed the current second snapshot's time); the step

@@ -36,7 +36,8 @@ KERNELS = {"auto": 0, "fp64": 1, "df": 2}
 EXPORTS = ("lcs_init", "lcs_step", "lcs_migrate", "lcs_sort", "lcs_set_state", "lcs_get_state",
            "lcs_get_field", "lcs_backward", "lcs_sync", "lcs_last_error", "lcs_destroy",
            "lcs_launch_count", "lcs_partition", "lcs_profile_steps", "lcs_partition_noalloc",
-           "lcs_tune", "lcs_set_step_config", "lcs_staged_tiles", "lcs_set_field")
+           "lcs_tune", "lcs_set_step_config", "lcs_staged_tiles", "lcs_set_field",
+           "lcs_pair_histogram")
 PARTITION_NOALLOC_MAX_N = 1 << 20
 DRAGS = {"stokes": 0, "nonlinear": 1}  # lcs_drag: f = 1, or the factor of Eq. (7)
 PROF_CLASSES = ("step", "finish", "unpack", "flip", "sort")
@@ -93,10 +94,12 @@ def lib():
         L.lcs_set_step_config.argtypes = [P, i32, i32, i32]
         L.lcs_staged_tiles.argtypes = [P, P]
         L.lcs_set_field.argtypes = [P, i32, P, C.c_double]
+        L.lcs_pair_histogram.argtypes = [P, i32, C.c_double, i32, P]
         for name in ("lcs_init", "lcs_step", "lcs_migrate", "lcs_sort", "lcs_set_state",
                      "lcs_get_state", "lcs_get_field", "lcs_backward", "lcs_sync",
                      "lcs_partition", "lcs_profile_steps", "lcs_partition_noalloc", "lcs_tune",
-                     "lcs_set_step_config", "lcs_staged_tiles", "lcs_set_field"):
+                     "lcs_set_step_config", "lcs_staged_tiles", "lcs_set_field",
+                     "lcs_pair_histogram"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -249,6 +252,24 @@ class Simulator:
         import torch
         f = _dev(field, torch.float64)
         self._check(lib().lcs_set_field(self._ctx, int(ens), f.data_ptr(), float(t)))
+
+    def pair_histogram(self, r_max: float, nbins: int, ens: int = 0) -> np.ndarray:
+        """Counts of particle pairs by separation (r < r_max <= L/N, nbins bins)."""
+        counts = np.zeros(int(nbins), dtype=np.int64)
+        self._check(lib().lcs_pair_histogram(self._ctx, int(ens), float(r_max), int(nbins),
+                                             _ptr(counts)))
+        return counts
+
+    def rdf(self, r_max: float, nbins: int, ens: int = 0):
+        """Radial distribution function: (bin centres, g, counts), with
+        g = counts / (np (np - 1) / 2 * shell volume / L^3)."""
+        counts = self.pair_histogram(r_max, nbins, ens)
+        n, box = self.meta[ens]["np"], self.meta[ens]["box"]
+        edges = np.linspace(0.0, r_max, int(nbins) + 1)
+        shell = 4.0 / 3.0 * math.pi * (edges[1:] ** 3 - edges[:-1] ** 3)
+        expected = n * (n - 1) / 2.0 * shell / box ** 3
+        g = np.divide(counts, expected, out=np.zeros(len(counts)), where=expected > 0)
+        return 0.5 * (edges[1:] + edges[:-1]), g, counts
 
     def set_step_config(self, block: int, items: int, mode: int = STEP_PLAIN):
         """Pin one of the step-kernel configurations lcs_tune chooses among."""

@@ -860,6 +860,45 @@ lcs_status lcs_get_field(lcs_ctx *c, int ens, double *out) {
   return LCS_OK;
 }
 
+lcs_status lcs_pair_histogram(lcs_ctx *c, int ens, double r_max, int nbins, int64_t *counts) {
+  lcs_status r = check_ctx(c);
+  if (r != LCS_OK) return r;
+  if (ens < 0 || ens >= (int)c->ens.size() || !counts || nbins < 1 || nbins > 4096)
+    return reject(c, "lcs_pair_histogram: bad argument");
+  Ens &e = c->ens[ens];
+  const Geom &g = e.a.geo;
+  if (g.N < 3 || !(r_max > 0) || !(r_max <= g.L / g.N))
+    return reject(c, "lcs_pair_histogram: needs N >= 3 and 0 < r_max <= L/N");
+  cudaStream_t st = c->st;
+  const int64_t n = e.np;
+  std::vector<unsigned long long> h(nbins, 0ull);
+  if (n > 1) {
+    const int64_t ncell = (int64_t)g.N * g.N * g.N;
+    char *mem = nullptr;
+    const size_t bytes = sizeof(int) * (ncell + 1) + sizeof(unsigned long long) * nbins + 64;
+    CK(cudaMallocAsync((void **)&mem, bytes, st));
+    int *start = (int *)mem;
+    unsigned long long *dcount =
+        (unsigned long long *)(mem + ((sizeof(int) * (ncell + 1) + 15) & ~size_t(15)));
+    CK(cudaMemsetAsync(dcount, 0, sizeof(unsigned long long) * nbins, st));
+    const int gs = grid_for(n, 256, c->sms * 8);
+    CK(launch_pair_keys(e.a, e.s.key[0], e.s.pay[0], n, gs, st));
+    k_one_segment<<<1, 1, 0, st>>>(e.a.m.cstart, g.Ptot, e.cs1, e.to1);
+    SortArgs s = e.s;
+    s.nseg = 1, s.cstart = e.cs1, s.tile_off = e.to1;
+    int ob = 0;
+    CK(radix_sort(s, ceil_log2(ncell), &ob, st, &c->launches));
+    CK(launch_pair_hist(e.a, s.key[ob], s.pay[ob], start, n, r_max, nbins, dcount, c->sms, st));
+    c->launches += 4;
+    CK(cudaMemcpyAsync(h.data(), dcount, sizeof(unsigned long long) * nbins,
+                       cudaMemcpyDeviceToHost, st));
+    CK(cudaFreeAsync(mem, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  for (int b = 0; b < nbins; ++b) counts[b] = (int64_t)h[b];
+  return read_status(c);
+}
+
 lcs_status lcs_set_field(lcs_ctx *c, int ens, const double *field, double t) {
   lcs_status r = check_ctx(c);
   if (r != LCS_OK) return r;

@@ -149,6 +149,16 @@ __device__ __forceinline__ int find_segment(const int *off, int P, int t) {
   return lo;
 }
 
+// Segment containing compacted index t: largest s with off[s] <= t.
+__device__ __forceinline__ int find_segment64(const int64_t *off, int P, int64_t t) {
+  int lo = 0, hi = P;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= t) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
 __device__ __forceinline__ int wrap_cell(int i, int N) {
   i = i < 0 ? i + N : i;
   i = i >= N ? i - N : i;
@@ -165,6 +175,13 @@ __host__ __device__ __forceinline__ int dir_comp(int a, int b, int P) {
   if (d == 1) return 1;
   if (P >= 3 && d == P - 1) return -1;
   return 2;
+}
+
+// FP64 position returned by the C ABI for a fixed-point coordinate:
+// RN(RN(q) L/N 2^-52), kept below L.
+__device__ __forceinline__ double export_pos(long long q, const Geom &g) {
+  const double x = __dmul_rn(__ll2double_rn(q), g.fix_dx);
+  return x >= g.L ? __longlong_as_double(__double_as_longlong(g.L) - 1) : x;
 }
 
 __device__ __forceinline__ void copy_rec(const Rec &S, int64_t i, const Rec &D, int64_t o) {
@@ -260,6 +277,12 @@ cudaError_t launch_unpack(const BatchArgs &bt, int total_P, cudaStream_t st);
 cudaError_t launch_flip(const BatchArgs &bt, cudaStream_t st);
 cudaError_t launch_field_expand(const void *src, int N, FieldKind kind, double *dst,
                                 cudaStream_t st);
+// Pair-separation histogram (lcs_stats.cu).
+cudaError_t launch_pair_keys(const StepArgs &a, uint32_t *key, uint32_t *pay, int64_t n,
+                             int grid, cudaStream_t st);
+cudaError_t launch_pair_hist(const StepArgs &a, const uint32_t *key, const uint32_t *pay,
+                             int *start, int64_t n, double r_max, int nbins,
+                             unsigned long long *counts, int sms, cudaStream_t st);
 int step_kernel_occupancy(FieldKind kind, int mode, int block, int items, bool evolve,
                           bool pf_tau, bool pf_img);
 

@@ -225,14 +225,6 @@ cudaError_t radix_sort(const SortArgs &s, int bits, int *out_buf, cudaStream_t s
 
 namespace lcs {
 
-__device__ __forceinline__ int find_segment64(const int64_t *off, int P, int64_t t) {
-  int lo = 0, hi = P;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (off[mid] <= t) lo = mid; else hi = mid;
-  }
-  return lo;
-}
 
 // Containing cell of a fixed-point coordinate (its integer part).
 __device__ __forceinline__ int cell_of(const Geom &g, long long q) {
@@ -424,14 +416,11 @@ __global__ void k_import(Rec R, int64_t n, Geom g, int *status) {
 }
 
 __global__ void k_export(Rec R, int64_t n, Geom g) {
-  const double below_L = __longlong_as_double(__double_as_longlong(g.L) - 1);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
-      double x = __dmul_rn(__ll2double_rn((long long)R.x[s][i]), g.fix_dx);
-      if (x >= g.L) x = below_L;
-      R.x[s][i] = __double_as_longlong(x);
+      R.x[s][i] = __double_as_longlong(export_pos((long long)R.x[s][i], g));
       const float2 p = R.v[s][i];
       *(double *)&R.v[s][i] = (double)p.x + (double)p.y;
     }

@@ -56,7 +56,11 @@ def draw_modes(M: int, kmin: float, kmax: float, g: np.random.Generator) -> Mode
     random r, so every mode (and the field) is exactly divergence free.
     """
     ks, seen = [], set()
+    draws = 0
     while len(ks) < M:
+        draws += 1
+        if draws > 10000 * M:  # the shell holds fewer than M distinct +-k pairs
+            raise ValueError(f"cannot draw {M} distinct wavevectors with {kmin} <= |k| <= {kmax}")
         mag = g.uniform(kmin, kmax)
         d = g.standard_normal(3)
         d /= np.linalg.norm(d)
