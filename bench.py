@@ -303,7 +303,8 @@ def variants_throughput(lcs, torch, w, field, dt, x, v, tau, steps=20, nu=2e-3):
     nu, density ratio 843) and with a field evolving linearly in time between
     two snapshots (the second a phase-shifted copy of the first), against the
     frozen field with Stokes drag: particle-updates/s for the FP64 field
-    (float-float kernel) and the FP32 field, deferred-scatter kernel."""
+    (float-float kernel) and the FP32 field, deferred-scatter kernel; and the
+    wall time of the pair-separation histogram (g(r)) on the bench state."""
     st = torch.cuda.current_stream()
     out = {"workload": f"{w.name}; drag of Eq. (7) with nu {nu}, rho_p/rho 843; evolving "
                        f"field between two snapshots", "steps": steps, "unit": UNIT}
@@ -328,6 +329,21 @@ def variants_throughput(lcs, torch, w, field, dt, x, v, tau, steps=20, nu=2e-3):
             out[f"{dtype}_{variant}_over_stokes"] = round(out[f"{dtype}_{variant}"] /
                                                           out[f"{dtype}_stokes"], 3)
     del field2
+    # particle statistics: the pair-separation histogram behind g(r) on the
+    # bench state (pairs closer than one grid cell, 32 bins)
+    sim = lcs.Simulator(field, x, v, dt, tau=tau, tau_const=w.tau_const, g=w.g, sub=w.sub,
+                        sort_every=w.sort_every)
+    sim.step(10)
+    sim.sync()
+    L = synth.L_BOX
+    t0 = time.perf_counter()
+    reps = 3
+    for _ in range(reps):
+        counts = sim.pair_histogram(L / w.N, 32)
+    ms = (time.perf_counter() - t0) * 1e3 / reps
+    sim.close()
+    out["pair_histogram"] = {"ms": round(ms, 3), "pairs_below_one_cell": int(counts.sum()),
+                             "particles_per_s": x.shape[1] / (ms * 1e-3)}
     return out
 
 
