@@ -67,6 +67,12 @@ def _load():
             lib.orc_round_f32.argtypes = [i64, P, P]
             lib.orc_round_bf16.argtypes = [i64, P, P]
             lib.orc_pair_hist.argtypes = [i64, P, P, P, dbl, dbl, i32, P]
+            lib.orc_stage1.argtypes = [P, i32, dbl, dbl, i64, P, P, P, dbl, dbl, P, i32, dbl,
+                                       dbl, P, dbl, dbl, dbl, P, P, P]
+            lib.orc_stage1.restype = i32
+            lib.orc_stage2.argtypes = [P, i32, dbl, dbl, i64, P, P, P, P, P, P, dbl, dbl, P,
+                                       i32, dbl, dbl, P, dbl, dbl, dbl, P]
+            lib.orc_stage2.restype = i32
             lib.orc_pair_hist.restype = None
             _lib = lib
     return _lib
@@ -279,6 +285,53 @@ def initial_state(N, L, P, x, v, tau, ids=None, track_img=False):
     return st
 
 
+def _wrapped(x, L):
+    """Positions folded into [0, L) as the wrap of Sec. 2.1 does (x == L -> 0)."""
+    w = np.where(x >= L, x - L, np.where(x < 0.0, x + L, x))
+    return np.where(w == L, 0.0, w)
+
+
+def step_per_stage(st: State, field, L, P, tau_const, dt, g, brick, do_sort: bool,
+                   drag=STOKES, field_b=None, times=(0.0, 0.0, 1.0)):
+    """One step with migration after each Runge-Kutta stage (Sec. 3.2.2): stage 1
+    gives X*, V*, A1; the particles move to the subdomain of X* (folded into the
+    box); stage 2 completes X', V' (wrapped); they move to the subdomain of X';
+    then the optional cell sort.  The stage values travel with the particles."""
+    lib = _load()
+    field = _c(field, np.float64)
+    N = field.shape[-1]
+    n = st.x.shape[1]
+    fb = None if field_b is None else _c(field_b, np.float64)
+    tau = None if st.tau is None else _c(st.tau, np.float64)
+    gg = _c(g, np.float64)
+    dr = (int(drag[0]), float(drag[1]) if drag[0] else 0.0, float(drag[2]) if drag[0] else 0.0)
+    xs, vs, a1 = np.empty((3, n)), np.empty((3, n)), np.empty((3, n))
+    status = lib.orc_stage1(_p(field), N, float(L), inv_dx(N, L), n, _p(st.x), _p(st.v),
+                            _p(tau), float(tau_const), float(dt), _p(gg), *dr, _p(fb),
+                            float(times[0]), float(times[1]), float(times[2]), _p(xs), _p(vs),
+                            _p(a1))
+    dest, _ = keys(N, L, P, brick, _wrapped(xs, L))
+    perm, seg_out, _ = migrate(int(np.prod(P)), st.seg, dest)
+    st.permute(perm)
+    st.seg = seg_out
+    xs, vs, a1 = (np.ascontiguousarray(a[:, perm]) for a in (xs, vs, a1))
+    tau = None if st.tau is None else _c(st.tau, np.float64)
+    s2 = lib.orc_stage2(_p(field), N, float(L), inv_dx(N, L), n, _p(st.x), _p(st.v), _p(xs),
+                        _p(vs), _p(a1), _p(tau), float(tau_const), float(dt), _p(gg), *dr,
+                        _p(fb), float(times[0]), float(times[1]), float(times[2]),
+                        _p(st.img))
+    status = status or s2
+    dest, key = keys(N, L, P, brick, st.x)
+    perm, seg_out, _ = migrate(int(np.prod(P)), st.seg, dest)
+    st.permute(perm)
+    st.seg = seg_out
+    if do_sort:
+        _, key = keys(N, L, P, brick, st.x)
+        perm = sort(int(np.prod(P)), st.seg, key)
+        st.permute(perm)
+    return status
+
+
 def step(st: State, field, L, P, tau_const, dt, g, brick, do_sort: bool, drag=STOKES,
          field_b=None, times=(0.0, 0.0, 1.0)):
     """One step of the path: advance + wrap, migrate, and (if do_sort) the cell sort."""
@@ -297,14 +350,15 @@ def step(st: State, field, L, P, tau_const, dt, g, brick, do_sort: bool, drag=ST
 
 
 def run(st: State, field, L, P, tau_const, dt, g, nsteps, sort_every=0, brick=8, step0=0,
-        drag=STOKES, field_b=None, t_start=0.0, t_field=(0.0, 1.0)):
+        drag=STOKES, field_b=None, t_start=0.0, t_field=(0.0, 1.0), per_stage=False):
     """nsteps steps; the sort runs after steps whose 1-based index is a multiple of sort_every.
     With field_b the field is linear in time between `field` at t_field[0] and
     field_b at t_field[1]; step k (counted from step0) starts at t_start + k dt."""
     status = ORC_OK
+    one = step_per_stage if per_stage else step
     for k in range(step0, step0 + nsteps):
-        s = step(st, field, L, P, tau_const, dt, g, brick,
-                 sort_every > 0 and (k + 1) % sort_every == 0, drag=drag, field_b=field_b,
-                 times=(t_start + k * dt, t_field[0], t_field[1]))
+        s = one(st, field, L, P, tau_const, dt, g, brick,
+                sort_every > 0 and (k + 1) % sort_every == 0, drag=drag, field_b=field_b,
+                times=(t_start + k * dt, t_field[0], t_field[1]))
         status = status or s
     return status

@@ -166,55 +166,150 @@ static void fluid_velocity(const double *fa, const double *fb, double theta, int
  * so that two runs which visit different interpolation cells can be told
  * apart.  Returns ORC_ERR_DISPLACEMENT if any step moves a particle by half
  * a box or more along an axis (one periodic image per step). */
+/* Stage 1 of Heun's method for one particle (Eqs. 5-6):
+ *   A1 = f1 (U(X, t) - V)/tau + g,  X* = X + dt V,  V* = V + dt A1. */
+static void heun_stage1(const double *field, const double *field_b, double th1, int N,
+                        double inv_dx, double tp, double dt, const double *g, int drag,
+                        double nu, double rr, const double x0[3], const double v0[3],
+                        double a1[3], double xs[3], double vs[3]) {
+  double u1[3];
+  fluid_velocity(field, field_b, th1, N, inv_dx, x0, u1);
+  double f1 = 1.0;
+  if (drag) {
+    const double rel[3] = {v0[0] - u1[0], v0[1] - u1[1], v0[2] - u1[2]};
+    f1 = drag_factor(tp, nu, rr, rel);
+  }
+  for (int s = 0; s < 3; ++s) {
+    a1[s] = f1 * (u1[s] - v0[s]) / tp + g[s];
+    xs[s] = x0[s] + dt * v0[s];
+    vs[s] = v0[s] + dt * a1[s];
+  }
+}
+
+/* Stage 2: A2 = f2 (U(X*, t + dt) - V*)/tau + g,
+ *   X' = X + dt/2 (V + V*),  V' = V + dt/2 (A1 + A2)   (X' not wrapped). */
+static void heun_stage2(const double *field, const double *field_b, double th2, int N,
+                        double inv_dx, double tp, double dt, const double *g, int drag,
+                        double nu, double rr, const double x0[3], const double v0[3],
+                        const double a1[3], const double xs[3], const double vs[3],
+                        double xn[3], double vn[3]) {
+  double u2[3];
+  fluid_velocity(field, field_b, th2, N, inv_dx, xs, u2);
+  double f2 = 1.0;
+  if (drag) {
+    const double rel[3] = {vs[0] - u2[0], vs[1] - u2[1], vs[2] - u2[2]};
+    f2 = drag_factor(tp, nu, rr, rel);
+  }
+  for (int s = 0; s < 3; ++s) {
+    const double a2 = f2 * (u2[s] - vs[s]) / tp + g[s];
+    xn[s] = x0[s] + 0.5 * dt * (v0[s] + vs[s]);
+    vn[s] = v0[s] + 0.5 * dt * (a1[s] + a2);
+  }
+}
+
+static int check_model(int drag, double nu, double rr, const double *field_b, double t_a,
+                       double t_b) {
+  if (drag != 0 && (drag != 1 || !(nu > 0.0) || !(rr > 0.0))) return ORC_ERR_ARG;
+  if (field_b && !(t_b > t_a)) return ORC_ERR_ARG;
+  return ORC_OK;
+}
+
 int orc_advance(const double *field, int N, double L, double inv_dx, int64_t n, double *x,
                 double *y, double *z, double *vx, double *vy, double *vz, const double *tau,
                 double tau_const, double dt, const double *g, int nsteps, int32_t *img,
                 uint64_t *cellhash, int drag, double nu, double rr, const double *field_b,
                 double t_start, double t_a, double t_b) {
-  int status = ORC_OK;
+  int status = check_model(drag, nu, rr, field_b, t_a, t_b);
+  if (status != ORC_OK) return status;
   double *X[3] = {x, y, z};
   double *V[3] = {vx, vy, vz};
-  if (drag != 0 && (drag != 1 || !(nu > 0.0) || !(rr > 0.0))) return ORC_ERR_ARG;
-  if (field_b && !(t_b > t_a)) return ORC_ERR_ARG;
   for (int step = 0; step < nsteps; ++step) {
     const double t = t_start + step * dt;
     const double th1 = field_b ? (t - t_a) / (t_b - t_a) : 0.0;
     const double th2 = field_b ? (t + dt - t_a) / (t_b - t_a) : 0.0;
     for (int64_t p = 0; p < n; ++p) {
       const double tp = tau ? tau[p] : tau_const;
-      double x0[3], v0[3], u1[3], a1[3], xs[3], vs[3], u2[3], a2[3];
+      double x0[3], v0[3], a1[3], xs[3], vs[3], xn[3], vn[3];
       for (int s = 0; s < 3; ++s) {
         x0[s] = X[s][p];
         v0[s] = V[s][p];
       }
-      fluid_velocity(field, field_b, th1, N, inv_dx, x0, u1);
       if (cellhash) cellhash[p] = cell_hash(cellhash[p], inv_dx, x0);
-      double f1 = 1.0, f2 = 1.0;
-      if (drag) {
-        const double rel[3] = {v0[0] - u1[0], v0[1] - u1[1], v0[2] - u1[2]};
-        f1 = drag_factor(tp, nu, rr, rel);
-      }
-      for (int s = 0; s < 3; ++s) {
-        a1[s] = f1 * (u1[s] - v0[s]) / tp + g[s];
-        xs[s] = x0[s] + dt * v0[s];
-        vs[s] = v0[s] + dt * a1[s];
-      }
-      fluid_velocity(field, field_b, th2, N, inv_dx, xs, u2);
+      heun_stage1(field, field_b, th1, N, inv_dx, tp, dt, g, drag, nu, rr, x0, v0, a1, xs, vs);
       if (cellhash) cellhash[p] = cell_hash(cellhash[p], inv_dx, xs);
-      if (drag) {
-        const double rel[3] = {vs[0] - u2[0], vs[1] - u2[1], vs[2] - u2[2]};
-        f2 = drag_factor(tp, nu, rr, rel);
-      }
+      heun_stage2(field, field_b, th2, N, inv_dx, tp, dt, g, drag, nu, rr, x0, v0, a1, xs, vs,
+                  xn, vn);
       for (int s = 0; s < 3; ++s) {
-        a2[s] = f2 * (u2[s] - vs[s]) / tp + g[s];
-        double xn = x0[s] + 0.5 * dt * (v0[s] + vs[s]);
-        double vn = v0[s] + 0.5 * dt * (a1[s] + a2[s]);
-        if (fabs(xn - x0[s]) >= 0.5 * L) status = ORC_ERR_DISPLACEMENT;
-        int im = wrap_coord(&xn, L);
+        if (fabs(xn[s] - x0[s]) >= 0.5 * L) status = ORC_ERR_DISPLACEMENT;
+        int im = wrap_coord(&xn[s], L);
         if (img) img[(int64_t)s * n + p] += im;
-        X[s][p] = xn;
-        V[s][p] = vn;
+        X[s][p] = xn[s];
+        V[s][p] = vn[s];
       }
+    }
+  }
+  return status;
+}
+
+/* The two stages of one step taken separately, for migration after each
+ * stage (Sec. 3.2.2: the particles are exchanged after every Runge-Kutta
+ * stage).  All arrays are (3, n) structure of arrays; the step starts at
+ * time t (field_b as in orc_advance).
+ * orc_stage1: from X, V compute X* (not wrapped), V* and A1.
+ * orc_stage2: from X, V, X*, V*, A1 compute X', V' in place of X, V, with
+ * the wrap of X' counted in img (may be NULL).  The arithmetic is exactly
+ * that of orc_advance. */
+int orc_stage1(const double *field, int N, double L, double inv_dx, int64_t n, const double *x,
+               const double *v, const double *tau, double tau_const, double dt, const double *g,
+               int drag, double nu, double rr, const double *field_b, double t, double t_a,
+               double t_b, double *xs, double *vs, double *a1) {
+  int status = check_model(drag, nu, rr, field_b, t_a, t_b);
+  if (status != ORC_OK) return status;
+  (void)L;
+  const double th1 = field_b ? (t - t_a) / (t_b - t_a) : 0.0;
+  for (int64_t p = 0; p < n; ++p) {
+    const double tp = tau ? tau[p] : tau_const;
+    double x0[3], v0[3], pa[3], px[3], pv[3];
+    for (int s = 0; s < 3; ++s) {
+      x0[s] = x[s * n + p];
+      v0[s] = v[s * n + p];
+    }
+    heun_stage1(field, field_b, th1, N, inv_dx, tp, dt, g, drag, nu, rr, x0, v0, pa, px, pv);
+    for (int s = 0; s < 3; ++s) {
+      a1[s * n + p] = pa[s];
+      xs[s * n + p] = px[s];
+      vs[s * n + p] = pv[s];
+    }
+  }
+  return ORC_OK;
+}
+
+int orc_stage2(const double *field, int N, double L, double inv_dx, int64_t n, double *x,
+               double *v, const double *xs, const double *vs, const double *a1,
+               const double *tau, double tau_const, double dt, const double *g, int drag,
+               double nu, double rr, const double *field_b, double t, double t_a, double t_b,
+               int32_t *img) {
+  int status = check_model(drag, nu, rr, field_b, t_a, t_b);
+  if (status != ORC_OK) return status;
+  const double th2 = field_b ? (t + dt - t_a) / (t_b - t_a) : 0.0;
+  for (int64_t p = 0; p < n; ++p) {
+    const double tp = tau ? tau[p] : tau_const;
+    double x0[3], v0[3], pa[3], px[3], pv[3], xn[3], vn[3];
+    for (int s = 0; s < 3; ++s) {
+      x0[s] = x[s * n + p];
+      v0[s] = v[s * n + p];
+      pa[s] = a1[s * n + p];
+      px[s] = xs[s * n + p];
+      pv[s] = vs[s * n + p];
+    }
+    heun_stage2(field, field_b, th2, N, inv_dx, tp, dt, g, drag, nu, rr, x0, v0, pa, px, pv,
+                xn, vn);
+    for (int s = 0; s < 3; ++s) {
+      if (fabs(xn[s] - x0[s]) >= 0.5 * L) status = ORC_ERR_DISPLACEMENT;
+      int im = wrap_coord(&xn[s], L);
+      if (img) img[(int64_t)s * n + p] += im;
+      x[s * n + p] = xn[s];
+      v[s * n + p] = vn[s];
     }
   }
   return status;

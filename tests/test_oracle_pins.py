@@ -317,6 +317,29 @@ def test_pair_histogram_of_uniform_points_gives_g_near_one():
     assert np.all(np.abs(g[1:] - 1) < 0.15) and abs(g[0] - 1) < 0.6, g
 
 
+def test_per_stage_migration_moves_particles_between_the_stages():
+    """Migration after each Runge-Kutta stage (Sec. 3.2.2): the trajectories are
+    those of the single-migration step bit for bit (same arithmetic, only the
+    storage moves), every particle ends in the segment of its position, and
+    particles whose predictor X* left the subdomain were moved before the second
+    stage (their order differs from the single-migration order)."""
+    N, P = 12, (3, 2, 2)
+    field, _, x, v, tau = synth.small_case(41, N, 12, 3.0, 6000, 0.05, dt=0.02)
+    v = np.ascontiguousarray(v + 3.0 * np.random.default_rng(5).standard_normal(v.shape))
+    a = oracle.initial_state(N, L, P, x, v, tau, track_img=True)
+    b = a.copy()
+    g = (0.0, 0.0, -9.8)
+    oracle.run(a, field, L, P, 0.0, 0.02, g, 6, sort_every=4, brick=2)
+    oracle.run(b, field, L, P, 0.0, 0.02, g, 6, sort_every=4, brick=2, per_stage=True)
+    oa, ob = np.argsort(a.ids), np.argsort(b.ids)
+    assert np.array_equal(a.x[:, oa], b.x[:, ob]) and np.array_equal(a.v[:, oa], b.v[:, ob])
+    assert np.array_equal(a.img[:, oa], b.img[:, ob])
+    dest, _ = oracle.keys(N, L, P, 1, b.x)
+    seg_of = np.repeat(np.arange(12), np.diff(b.seg))
+    assert np.array_equal(dest, seg_of)
+    assert np.array_equal(a.seg, b.seg) and not np.array_equal(a.ids, b.ids)
+
+
 def test_heun_stage_structure_brute_force():
     """One step on a random field equals the Heun formulas evaluated with the
     independent scipy interpolator (catches a wrong stage, sign or weight)."""
