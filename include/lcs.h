@@ -122,6 +122,13 @@ typedef struct {
   const double *field_next; /* device [3][N][N][N] or NULL; read during the call only */
   double t_start;         /* time of the initial state */
   double t_field[2];      /* times of field and field_next, t_field[1] > t_field[0] */
+  /* 1: migrate after each Runge-Kutta stage, as the paper does (Sec. 3.2.2):
+   * after the predictor X* (folded into the box) and again after X'; the
+   * stage velocity V* travels with the particle.  Trajectories equal those of
+   * the default single migration after the step up to rounding; only the
+   * storage order differs.  All ensembles of a context must agree.  Not with
+   * field_next or ckpt_every (the deferred-scatter step kernel only). */
+  int migrate_per_stage;
 } lcs_desc;
 
 /* Create a context for n_ens ensembles (1 <= n_ens <= 1024, all with the same

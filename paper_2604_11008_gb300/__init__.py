@@ -57,7 +57,8 @@ class Desc(C.Structure):
                 ("g", C.c_double * 3), ("sort_every", C.c_int), ("sort_brick", C.c_int),
                 ("track_images", C.c_int), ("ckpt_every", C.c_int), ("drag", C.c_int),
                 ("nu", C.c_double), ("density_ratio", C.c_double), ("field_next", C.c_void_p),
-                ("t_start", C.c_double), ("t_field", C.c_double * 2)]
+                ("t_start", C.c_double), ("t_field", C.c_double * 2),
+                ("migrate_per_stage", C.c_int)]
 
 
 _lib = None
@@ -137,7 +138,7 @@ class Simulator:
                  sub=(1, 1, 1), box=2 * math.pi, field_dtype="f64", kernel="auto", ids=None,
                  sort_every=0, sort_brick=0, track_images=False, ckpt_every=0, stream=None,
                  ensembles=None, drag="stokes", nu=0.0, density_ratio=0.0, field_next=None,
-                 t_start=0.0, t_field=(0.0, 1.0)):
+                 t_start=0.0, t_field=(0.0, 1.0), migrate_per_stage=False):
         import torch
         self._keep = []
         self._stream = stream
@@ -146,7 +147,7 @@ class Simulator:
             box=box, field_dtype=field_dtype, kernel=kernel, ids=ids, sort_every=sort_every,
             sort_brick=sort_brick, track_images=track_images, ckpt_every=ckpt_every,
             drag=drag, nu=nu, density_ratio=density_ratio, field_next=field_next,
-            t_start=t_start, t_field=t_field)]
+            t_start=t_start, t_field=t_field, migrate_per_stage=migrate_per_stage)]
         descs = (Desc * len(specs))()
         self.meta = []
         for k, sp in enumerate(specs):
@@ -180,6 +181,7 @@ class Simulator:
             d.field_next = fn.data_ptr() if fn is not None else None
             d.t_start = float(sp.get("t_start", 0.0))
             d.t_field[:] = [float(a) for a in sp.get("t_field", (0.0, 1.0))]
+            d.migrate_per_stage = int(bool(sp.get("migrate_per_stage", False)))
             self.meta.append(dict(n=d.n, np=d.np, P=int(np.prod(d.sub[:])), has_tau=t is not None,
                                   tau_const=d.tau_const, box=d.box))
         self._ctx = C.c_void_p()

@@ -80,6 +80,7 @@ struct lcs_ctx {
   int mode = 0;  // step kernel: 0 plain, 1 staged field box, 2 prefetched records, 3 deferred
   bool pf_tau = false, pf_img = false;  // some ensemble has per-particle tau / images
   bool evolve = false;  // some ensemble has an evolving field (mode-3 kernels only)
+  bool per_stage = false;  // migration after each Runge-Kutta stage (mode-3 kernels only)
   int block = 256, items = 2;   // threads per block, particles per thread (set in setup_batch)
   int step_grid = 1, total_P = 0;
   int64_t total_tiles = 0;      // sum of the ensembles' look-back array sizes
@@ -162,9 +163,11 @@ std::vector<int> finish_table(const int Pd[3]) {
 
 // Record arrays get 4 elements (>= 16 bytes) of slack: the step kernel's bulk
 // copies round a tile's rows out to 16-byte boundaries.
-lcs_status alloc_rec(lcs_ctx *c, Rec &r, int64_t cap, bool has_tau, bool has_img) {
+lcs_status alloc_rec(lcs_ctx *c, Rec &r, int64_t cap, bool has_tau, bool has_img, bool has_vs) {
   cap += 4;
   for (int s = 0; s < 3; ++s) {
+    r.vs[s] = nullptr;
+    if (has_vs) CK(dalloc(c, &r.vs[s], cap));
     CK(dalloc(c, &r.x[s], cap));
     CK(dalloc(c, &r.v[s], cap));
     r.img[s] = nullptr;
@@ -216,13 +219,13 @@ lcs_status enqueue_sort(lcs_ctx *c, Ens &e, cudaStream_t st) {
 }
 
 // The step kernel of every group of ensembles (one launch per GROUP_ENS ensembles).
-lcs_status launch_steps(lcs_ctx *c, cudaStream_t st) {
+lcs_status launch_steps(lcs_ctx *c, cudaStream_t st, int stage) {
   static thread_local StepGroup<GROUP_ENS> big;
   for (size_t gi = 0; gi < c->groups.size(); ++gi) {
     const int first = c->groups[gi].first, cnt = c->groups[gi].second;
     const int occ = std::max(
-        1, step_kernel_occupancy(c->kind, c->mode, c->block, c->items, c->evolve, c->pf_tau,
-                                 c->pf_img));
+        1, step_kernel_occupancy(c->kind, c->mode, c->block, c->items, c->evolve, stage,
+                                 c->pf_tau, c->pf_img, c->per_stage));
     const int grid = (int)std::max<int64_t>(
         1, std::min<int64_t>(c->group_tiles[gi], (int64_t)occ * c->sms));
     if (cnt == 1) {
@@ -231,16 +234,19 @@ lcs_status launch_steps(lcs_ctx *c, cudaStream_t st) {
       one.n = 1;
       one.pf_tau = c->pf_tau;
       one.pf_img = c->pf_img;
+      one.pf_vs = c->per_stage;
       one.counter = c->d_counter + gi;
-      CK(launch_step_group<1>(one, c->kind, c->mode, c->block, c->items, c->evolve, grid, st));
+      CK(launch_step_group<1>(one, c->kind, c->mode, c->block, c->items, c->evolve, stage, grid,
+                              st));
     } else {
       for (int k = 0; k < cnt; ++k) big.a[k] = c->ens[first + k].a;
       big.n = cnt;
       big.pf_tau = c->pf_tau;
       big.pf_img = c->pf_img;
+      big.pf_vs = c->per_stage;
       big.counter = c->d_counter + gi;
-      CK(launch_step_group<GROUP_ENS>(big, c->kind, c->mode, c->block, c->items, c->evolve, grid,
-                                      st));
+      CK(launch_step_group<GROUP_ENS>(big, c->kind, c->mode, c->block, c->items, c->evolve, stage,
+                                      grid, st));
     }
     c->launches += 1;
   }
@@ -248,15 +254,20 @@ lcs_status launch_steps(lcs_ctx *c, cudaStream_t st) {
 }
 
 // One step of every ensemble: 1 memset + (step groups + 3) launches, whatever
-// the number of ensembles (one step group per GROUP_ENS ensembles).
+// the number of ensembles (one step group per GROUP_ENS ensembles); twice
+// that with migration per stage (the predictor pass, then the corrector).
 lcs_status enqueue_step(lcs_ctx *c, cudaStream_t st) {
-  CK(cudaMemsetAsync(c->tile_status, 0, sizeof(unsigned long long) * c->total_tiles, st));
-  lcs_status rs = launch_steps(c, st);
-  if (rs != LCS_OK) return rs;
-  CK(launch_finish(c->bt, st));
-  CK(launch_unpack(c->bt, c->total_P, st));
-  CK(launch_flip(c->bt, st));
-  c->launches += 3;
+  const int passes = c->per_stage ? 2 : 1;
+  for (int p = 0; p < passes; ++p) {
+    const int stage = c->per_stage ? p + 1 : 0;
+    CK(cudaMemsetAsync(c->tile_status, 0, sizeof(unsigned long long) * c->total_tiles, st));
+    lcs_status rs = launch_steps(c, st, stage);
+    if (rs != LCS_OK) return rs;
+    CK(launch_finish(c->bt, st));
+    CK(launch_unpack(c->bt, c->total_P, st));
+    CK(launch_flip(c->bt, st, p == passes - 1));
+    c->launches += 3;
+  }
   return LCS_OK;
 }
 
@@ -279,18 +290,21 @@ lcs_status enqueue_step_profiled(lcs_ctx *c, const std::vector<bool> &sorts, Pro
     cudaEventRecord(e0, st);
     pf.cls.push_back(cls);
   };
-  mark(LCS_PROF_FLIP);
-  CK(cudaMemsetAsync(c->tile_status, 0, sizeof(unsigned long long) * c->total_tiles, st));
-  mark(LCS_PROF_STEP);
-  lcs_status rs = launch_steps(c, st);
-  if (rs != LCS_OK) return rs;
-  mark(LCS_PROF_FINISH);
-  CK(launch_finish(c->bt, st));
-  mark(LCS_PROF_UNPACK);
-  CK(launch_unpack(c->bt, c->total_P, st));
-  mark(LCS_PROF_FLIP);
-  CK(launch_flip(c->bt, st));
-  c->launches += 3;
+  const int passes = c->per_stage ? 2 : 1;
+  for (int p = 0; p < passes; ++p) {
+    mark(LCS_PROF_FLIP);
+    CK(cudaMemsetAsync(c->tile_status, 0, sizeof(unsigned long long) * c->total_tiles, st));
+    mark(LCS_PROF_STEP);
+    lcs_status rs = launch_steps(c, st, c->per_stage ? p + 1 : 0);
+    if (rs != LCS_OK) return rs;
+    mark(LCS_PROF_FINISH);
+    CK(launch_finish(c->bt, st));
+    mark(LCS_PROF_UNPACK);
+    CK(launch_unpack(c->bt, c->total_P, st));
+    mark(LCS_PROF_FLIP);
+    CK(launch_flip(c->bt, st, p == passes - 1));
+    c->launches += 3;
+  }
   bool any = false;
   for (bool b : sorts) any |= b;
   if (any) {
@@ -344,7 +358,7 @@ void drop_graphs(lcs_ctx *c) {
 }
 
 int64_t launches_per_step(lcs_ctx *c, const std::vector<bool> &sorts) {
-  int64_t n = 3 + (int64_t)c->groups.size();
+  int64_t n = (3 + (int64_t)c->groups.size()) * (c->per_stage ? 2 : 1);
   for (size_t k = 0; k < c->ens.size(); ++k) {
     const Ens &e = c->ens[k];
     if (sorts[k]) {
@@ -426,7 +440,10 @@ lcs_status setup_batch(lcs_ctx *c) {
     c->pf_tau |= e.a.buf[0].tau != nullptr;
     c->pf_img |= e.a.buf[0].img[0] != nullptr;
     c->evolve |= e.field_b != nullptr;
+    if (e.d.migrate_per_stage != c->ens[0].d.migrate_per_stage)
+      return fail(c, LCS_ERR_ARG, "all ensembles of a context need the same migration schedule");
   }
+  c->per_stage = c->ens[0].d.migrate_per_stage != 0;
   // default step kernel (lcs_tune / lcs_set_step_config change it): the
   // deferred scatter, one particle per thread for the FP64-field kernels
   c->mode = LCS_STEP_DEFERRED;
@@ -517,6 +534,10 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
       r = fail(c, LCS_ERR_ARG, "lcs_backward supports a frozen field only (ckpt_every > 0)");
       break;
     }
+    if (d.migrate_per_stage && (d.migrate_per_stage != 1 || d.field_next || d.ckpt_every > 0)) {
+      r = fail(c, LCS_ERR_ARG, "migrate_per_stage: not with field_next or ckpt_every");
+      break;
+    }
     switch (d.field_dtype) {
       case LCS_F64:
         e.kind = d.field_kernel == LCS_KERNEL_FP64 ? FK_F64 : FK_DF;
@@ -573,8 +594,10 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
       for (int s = 0; s < 3; ++s) split(d.dt * d.g[s], e.a.dfk + 6 + 2 * s);
     }
     const bool has_tau = d.tau != nullptr, has_img = d.track_images != 0;
-    for (int b = 0; b < 2 && r == LCS_OK; ++b) r = alloc_rec(c, e.a.buf[b], e.cap, has_tau, has_img);
-    if (r == LCS_OK) r = alloc_rec(c, e.a.pack, e.cap, has_tau, has_img);
+    const bool has_vs = d.migrate_per_stage != 0;
+    for (int b = 0; b < 2 && r == LCS_OK; ++b)
+      r = alloc_rec(c, e.a.buf[b], e.cap, has_tau, has_img, has_vs);
+    if (r == LCS_OK) r = alloc_rec(c, e.a.pack, e.cap, has_tau, has_img, has_vs);
     if (r != LCS_OK) break;
     Meta &m = e.a.m;
     auto A = [&](cudaError_t err) {
@@ -1014,7 +1037,8 @@ lcs_status lcs_set_step_config(lcs_ctx *c, int block, int items, int mode) {
   bool known = false;
   for (const auto &k : kStepConfigs) known |= k[0] == block && k[1] == items && k[2] == mode;
   if (!known || (mode == LCS_STEP_STAGED_FIELD && c->kind == FK_F64) ||
-      (c->evolve && mode != LCS_STEP_DEFERRED))
+      (c->evolve && mode != LCS_STEP_DEFERRED) ||
+      (c->per_stage && (mode != LCS_STEP_DEFERRED || block != 256)))
     return reject(c, "lcs_set_step_config: configuration not available");
   CK(cudaStreamSynchronize(c->st));
   c->block = block;
@@ -1053,6 +1077,7 @@ lcs_status lcs_tune(lcs_ctx *c, int steps_per_trial, int *block, int *items, int
     if (trial_ms) trial_ms[k] = -1.0;
     if (cfg[k][2] == LCS_STEP_STAGED_FIELD && c->kind == FK_F64) continue;  // no FP64 form
     if (c->evolve && cfg[k][2] != LCS_STEP_DEFERRED) continue;  // no evolving-field form
+    if (c->per_stage && (cfg[k][2] != LCS_STEP_DEFERRED || cfg[k][0] != 256)) continue;
     c->block = cfg[k][0];
     c->items = cfg[k][1];
     c->mode = cfg[k][2];

@@ -50,6 +50,7 @@ struct Rec {
   double *tau;      // nullptr when tau is a constant
   uint32_t *id;
   int32_t *img[3];  // nullptr entries when images are not tracked
+  float2 *vs[3];    // stage velocity V* float pairs (migration per stage), else nullptr
 };
 
 // Field storage kinds.
@@ -129,12 +130,13 @@ struct BatchArgs {
 
 // A group of at most CAP ensembles advanced by one step-kernel launch; the
 // whole struct is the kernel's parameter block (<= 32 KB for CAP = GROUP_ENS).
-constexpr int GROUP_ENS = 48;
+constexpr int GROUP_ENS = 42;
 template <int CAP>
 struct StepGroup {
   StepArgs a[CAP];
   int n;
   int pf_tau, pf_img;  // record rows present in some ensemble (prefetch layout)
+  int pf_vs;           // stage-velocity rows (migration per stage)
   unsigned int *counter;
 };
 static_assert(sizeof(StepGroup<GROUP_ENS>) <= 32764, "kernel parameter block too large");
@@ -193,6 +195,10 @@ __device__ __forceinline__ void copy_rec(const Rec &S, int64_t i, const Rec &D, 
   }
   if (S.tau) D.tau[o] = S.tau[i];
   D.id[o] = S.id[i];
+  if (S.vs[0]) {
+#pragma unroll
+    for (int s = 0; s < 3; ++s) D.vs[s][o] = S.vs[s][i];
+  }
 }
 
 // ---------------------------------------------------------------- block scan helper
@@ -268,13 +274,14 @@ __device__ __forceinline__ void layout_from_counts(int P, int step_tile, const i
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_field_convert(const double *src, int N, FieldKind kind, void *dst,
                                  cudaStream_t st);
-// evolve: the evolving-field instantiation (mode 3 only)
+// evolve: the evolving-field instantiation; stage: 0 whole step, 1/2 the
+// Runge-Kutta stages for migration per stage (both mode 3 only)
 template <int CAP>
 cudaError_t launch_step_group(const StepGroup<CAP> &pb, FieldKind kind, int mode, int block,
-                              int items, bool evolve, int grid, cudaStream_t st);
+                              int items, bool evolve, int stage, int grid, cudaStream_t st);
 cudaError_t launch_finish(const BatchArgs &bt, cudaStream_t st);
 cudaError_t launch_unpack(const BatchArgs &bt, int total_P, cudaStream_t st);
-cudaError_t launch_flip(const BatchArgs &bt, cudaStream_t st);
+cudaError_t launch_flip(const BatchArgs &bt, cudaStream_t st, int count_step);
 cudaError_t launch_field_expand(const void *src, int N, FieldKind kind, double *dst,
                                 cudaStream_t st);
 // Pair-separation histogram (lcs_stats.cu).
@@ -284,7 +291,7 @@ cudaError_t launch_pair_hist(const StepArgs &a, const uint32_t *key, const uint3
                              int *start, int64_t n, double r_max, int nbins,
                              unsigned long long *counts, int sms, cudaStream_t st);
 int step_kernel_occupancy(FieldKind kind, int mode, int block, int items, bool evolve,
-                          bool pf_tau, bool pf_img);
+                          int stage, bool pf_tau, bool pf_img, bool pf_vs);
 
 // Adjoint: checkpoint of the live particles (compacted, storage order).
 struct TapeSlot {

@@ -404,6 +404,116 @@ __device__ __forceinline__ void heun_step_lo(const StepArgs &a, long long q[3], 
   }
 }
 
+// ---------------------------------------------------------------- stages taken apart
+
+// The two Heun stages as separate passes, for migration after each stage
+// (Sec. 3.2.2).  Stage 1 moves the particle to its predictor position and
+// records the stage velocity:  X* = X + dt V (wrapped),  V* = V + h1 D1 + dt g,
+// V unchanged.  Stage 2 completes the step from X*, V, V*:
+//   X' = X* + (dt/2)(V* - V)          [= X + (dt/2)(V + V*)]
+//   V' = (V + V* + h2 D2 + dt g) / 2  [= V + (dt/2)(A1 + A2), dt A1 = V* - V]
+// with D2 = U(X*) - V*.  Same arithmetic pieces as the fused step.
+template <int KIND>
+__device__ __forceinline__ void heun_stage1_df(const StepArgs &a, long long q[3], const df V[3],
+                                               df Vs[3], double tau, int img[3], int &bad) {
+  const Geom &g = a.geo;
+  const df dt = {a.dfk[0], a.dfk[1]}, cx = {a.dfk[4], a.dfk[5]};
+  const df h = df_mul(dt, df_recip(split_d(tau)));
+  df U[3], D[3];
+  interp_any<KIND>(a.field, g.N, q, U, FieldBox{});
+#pragma unroll
+  for (int s = 0; s < 3; ++s) D[s] = df_add(U[s], df_neg(V[s]));
+  const df h1 = a.drag ? df_mul(h, drag_factor_df(a.drag_c, tau, D)) : h;
+  const float half_box = 0.5f * (float)g.N;
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const df gd = {a.dfk[6 + 2 * s], a.dfk[7 + 2 * s]};
+    Vs[s] = df_add(df_add(V[s], df_mul(h1, D[s])), gd);
+    const df dXc = df_mul(cx, V[s]);
+    if (!(fabsf(dXc.h) < half_box)) bad |= isfinite(dXc.h) ? 2 : 1;
+    if (!isfinite(Vs[s].h)) bad |= 1;
+    q[s] = wrap_fix(fix_stage2(q[s], V[s], cx), g.qL, img[s]);
+  }
+}
+
+template <int KIND>
+__device__ __forceinline__ void heun_stage2_df(const StepArgs &a, long long q[3], df V[3],
+                                               const df Vs[3], double tau, int img[3],
+                                               int &bad) {
+  const Geom &g = a.geo;
+  const df dt = {a.dfk[0], a.dfk[1]}, cx = {a.dfk[4], a.dfk[5]};
+  const df hcx = df_scale2(cx, 0.5f);
+  const df h = df_mul(dt, df_recip(split_d(tau)));
+  df U[3], D[3];
+  interp_any<KIND>(a.field, g.N, q, U, FieldBox{});
+#pragma unroll
+  for (int s = 0; s < 3; ++s) D[s] = df_add(U[s], df_neg(Vs[s]));
+  const df h2 = a.drag ? df_mul(h, drag_factor_df(a.drag_c, tau, D)) : h;
+  const float half_box = 0.5f * (float)g.N;
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const df gd = {a.dfk[6 + 2 * s], a.dfk[7 + 2 * s]};
+    const df dXc = df_mul(hcx, df_add(Vs[s], df_neg(V[s])));
+    const df vn =
+        df_scale2(df_add(df_add(V[s], Vs[s]), df_add(df_mul(h2, D[s]), gd)), 0.5f);
+    if (!(fabsf(dXc.h) < half_box)) bad |= isfinite(dXc.h) ? 2 : 1;
+    if (!isfinite(vn.h)) bad |= 1;
+    q[s] = wrap_fix(q[s] + f_to_fix52(dXc.h) + f_to_fix52(dXc.l), g.qL, img[s]);
+    V[s] = vn;
+  }
+}
+
+template <int KIND>
+__device__ __forceinline__ void heun_stage1_lo(const StepArgs &a, long long q[3], const df V[3],
+                                               df Vs[3], double tau, int img[3], int &bad) {
+  const Geom &g = a.geo;
+  const float dt = a.dfk[0], cx = a.dfk[4];
+  const float taus = split_d(tau).h;
+  const float h = dt * __frcp_rn(taus);
+  df U[3];
+  float D[3];
+  interp_lo<KIND>(a.field, g.N, q, U, FieldBox{});
+#pragma unroll
+  for (int s = 0; s < 3; ++s) D[s] = U[s].h - V[s].h;
+  const float h1 = a.drag ? h * drag_factor_f32((float)a.drag_c, taus, D) : h;
+  const float half_box = 0.5f * (float)g.N;
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    Vs[s] = df_add(V[s], df{h1 * D[s] + a.dfk[6 + 2 * s], 0.f});
+    const float dXc = cx * V[s].h;
+    if (!(fabsf(dXc) < half_box)) bad |= isfinite(dXc) ? 2 : 1;
+    if (!isfinite(Vs[s].h)) bad |= 1;
+    q[s] = wrap_fix(fix_stage2_lo(q[s], V[s].h, cx), g.qL, img[s]);
+  }
+}
+
+template <int KIND>
+__device__ __forceinline__ void heun_stage2_lo(const StepArgs &a, long long q[3], df V[3],
+                                               const df Vs[3], double tau, int img[3],
+                                               int &bad) {
+  const Geom &g = a.geo;
+  const float dt = a.dfk[0], cx = a.dfk[4];
+  const float taus = split_d(tau).h;
+  const float h = dt * __frcp_rn(taus);
+  df U[3];
+  float D[3];
+  interp_lo<KIND>(a.field, g.N, q, U, FieldBox{});
+#pragma unroll
+  for (int s = 0; s < 3; ++s) D[s] = U[s].h - Vs[s].h;
+  const float h2 = a.drag ? h * drag_factor_f32((float)a.drag_c, taus, D) : h;
+  const float half_box = 0.5f * (float)g.N;
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const df dv = df_add(Vs[s], df_neg(V[s]));   // dt A1 = V* - V
+    const float dXc = 0.5f * cx * dv.h;
+    const df vn = df_add(V[s], df{0.5f * (dv.h + h2 * D[s] + a.dfk[6 + 2 * s]), 0.f});
+    if (!(fabsf(dXc) < half_box)) bad |= isfinite(dXc) ? 2 : 1;
+    if (!isfinite(vn.h)) bad |= 1;
+    q[s] = wrap_fix(q[s] + f_to_fix52(dXc), g.qL, img[s]);
+    V[s] = vn;
+  }
+}
+
 // FP64 position of a fixed-point coordinate and velocity of a float pair
 // (the all-FP64 kernel and its adjoint read the state through these).
 __device__ __forceinline__ double pos_of_fix(long long q, const Geom &g) {
@@ -467,6 +577,57 @@ __device__ __forceinline__ void heun_step64(const StepArgs &a, long long q[3], d
     const double xn = x[s] + a.half_dt * (v[s] + vs[s]);
     const double vn = v[s] + a.half_dt * (a1[s] + a2);
     if (!(fabs(xn - x[s]) < 0.5 * g.L)) bad |= fabs(xn) <= 1e300 ? 2 : 1;
+    if (!isfinite(vn)) bad |= 1;
+    q[s] = wrap_fix(d_to_fix52(__dmul_rn(xn, g.inv_dx)), g.qL, img[s]);
+    V[s] = df_of_double(vn);
+  }
+}
+
+// The two stages in FP64 arithmetic (see heun_stage1_df).
+__device__ __forceinline__ void heun_stage1_64(const StepArgs &a, long long q[3], const df V[3],
+                                               df Vs[3], double tau, int img[3], int &bad) {
+  const Geom &g = a.geo;
+  const double itau = 1.0 / tau;
+  double x[3], v[3], u1[3];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    x[s] = pos_of_fix(q[s], g);
+    v[s] = vel_of_df(V[s]);
+  }
+  interp64(a.field, g, x[0], x[1], x[2], u1[0], u1[1], u1[2]);
+  const double f1 = a.drag ? drag_factor64(a.drag_c, tau, u1, v) * itau : itau;
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const double a1 = (u1[s] - v[s]) * f1 + a.g[s];
+    const double xs = predictor64(x[s], v[s], a.dt);
+    const double vs = v[s] + a.dt * a1;
+    if (!(fabs(xs - x[s]) < 0.5 * g.L)) bad |= fabs(xs) <= 1e300 ? 2 : 1;
+    if (!isfinite(vs)) bad |= 1;
+    q[s] = wrap_fix(d_to_fix52(__dmul_rn(xs, g.inv_dx)), g.qL, img[s]);
+    Vs[s] = df_of_double(vs);
+  }
+}
+
+__device__ __forceinline__ void heun_stage2_64(const StepArgs &a, long long q[3], df V[3],
+                                               const df Vs[3], double tau, int img[3],
+                                               int &bad) {
+  const Geom &g = a.geo;
+  const double itau = 1.0 / tau;
+  double xs[3], v[3], vs[3], u2[3];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    xs[s] = pos_of_fix(q[s], g);
+    v[s] = vel_of_df(V[s]);
+    vs[s] = vel_of_df(Vs[s]);
+  }
+  interp64(a.field, g, xs[0], xs[1], xs[2], u2[0], u2[1], u2[2]);
+  const double f2 = a.drag ? drag_factor64(a.drag_c, tau, u2, vs) * itau : itau;
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const double a2 = (u2[s] - vs[s]) * f2 + a.g[s];
+    const double xn = xs[s] + a.half_dt * (vs[s] - v[s]);
+    const double vn = 0.5 * (v[s] + vs[s]) + a.half_dt * a2;
+    if (!(fabs(xn - xs[s]) < 0.5 * g.L)) bad |= fabs(xn) <= 1e300 ? 2 : 1;
     if (!isfinite(vn)) bad |= 1;
     q[s] = wrap_fix(d_to_fix52(__dmul_rn(xn, g.inv_dx)), g.qL, img[s]);
     V[s] = df_of_double(vn);

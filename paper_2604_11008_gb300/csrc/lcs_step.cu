@@ -119,33 +119,43 @@ cudaError_t launch_field_expand(const void *src, int N, FieldKind kind, double *
 
 template <int KIND, int CAP>
 cudaError_t launch_step_kind(const StepGroup<CAP> &pb, int mode, int block, int items,
-                             bool evolve, int grid, cudaStream_t st);
+                             bool evolve, int stage, int grid, cudaStream_t st);
 template <int KIND>
-int step_occupancy_kind(int mode, int block, int items, bool evolve, bool pf_tau, bool pf_img);
+int step_occupancy_kind(int mode, int block, int items, bool evolve, int stage, bool pf_tau,
+                        bool pf_img, bool pf_vs);
 
 template <int CAP>
 cudaError_t launch_step_group(const StepGroup<CAP> &pb, FieldKind kind, int mode, int block,
-                              int items, bool evolve, int grid, cudaStream_t st) {
+                              int items, bool evolve, int stage, int grid, cudaStream_t st) {
   switch (kind) {
-    case FK_F64: return launch_step_kind<FK_F64, CAP>(pb, mode, block, items, evolve, grid, st);
-    case FK_DF: return launch_step_kind<FK_DF, CAP>(pb, mode, block, items, evolve, grid, st);
-    case FK_F32: return launch_step_kind<FK_F32, CAP>(pb, mode, block, items, evolve, grid, st);
-    case FK_BF16: return launch_step_kind<FK_BF16, CAP>(pb, mode, block, items, evolve, grid, st);
+    case FK_F64:
+      return launch_step_kind<FK_F64, CAP>(pb, mode, block, items, evolve, stage, grid, st);
+    case FK_DF:
+      return launch_step_kind<FK_DF, CAP>(pb, mode, block, items, evolve, stage, grid, st);
+    case FK_F32:
+      return launch_step_kind<FK_F32, CAP>(pb, mode, block, items, evolve, stage, grid, st);
+    case FK_BF16:
+      return launch_step_kind<FK_BF16, CAP>(pb, mode, block, items, evolve, stage, grid, st);
   }
   return cudaErrorInvalidValue;
 }
 template cudaError_t launch_step_group<1>(const StepGroup<1> &, FieldKind, int, int, int, bool,
-                                          int, cudaStream_t);
+                                          int, int, cudaStream_t);
 template cudaError_t launch_step_group<GROUP_ENS>(const StepGroup<GROUP_ENS> &, FieldKind, int,
-                                                  int, int, bool, int, cudaStream_t);
+                                                  int, int, bool, int, int, cudaStream_t);
 
 int step_kernel_occupancy(FieldKind kind, int mode, int block, int items, bool evolve,
-                          bool pf_tau, bool pf_img) {
+                          int stage, bool pf_tau, bool pf_img, bool pf_vs) {
   switch (kind) {
-    case FK_F64: return step_occupancy_kind<FK_F64>(mode, block, items, evolve, pf_tau, pf_img);
-    case FK_DF: return step_occupancy_kind<FK_DF>(mode, block, items, evolve, pf_tau, pf_img);
-    case FK_F32: return step_occupancy_kind<FK_F32>(mode, block, items, evolve, pf_tau, pf_img);
-    case FK_BF16: return step_occupancy_kind<FK_BF16>(mode, block, items, evolve, pf_tau, pf_img);
+    case FK_F64:
+      return step_occupancy_kind<FK_F64>(mode, block, items, evolve, stage, pf_tau, pf_img, pf_vs);
+    case FK_DF:
+      return step_occupancy_kind<FK_DF>(mode, block, items, evolve, stage, pf_tau, pf_img, pf_vs);
+    case FK_F32:
+      return step_occupancy_kind<FK_F32>(mode, block, items, evolve, stage, pf_tau, pf_img, pf_vs);
+    case FK_BF16:
+      return step_occupancy_kind<FK_BF16>(mode, block, items, evolve, stage, pf_tau, pf_img,
+                                          pf_vs);
   }
   return 0;
 }
@@ -274,7 +284,7 @@ cudaError_t launch_unpack(const BatchArgs &bt, int total_P, cudaStream_t st) {
 // The old input buffer becomes the next output with the layout from
 // k_finish; the output becomes the input.
 // One block per ensemble; block 0 also resets the step groups' tile counters.
-__global__ void k_flip(BatchArgs bt) {
+__global__ void k_flip(BatchArgs bt, int count_step) {
   const StepArgs &a = bt.args[blockIdx.x];
   const int ph = *a.m.phase;
   for (int d = threadIdx.x; d < a.geo.Ptot; d += blockDim.x) {
@@ -285,14 +295,14 @@ __global__ void k_flip(BatchArgs bt) {
   if (threadIdx.x == 0) {
     *a.m.phase = ph ^ 1;
     *a.m.tile_counter = 0u;
-    *a.m.nstep += 1;
+    if (count_step) *a.m.nstep += 1;
   }
   if (blockIdx.x == 0)
     for (int k = threadIdx.x; k < bt.ngroups; k += blockDim.x) bt.counter[k] = 0u;
 }
 
-cudaError_t launch_flip(const BatchArgs &bt, cudaStream_t st) {
-  k_flip<<<bt.n_ens, 1024, 0, st>>>(bt);
+cudaError_t launch_flip(const BatchArgs &bt, cudaStream_t st, int count_step) {
+  k_flip<<<bt.n_ens, 1024, 0, st>>>(bt, count_step);
   return cudaGetLastError();
 }
 

@@ -457,11 +457,13 @@ struct ParkLayout {
   }
 };
 
+// Stage-velocity rows (migration per stage) follow the bins: 3 rows of T
+// float pairs at offset ParkLayout<T>::bytes(tau, img).
 template <int T>
 __device__ __forceinline__ void park_put(unsigned char *pk, bool lay_tau, bool lay_img,
                                          const Rec &A, int j, const long long x[3],
                                          const df v[3], double tau, uint32_t id,
-                                         const int img[3], int bin) {
+                                         const int img[3], int bin, const df *vs = nullptr) {
   long long *r8 = (long long *)pk;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
@@ -476,6 +478,11 @@ __device__ __forceinline__ void park_put(unsigned char *pk, bool lay_tau, bool l
     for (int s = 0; s < 3; ++s) r4[(1 + s) * T + j] = (uint32_t)img[s];
   }
   pk[ParkLayout<T>::bytes(lay_tau, lay_img) - T + j] = (unsigned char)bin;
+  if (vs) {
+    float2 *rv = (float2 *)(pk + ParkLayout<T>::bytes(lay_tau, lay_img));
+#pragma unroll
+    for (int s = 0; s < 3; ++s) rv[s * T + j] = df_to2(vs[s]);
+  }
 }
 
 // Copy parked row j to record i of R (and its bin to bins[i] when given).
@@ -496,16 +503,23 @@ __device__ __forceinline__ void park_get(const unsigned char *pk, bool lay_tau, 
     for (int s = 0; s < 3; ++s) R.img[s][i] = (int32_t)r4[(1 + s) * T + j];
   }
   if (bins) bins[i] = pk[ParkLayout<T>::bytes(lay_tau, lay_img) - T + j];
+  if (R.vs[0]) {
+    const float2 *rv = (const float2 *)(pk + ParkLayout<T>::bytes(lay_tau, lay_img));
+#pragma unroll
+    for (int s = 0; s < 3; ++s) R.vs[s][i] = rv[s * T + j];
+  }
 }
 
 // Load and integrate the tile's particles (ITEMS per thread, consecutive):
 // Heun step, wrap, destination bin (-2 for no particle), the per-thread
 // packed (stay << 16 | leave) count and the block's direction histogram.
-template <int KIND, int ITEMS, bool EVOLVE>
+// STAGE 0: the whole Heun step; 1: the predictor stage (x becomes X*, vs
+// receives V*); 2: the corrector stage (reads vs).
+template <int KIND, int ITEMS, bool EVOLVE, int STAGE>
 __device__ __forceinline__ unsigned integrate_items(const StepArgs &a, const TileMeta &mt,
                                                     BlockShared &sh, long long x[][3],
                                                     df v[][3], double tau[], uint32_t id[],
-                                                    int img[][3], int bin[]) {
+                                                    int img[][3], int bin[], df vs[][3]) {
   const Rec &A = a.buf[mt.ph];
   const int64_t l0 = mt.first + (int64_t)threadIdx.x * ITEMS;
   unsigned packed = 0;
@@ -516,10 +530,23 @@ __device__ __forceinline__ unsigned integrate_items(const StepArgs &a, const Til
     bin[k] = -2;
     if (l0 + k < mt.cnt) {
       load_rec(A, mt.bA + l0 + k, x[k], v[k], tau[k], id[k], img[k], a.tau_const);
-      if (KIND == FK_F64) heun_step64<EVOLVE>(a, x[k], v[k], tau[k], img[k], bad, tt);
-      else if (KIND == FK_DF)
-        heun_step_df<KIND, EVOLVE>(a, x[k], v[k], tau[k], img[k], bad, FieldBox{}, tt);
-      else heun_step_lo<KIND, EVOLVE>(a, x[k], v[k], tau[k], img[k], bad, FieldBox{}, tt);
+      if (STAGE == 0) {
+        if (KIND == FK_F64) heun_step64<EVOLVE>(a, x[k], v[k], tau[k], img[k], bad, tt);
+        else if (KIND == FK_DF)
+          heun_step_df<KIND, EVOLVE>(a, x[k], v[k], tau[k], img[k], bad, FieldBox{}, tt);
+        else heun_step_lo<KIND, EVOLVE>(a, x[k], v[k], tau[k], img[k], bad, FieldBox{}, tt);
+      } else if (STAGE == 1) {
+        if (KIND == FK_F64) heun_stage1_64(a, x[k], v[k], vs[k], tau[k], img[k], bad);
+        else if (KIND == FK_DF) heun_stage1_df<KIND>(a, x[k], v[k], vs[k], tau[k], img[k], bad);
+        else heun_stage1_lo<KIND>(a, x[k], v[k], vs[k], tau[k], img[k], bad);
+      } else {
+        const int64_t i = mt.bA + l0 + k;
+#pragma unroll
+        for (int s = 0; s < 3; ++s) vs[k][s] = df_from2(A.vs[s][i]);
+        if (KIND == FK_F64) heun_stage2_64(a, x[k], v[k], vs[k], tau[k], img[k], bad);
+        else if (KIND == FK_DF) heun_stage2_df<KIND>(a, x[k], v[k], vs[k], tau[k], img[k], bad);
+        else heun_stage2_lo<KIND>(a, x[k], v[k], vs[k], tau[k], img[k], bad);
+      }
       int b = dest_bin(a.geo, mt.ps, x[k]);
       if (b < 0) {
         bad |= 2;
@@ -545,7 +572,7 @@ __device__ __forceinline__ unsigned integrate_items(const StepArgs &a, const Til
 // not stall the block.  The parked tile is then written out with coalesced
 // stores: its stayers form one contiguous run of the output window and its
 // leavers one contiguous run of the pack buffer.
-template <int KIND, int BLOCK, int ITEMS, int CAP, bool EVOLVE>
+template <int KIND, int BLOCK, int ITEMS, int CAP, bool EVOLVE, int STAGE>
 __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockShared &sh,
                                               const int *s_off, unsigned char *pk) {
   constexpr int T = BLOCK * ITEMS;
@@ -566,12 +593,14 @@ __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockSha
   double tau[ITEMS];
     uint32_t id[ITEMS];
     int img[ITEMS][3], bin[ITEMS];
+    df vs[ITEMS][3];
     unsigned packed = 0;
     TileMeta m;
     if (fresh) {
       const int e = CAP == 1 ? 0 : find_ensemble(s_off, n, g);
       m = tile_meta<T>(pb.a[e], g, e, g - s_off[e]);
-      packed = integrate_items<KIND, ITEMS, EVOLVE>(pb.a[e], m, sh, x, v, tau, id, img, bin);
+      packed = integrate_items<KIND, ITEMS, EVOLVE, STAGE>(pb.a[e], m, sh, x, v, tau, id, img,
+                                                           bin, vs);
     }
     if (parked) {
       const TileMeta pm = s_park;
@@ -646,7 +675,8 @@ __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockSha
     for (int k = 0; k < ITEMS; ++k) {
       if (bin[k] == -2) continue;
       const int j = bin[k] == BIN_STAY ? rs++ : T - 1 - rm++;
-      park_put<T>(pk, lay_tau, lay_img, A, j, x[k], v[k], tau[k], id[k], img[k], bin[k]);
+      park_put<T>(pk, lay_tau, lay_img, A, j, x[k], v[k], tau[k], id[k], img[k], bin[k],
+                  STAGE == 1 ? vs[k] : nullptr);
     }
     parked = true;
   }
@@ -668,7 +698,7 @@ constexpr long long PF_WAIT_LIMIT = 1LL << 20;  // bounded wait for a tile's bul
 // staged in shared memory; 2: records of the next tile prefetched by bulk
 // copies (TMA) into the second of two shared-memory buffers while the
 // current tile is integrated, scanned and scattered.
-template <int KIND, int BLOCK, int ITEMS, int CAP, int MODE, bool EVOLVE>
+template <int KIND, int BLOCK, int ITEMS, int CAP, int MODE, bool EVOLVE, int STAGE>
 __global__ void __launch_bounds__(BLOCK, (step_min_blocks<KIND, BLOCK, ITEMS>()))
     k_step_block(const __grid_constant__ StepGroup<CAP> pb) {
   constexpr int T = BLOCK * ITEMS;
@@ -689,7 +719,7 @@ __global__ void __launch_bounds__(BLOCK, (step_min_blocks<KIND, BLOCK, ITEMS>())
   }
   if (MODE == 3) {
     __syncthreads();
-    step_deferred<KIND, BLOCK, ITEMS, CAP, EVOLVE>(pb, sh, s_off, s_dyn);
+    step_deferred<KIND, BLOCK, ITEMS, CAP, EVOLVE, STAGE>(pb, sh, s_off, s_dyn);
     return;
   }
   if (MODE != 2) {
@@ -750,18 +780,21 @@ __global__ void __launch_bounds__(BLOCK, (step_min_blocks<KIND, BLOCK, ITEMS>())
 
 // (kernel mode, threads per block, particles per thread) configurations the
 // tuner tries; mode 1 (staged field box) has no all-FP64 form
-// The last argument marks the evolving-field instantiations (mode 3 only).
+// The last two arguments: evolving-field instantiation, Runge-Kutta stage
+// (0: whole step; 1, 2: migration per stage); both exist in mode 3 only.
 #define LCS_STEP_CONFIGS(X, K, C)                                                   \
-  X(K, 0, 256, 2, C, 0) X(K, 0, 256, 1, C, 0) X(K, 0, 128, 2, C, 0)                \
-  X(K, 1, 256, 2, C, 0) X(K, 1, 128, 2, C, 0) X(K, 2, 256, 2, C, 0)                \
-  X(K, 2, 128, 2, C, 0) X(K, 2, 256, 1, C, 0) X(K, 3, 256, 2, C, 0)                \
-  X(K, 3, 128, 2, C, 0) X(K, 3, 256, 1, C, 0) X(K, 3, 256, 2, C, 1)                \
-  X(K, 3, 128, 2, C, 1) X(K, 3, 256, 1, C, 1)
+  X(K, 0, 256, 2, C, 0, 0) X(K, 0, 256, 1, C, 0, 0) X(K, 0, 128, 2, C, 0, 0)       \
+  X(K, 1, 256, 2, C, 0, 0) X(K, 1, 128, 2, C, 0, 0) X(K, 2, 256, 2, C, 0, 0)       \
+  X(K, 2, 128, 2, C, 0, 0) X(K, 2, 256, 1, C, 0, 0) X(K, 3, 256, 2, C, 0, 0)       \
+  X(K, 3, 128, 2, C, 0, 0) X(K, 3, 256, 1, C, 0, 0) X(K, 3, 256, 2, C, 1, 0)       \
+  X(K, 3, 128, 2, C, 1, 0) X(K, 3, 256, 1, C, 1, 0) X(K, 3, 256, 2, C, 0, 1)       \
+  X(K, 3, 256, 2, C, 0, 2) X(K, 3, 256, 1, C, 0, 1) X(K, 3, 256, 1, C, 0, 2)
 
 // Dynamic shared memory of a configuration: the staged field box (mode 1),
 // the two record buffers (mode 2) or the parked tile (mode 3).
-constexpr int step_dyn_smem(int kind, int mode, int tile, bool tau, bool img) {
-  return mode == 1   ? (kind != FK_F64 ? STAGE_BYTES : 0)
+constexpr int step_dyn_smem(int kind, int mode, int tile, bool tau, bool img, bool vs = false) {
+  return mode == 3 && vs ? step_dyn_smem(kind, 3, tile, tau, img) + 3 * tile * 8
+         : mode == 1 ? (kind != FK_F64 ? STAGE_BYTES : 0)
          : mode == 2 ? 2 * ((6 + (tau ? 1 : 0)) * (tile + 2) * 8 +
                             (1 + (img ? 3 : 0)) * (tile + 4) * 4)
          : mode == 3 ? (6 + (tau ? 1 : 0)) * tile * 8 + (1 + (img ? 3 : 0)) * tile * 4 + tile
@@ -772,16 +805,17 @@ constexpr int step_dyn_smem(int kind, int mode, int tile, bool tau, bool img) {
 // One field storage's configurations: launch / occupancy (lcs_step_<kind>.cu).
 template <int KIND, int CAP>
 cudaError_t launch_step_kind(const StepGroup<CAP> &pb, int mode, int block, int items,
-                             bool evolve, int grid, cudaStream_t st) {
-#define LCS_LAUNCH(K, M, B, I, C, E)                                                       \
-  if (mode == M && block == B && items == I && evolve == (E != 0) &&                      \
+                             bool evolve, int stage, int grid, cudaStream_t st) {
+#define LCS_LAUNCH(K, M, B, I, C, E, S)                                                    \
+  if (mode == M && block == B && items == I && evolve == (E != 0) && stage == S &&        \
       !(M == 1 && K == FK_F64)) {                                                          \
     static_assert(PfLayout<B * I>::bytes(true, true) ==                                    \
                       step_dyn_smem(K, 2, B * I, true, true) / 2, "layout");               \
     static_assert(ParkLayout<B * I>::bytes(true, false) ==                                 \
                       step_dyn_smem(K, 3, B * I, true, false), "layout");                  \
-    auto ker = k_step_block<K, B, I, CAP, M, (E != 0)>;                                    \
-    const int smem = step_dyn_smem(K, M, B * I, pb.pf_tau != 0, pb.pf_img != 0);           \
+    auto ker = k_step_block<K, B, I, CAP, M, (E != 0), S>;                                 \
+    const int smem = step_dyn_smem(K, M, B * I, pb.pf_tau != 0, pb.pf_img != 0,            \
+                                   pb.pf_vs != 0);                                         \
     if (smem) cudaFuncSetAttribute(ker, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
     ker<<<grid, B, smem, st>>>(pb);                                                        \
     return cudaGetLastError();                                                             \
@@ -792,13 +826,14 @@ cudaError_t launch_step_kind(const StepGroup<CAP> &pb, int mode, int block, int 
 }
 
 template <int KIND>
-int step_occupancy_kind(int mode, int block, int items, bool evolve, bool pf_tau, bool pf_img) {
+int step_occupancy_kind(int mode, int block, int items, bool evolve, int stage, bool pf_tau,
+                        bool pf_img, bool pf_vs) {
   int n = 0;
-#define LCS_OCC(K, M, B, I, C, E)                                                          \
-  if (mode == M && block == B && items == I && evolve == (E != 0) &&                      \
+#define LCS_OCC(K, M, B, I, C, E, S)                                                       \
+  if (mode == M && block == B && items == I && evolve == (E != 0) && stage == S &&        \
       !(M == 1 && K == FK_F64)) {                                                          \
-    auto ker = k_step_block<K, B, I, C, M, (E != 0)>;                                      \
-    const int smem = step_dyn_smem(K, M, B * I, pf_tau, pf_img);                           \
+    auto ker = k_step_block<K, B, I, C, M, (E != 0), S>;                                   \
+    const int smem = step_dyn_smem(K, M, B * I, pf_tau, pf_img, pf_vs);                    \
     if (smem) cudaFuncSetAttribute(ker, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ker, B, smem);                       \
   }
@@ -809,9 +844,9 @@ int step_occupancy_kind(int mode, int block, int items, bool evolve, bool pf_tau
 
 #define LCS_STEP_KIND_INSTANTIATE(K)                                                       \
   template cudaError_t launch_step_kind<K, 1>(const StepGroup<1> &, int, int, int, bool, int, \
-                                              cudaStream_t);                              \
+                                              int, cudaStream_t);                         \
   template cudaError_t launch_step_kind<K, GROUP_ENS>(const StepGroup<GROUP_ENS> &, int, int, \
-                                                      int, bool, int, cudaStream_t);      \
-  template int step_occupancy_kind<K>(int, int, int, bool, bool, bool);
+                                                      int, bool, int, int, cudaStream_t); \
+  template int step_occupancy_kind<K>(int, int, int, bool, int, bool, bool, bool);
 
 }  // namespace lcs
