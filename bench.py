@@ -61,12 +61,14 @@ def build_workload(name: str, device: str, n_override: int | None = None):
 # ---------------------------------------------------------------- traffic
 
 def library_source_hash() -> str:
-    """SHA-256 over the CUDA sources and the C header of the library."""
+    """SHA-256 over the sources that define the step kernel (its templates,
+    the physics and arithmetic headers, the per-storage instantiations)."""
     import glob
     import hashlib
     root = os.path.dirname(os.path.abspath(__file__))
     csrc = os.path.join(root, "paper_2604_11008_gb300", "csrc")
-    files = sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")))
+    files = sorted(glob.glob(os.path.join(csrc, "lcs_step_*.cu")) +
+                   glob.glob(os.path.join(csrc, "*.cuh")))
     files.append(os.path.join(root, "include", "lcs.h"))
     h = hashlib.sha256()
     for f in files:
