@@ -127,6 +127,16 @@ def _dev(t, dtype):
     return t.to(device="cuda", dtype=dtype).contiguous()
 
 
+def _dev_or_host(t, dtype):
+    """A contiguous tensor of `dtype` where `t` already is: CUDA tensors stay
+    on the device, host arrays stay on the host (the library copies them
+    itself, at full speed from pinned memory)."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        t = torch.as_tensor(np.asarray(t))
+    return t.to(dtype=dtype).contiguous()
+
+
 class Simulator:
     """Particles of one or more ensembles advancing in frozen periodic fields.
 
@@ -311,11 +321,12 @@ class Simulator:
 
     def set_state(self, x, v, ids, seg, tau=None, img=None, ens: int = 0):
         import torch
-        xs = _dev(x, torch.float64)
-        vs = _dev(v, torch.float64)
-        ii = _dev(ids, torch.int32)
-        tt = None if tau is None else _dev(tau, torch.float64)
-        im = None if img is None else _dev(img, torch.int32)
+        # host or device buffers, copied by lcs_set_state (synchronising)
+        xs = _dev_or_host(x, torch.float64)
+        vs = _dev_or_host(v, torch.float64)
+        ii = _dev_or_host(ids, torch.int32)
+        tt = None if tau is None else _dev_or_host(tau, torch.float64)
+        im = None if img is None else _dev_or_host(img, torch.int32)
         seg = np.ascontiguousarray(seg, dtype=np.int64)
         self._check(lib().lcs_set_state(self._ctx, ens, _ptr(xs), _ptr(vs), _ptr(tt), _ptr(ii),
                                         _ptr(im), _ptr(seg)))

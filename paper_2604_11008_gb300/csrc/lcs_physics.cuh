@@ -7,6 +7,7 @@
 #pragma once
 
 #include "lcs_df.cuh"
+#include "lcs_dfmath.cuh"
 #include "lcs_internal.cuh"
 
 namespace lcs {
@@ -240,9 +241,13 @@ __device__ __forceinline__ void interp_any(const void *field, int N, const long 
 // Drag factor of Eq. (7): f = 1 + 0.15 Re_p^0.687 with Re_p^2 = c tau |D|^2,
 // c = 18 / (nu rho_p/rho) (the radius from tau_p = (2/9)(rho_p/rho) r^2/nu,
 // Sec. 2.2), D = U - V, so f = 1 + 0.15 (c tau |D|^2)^(0.687/2).  The float-
-// float kernel evaluates it in FP64 with CUDA's pow (about 1 ulp), the
-// FP32/BF16 kernels in FP32 with powf.
+// float kernel evaluates it with the float-float log2 / exp2 of
+// lcs_dfmath.cuh (relative error about 2^-46) whenever c tau lies in
+// [2^-90, 2^90], which covers every physical case, else in FP64 with CUDA's
+// pow; the FP32/BF16 kernels in FP32 with powf.
 static __device__ __noinline__ df drag_factor_df(double c, double tau, const df D[3]) {
+  const df ct = df_mul(split_d(c), split_d(tau));
+  if (ct.h >= 8.0779356e-28f && ct.h <= 1.2379400e27f) return drag_factor_dfp(ct, D);
   double d2 = 0.0;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {

@@ -2,9 +2,11 @@
 
 f = 1 + 0.15 Re_p^0.687, Re_p = 2 r |V - U| / nu, r from
 tau_p = (2/9)(rho_p/rho) r^2 / nu (Sec. 2.2).  The FP64 and float-float
-kernels evaluate f with FP64 pow and must meet the FP64 bar (1e-12); the
+kernels must meet the FP64 bar (1e-12); the
 FP32 / BF16 kernels use FP32 powf and must meet their bars against the oracle
-on the same rounded field and on the FP64 field.  With a small viscosity the
+on the same rounded field and on the FP64 field.  The float-float kernel's
+power is its own table-driven float-float log2 / exp2; slips over twelve
+decades run it across its whole reduction range.  With a small viscosity the
 particle Reynolds numbers reach O(1-10), so f departs from 1 by tens of
 percent and a wrong factor could not hide inside the tolerances.
 """
@@ -13,7 +15,7 @@ import pytest
 
 import oracle
 import synth
-from helpers import L, assert_same_storage, gpu_state, traj_errors
+from helpers import L, assert_same_storage, by_id, gpu_state, traj_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -71,6 +73,32 @@ def test_nonlinear_drag_fp64_trajectories(lcs, kernel):
     oracle.run(stokes, field, L, P, 0.0, 0.005, (0.0, 0.0, -9.8), steps, sort_every=7, brick=4)
     ex_s, ev_s, _, _ = traj_errors(st["x"], st["img"], st["v"], st["ids"], stokes, x)
     assert ev_s > 1e-3, ev_s
+
+
+@pytest.mark.parametrize("kernel", ["df", "fp64"])
+def test_nonlinear_drag_over_decades_of_slip(lcs, kernel):
+    # |V - U| from 1e-9 to 1e3 (Re_p from about 1e-9 to 1e3), every particle
+    # checked on its own against the oracle
+    N, n, P, steps, dt = 16, 6000, (2, 2, 2), 4, 0.001
+    field, x, _, tau = case(seed=123, N=N, n=n)
+    u = np.stack(oracle.interp(field, L, x))
+    rng = np.random.default_rng(123)
+    d = rng.standard_normal(x.shape)
+    d *= 10.0 ** rng.uniform(-9, 3, n) / np.linalg.norm(d, axis=0)
+    v = np.ascontiguousarray(u + d)
+    sim = lcs.Simulator(field, x, v, dt, tau=tau, sub=P, track_images=True, kernel=kernel,
+                        drag="nonlinear", nu=NU, density_ratio=RHO)
+    sim.step(steps)
+    st = gpu_state(sim)
+    ref = oracle.initial_state(N, L, P, x, v, tau, track_img=True)
+    oracle.run(ref, field, L, P, 0.0, dt, (0.0, 0.0, 0.0), steps, drag=DRAG)
+    ex, ev, _, _ = traj_errors(st["x"], st["img"], st["v"], st["ids"], ref, x)
+    assert ex < 1e-12 and ev < 1e-12, (ex, ev)
+    xg, vg, ig = by_id(st["ids"], st["x"], st["v"], st["img"])
+    xr, vr, ir = by_id(ref.ids, ref.x, ref.v, ref.img)
+    dv = np.linalg.norm(vg - vr, axis=0) / np.linalg.norm(vr, axis=0)
+    dx = np.linalg.norm(xg + L * ig - xr - L * ir, axis=0) / np.linalg.norm(xr + L * ir - x, axis=0)
+    assert dv.max() < 1e-11 and dx.max() < 1e-11, (dv.max(), dx.max())
 
 
 @pytest.mark.parametrize("dtype,tol_q,tol_64", [("f32", 1e-6, 1e-5), ("bf16", 1e-5, 1e-2)])
