@@ -177,12 +177,12 @@ template <int KIND>
 __device__ __forceinline__ void field_pair(const void *field, uint32_t cell, float h[3],
                                            float l[3]) {
   if (KIND == FK_DF) {
-    const float4 A = __ldg((const float4 *)field + 2 * (size_t)cell);
-    const float4 B = __ldg((const float4 *)field + 2 * (size_t)cell + 1);
+    float4 A, B;
+    ldg_cell32((const float4 *)field + 2 * (size_t)cell, A, B);
     h[0] = A.x, h[1] = A.y, h[2] = A.z, l[0] = A.w, l[1] = B.x, l[2] = B.y;
   } else if (KIND == FK_F64) {
-    const double2 A = __ldg((const double2 *)field + 2 * (size_t)cell);
-    const double2 B = __ldg((const double2 *)field + 2 * (size_t)cell + 1);
+    double2 A, B;
+    ldg_cell32((const double2 *)field + 2 * (size_t)cell, A, B);
     const df u = split_d(A.x), v = split_d(A.y), w = split_d(B.x);
     h[0] = u.h, h[1] = v.h, h[2] = w.h, l[0] = u.l, l[1] = v.l, l[2] = w.l;
   } else if (KIND == FK_F32) {

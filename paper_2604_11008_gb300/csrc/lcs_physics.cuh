@@ -14,6 +14,22 @@ namespace lcs {
 
 // ---------------------------------------------------------------- interpolation
 
+// One 32-byte field record (a cell of the float-pair or the FP64 field) in a
+// single 256-bit non-coherent load (sm_100 and later); the record must be
+// 32-byte aligned, which the cudaMalloc'd field arrays guarantee.  Two
+// 128-bit loads per cell made the float-float step 6 % slower.
+__device__ __forceinline__ void ldg_cell32(const float4 *p, float4 &a, float4 &b) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+      : "l"(p));
+}
+
+__device__ __forceinline__ void ldg_cell32(const double2 *p, double2 &a, double2 &b) {
+  asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];"
+      : "=d"(a.x), "=d"(a.y), "=d"(b.x), "=d"(b.y)
+      : "l"(p));
+}
+
 struct Stencil {
   uint32_t c[8];   // corner cell indices, order (a, b, d) = x outer, z inner
   double w[8];     // FP64 weights wx[a] * wy[b] * wz[d]
@@ -64,8 +80,8 @@ __device__ __forceinline__ void interp64(const void *field, const Geom &g, doubl
   double au = 0.0, av = 0.0, aw = 0.0;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    const double2 p = __ldg(f + 2 * (size_t)S.c[q]);
-    const double2 r = __ldg(f + 2 * (size_t)S.c[q] + 1);
+    double2 p, r;
+    ldg_cell32(f + 2 * (size_t)S.c[q], p, r);
     au = fma(S.w[q], p.x, au);
     av = fma(S.w[q], p.y, av);
     aw = fma(S.w[q], r.x, aw);
@@ -159,7 +175,7 @@ __device__ __forceinline__ void interp_df(const float4 *__restrict__ f, int N,
           A = sm[0], B = sm[1];
         } else {
           const size_t cell = (size_t)(ii[a] + jj[b] + kk[d]);
-          A = __ldg(f + 2 * cell), B = __ldg(f + 2 * cell + 1);
+          ldg_cell32(f + 2 * cell, A, B);
         }
         const float hv[3] = {A.x, A.y, A.z}, lv[3] = {A.w, B.x, B.y};
 #pragma unroll

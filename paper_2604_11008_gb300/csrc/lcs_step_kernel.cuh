@@ -337,8 +337,8 @@ __device__ __forceinline__ void step_block_tile(const StepArgs &a, const TileMet
         while (gz >= N) gz -= N;
         const size_t g = (size_t)gx + (size_t)N * ((size_t)gy + (size_t)N * gz);
         if (KIND == FK_DF) {
-          ((float4 *)stage)[2 * c] = __ldg((const float4 *)a.field + 2 * g);
-          ((float4 *)stage)[2 * c + 1] = __ldg((const float4 *)a.field + 2 * g + 1);
+          ldg_cell32((const float4 *)a.field + 2 * g, ((float4 *)stage)[2 * c],
+                     ((float4 *)stage)[2 * c + 1]);
         } else if (KIND == FK_F32) {
           ((float4 *)stage)[c] = __ldg((const float4 *)a.field + g);
         } else {
