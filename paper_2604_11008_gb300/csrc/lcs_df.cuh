@@ -109,6 +109,14 @@ __device__ __forceinline__ long long f_to_fix52(float f) {
   return (u & 0x80000000u) ? -(long long)q : (long long)q;
 }
 
+// The same value by one float -> int64 conversion that truncates the exact
+// product f 2^52 toward zero (bit-identical to f_to_fix52 for |f| < 2^11).
+// Fewer instructions: 6 % faster in the float-float step, which converts
+// twelve values per particle; measured no faster in the FP32 step (six).
+__device__ __forceinline__ long long f_to_fix52_cvt(float f) {
+  return __float2ll_rz(__fmul_rn(f, 4503599627370496.0f));  // 2^52
+}
+
 // Fixed point with 52 fraction bits of a non-negative or negative double
 // with |x| < 2^11 (exact up to the truncated bits below 2^-52).
 __device__ __forceinline__ long long d_to_fix52(double x) {

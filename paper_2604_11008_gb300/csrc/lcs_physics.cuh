@@ -117,7 +117,7 @@ __device__ __forceinline__ long long fix_stage1(double x, double inv_dx) {
 // Coordinate of the predictor X* = X + dt V: q1 + (dt N/L) V in fixed point.
 __device__ __forceinline__ long long fix_stage2(long long q1, df V, df cx) {
   const df cv = df_mul(cx, V);
-  return q1 + f_to_fix52(cv.h) + f_to_fix52(cv.l);
+  return q1 + f_to_fix52_cvt(cv.h) + f_to_fix52_cvt(cv.l);
 }
 
 // The same for the FP32 increments of FP32 / BF16 storage: q1 + fix(cx V)
@@ -372,7 +372,7 @@ __device__ __forceinline__ void heun_step_df(const StepArgs &a, long long q[3], 
     const df vn = df_add(V[s], dV);
     if (!(fabsf(dXc.h) < half_box)) bad |= isfinite(dXc.h) ? 2 : 1;
     if (!isfinite(vn.h)) bad |= 1;
-    q[s] = wrap_fix(q[s] + f_to_fix52(dXc.h) + f_to_fix52(dXc.l), g.qL, img[s]);
+    q[s] = wrap_fix(q[s] + f_to_fix52_cvt(dXc.h) + f_to_fix52_cvt(dXc.l), g.qL, img[s]);
     V[s] = vn;
   }
 }
@@ -479,7 +479,7 @@ __device__ __forceinline__ void heun_stage2_df(const StepArgs &a, long long q[3]
         df_scale2(df_add(df_add(V[s], Vs[s]), df_add(df_mul(h2, D[s]), gd)), 0.5f);
     if (!(fabsf(dXc.h) < half_box)) bad |= isfinite(dXc.h) ? 2 : 1;
     if (!isfinite(vn.h)) bad |= 1;
-    q[s] = wrap_fix(q[s] + f_to_fix52(dXc.h) + f_to_fix52(dXc.l), g.qL, img[s]);
+    q[s] = wrap_fix(q[s] + f_to_fix52_cvt(dXc.h) + f_to_fix52_cvt(dXc.l), g.qL, img[s]);
     V[s] = vn;
   }
 }
