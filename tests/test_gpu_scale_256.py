@@ -1,0 +1,75 @@
+"""The throughput workload at full size, as bench.py runs it (needs a GPU).
+
+256^3 FP64 field (512 modes, k 1-32), 16,777,216 particles, log-normal tau
+(median 0.05, sigma 0.5), gravity, 4x4x4 subdomains, cell sort every 10
+steps, 1000 steps, step kernel autotuned as in bench.py.  Particles do not
+interact (one-way coupling, Eqs. 5-6), so 20,000 sampled particles are
+checked against the FP64 oracle run on those particles alone (norm-wise
+relative errors within 1e-12; positions compared modulo the period, as the
+run does not track images).  The whole final state is checked for what holds
+at any size: the id multiset is unchanged, every particle sits in the segment
+of the subdomain that contains it (migration, Sec. 2.3.3), and, the last step
+being a sort step, the cell keys inside every segment are in order.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import L
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def final():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2604_11008_gb300 as lcs
+    from paper_2604_11008_gb300 import build
+    build.build()
+    w = synth.WORKLOADS["scale_256"]
+    field, _ = synth.make_field(w, device="cuda")
+    dt = w.dt if w.dt is not None else synth.cfl_dt(synth.max_speed(field), w.N)
+    x, v, tau = synth.make_particles(w, dt)
+    sim = lcs.Simulator(field, x, v, dt, tau=tau, tau_const=w.tau_const, g=w.g, sub=w.sub,
+                        sort_every=w.sort_every)
+    sim.tune(2)                        # advances 2 steps per tried configuration
+    done = 2 * int((sim.tune_trials_ms > 0).sum())
+    assert w.steps % w.sort_every == 0
+    sim.step(w.steps - done)
+    st = sim.get_state(device="cpu")
+    sim.close()
+    st = {k: (a.numpy() if hasattr(a, "numpy") else a) for k, a in st.items()}
+    return w, field.cpu().numpy(), dt, x, v, tau, st
+
+
+def test_sampled_trajectories_against_oracle(final):
+    w, field, dt, x, v, tau, st = final
+    sample = np.sort(np.random.default_rng(256).choice(w.np_, 20_000, replace=False))
+    xs, vs, ts = x[:, sample].copy(), v[:, sample].copy(), tau[sample].copy()
+    img = np.zeros((3, len(sample)), np.int32)
+    oracle.advance(field, L, xs, vs, ts, 0.0, dt, w.g, w.steps, img=img)
+    pos = np.empty(w.np_, np.int64)
+    pos[st["ids"].astype(np.int64)] = np.arange(w.np_)
+    at = pos[sample]
+    d = st["x"][:, at] - xs
+    d -= L * np.round(d / L)           # the same point modulo the period
+    ex = np.linalg.norm(d) / np.linalg.norm(xs + L * img - x[:, sample])
+    ev = np.linalg.norm(st["v"][:, at] - vs) / np.linalg.norm(vs)
+    assert ex < 1e-12 and ev < 1e-12, (ex, ev)
+
+
+def test_ids_segments_and_cell_order(final):
+    w, field, dt, x, v, tau, st = final
+    ids = st["ids"].astype(np.int64)
+    assert np.array_equal(np.sort(ids), np.arange(w.np_))
+    seg = st["seg"]
+    assert seg[0] == 0 and seg[-1] == w.np_ and np.all(np.diff(seg) >= 0)
+    dest, key = oracle.keys(w.N, L, w.sub, 8, st["x"])
+    owner = np.repeat(np.arange(len(seg) - 1), np.diff(seg))
+    assert np.array_equal(dest, owner)
+    # keys non-decreasing inside every segment (drops only at segment starts)
+    drops = np.nonzero(np.diff(key) < 0)[0] + 1
+    assert np.isin(drops, seg[1:-1]).all()
