@@ -304,8 +304,9 @@ def variants_throughput(lcs, torch, w, field, dt, x, v, tau, steps=20, nu=2e-3):
     """The bench workload with the drag factor of Eq. (7) (kinematic viscosity
     nu, density ratio 843) and with a field evolving linearly in time between
     two snapshots (the second a phase-shifted copy of the first), against the
-    frozen field with Stokes drag, and with migration after each Runge-Kutta
-    stage: particle-updates/s for the FP64 field (float-float kernel) and the
+    frozen field with Stokes drag, with migration after each Runge-Kutta
+    stage, and with every subdomain reading its own field brick (owned-field
+    mode, the multi-GPU memory pattern): particle-updates/s for the FP64 field (float-float kernel) and the
     FP32 field, deferred-scatter kernel; and the wall time of the
     pair-separation histogram (g(r)) on the bench state."""
     st = torch.cuda.current_stream()
@@ -313,12 +314,15 @@ def variants_throughput(lcs, torch, w, field, dt, x, v, tau, steps=20, nu=2e-3):
                        f"field between two snapshots", "steps": steps, "unit": UNIT}
     field2 = torch.roll(field, shifts=7, dims=-1)
     for dtype in ("f64", "f32"):
-        for variant in ("stokes", "nonlinear_drag", "evolving_field", "migrate_per_stage"):
+        for variant in ("stokes", "nonlinear_drag", "evolving_field", "migrate_per_stage",
+                        "owned_field"):
             kw = dict(drag="nonlinear", nu=nu) if variant == "nonlinear_drag" else {}
             if variant == "evolving_field":
                 kw = dict(field_next=field2, t_start=0.0, t_field=(0.0, 100.0 * dt))
             if variant == "migrate_per_stage":
                 kw = dict(migrate_per_stage=True)
+            if variant == "owned_field":
+                kw = dict(owned_field=True)
             sim = lcs.Simulator(field, x, v, dt, tau=tau, tau_const=w.tau_const, g=w.g,
                                 sub=w.sub, field_dtype=dtype, sort_every=w.sort_every, **kw)
             sim.step(10)
@@ -330,7 +334,7 @@ def variants_throughput(lcs, torch, w, field, dt, x, v, tau, steps=20, nu=2e-3):
             sim.sync()
             out[f"{dtype}_{variant}"] = x.shape[1] * steps / (e0.elapsed_time(e1) * 1e-3)
             sim.close()
-        for variant in ("nonlinear_drag", "evolving_field", "migrate_per_stage"):
+        for variant in ("nonlinear_drag", "evolving_field", "migrate_per_stage", "owned_field"):
             out[f"{dtype}_{variant}_over_stokes"] = round(out[f"{dtype}_{variant}"] /
                                                           out[f"{dtype}_stokes"], 3)
     del field2

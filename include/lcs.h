@@ -129,6 +129,17 @@ typedef struct {
    * storage order differs.  All ensembles of a context must agree.  Not with
    * field_next or ckpt_every (the deferred-scatter step kernel only). */
   int migrate_per_stage;
+  /* 1: owned-field mode, the memory pattern of the multi-GPU decomposition
+   * (Sec. 2.1, 2.3): every subdomain interpolates only from its own copy of
+   * the field cells it owns plus a halo of two cells per side (its brick,
+   * (N/P_s + 4) cells per axis, built from the field at lcs_init).  A
+   * stencil outside the brick -- a particle moved more than one cell beyond
+   * its subdomain within a stage -- is reported as LCS_ERR_DISPLACEMENT.
+   * Results equal those of the shared field bit for bit otherwise.  All
+   * ensembles of a context must agree.  Not with LCS_KERNEL_FP64,
+   * field_next or ckpt_every; the step kernel is then mode
+   * LCS_STEP_OWNED_FIELD.  0: every subdomain reads the one field copy. */
+  int owned_field;
 } lcs_desc;
 
 /* Create a context for n_ens ensembles (1 <= n_ens <= 1024, all with the same
@@ -244,23 +255,30 @@ lcs_status lcs_profile_steps(lcs_ctx *ctx, int64_t nsteps, double *ms, int64_t *
  *   LCS_STEP_DEFERRED       a block integrates its next tile before it
  *                           resolves the scan prefix of the previous one,
  *                           which waits parked in shared memory and is then
- *                           written out with coalesced stores. */
+ *                           written out with coalesced stores;
+ *   LCS_STEP_OWNED_FIELD    LCS_STEP_DEFERRED reading the subdomains' own
+ *                           field bricks (owned_field contexts only, which
+ *                           use no other mode). */
 #define LCS_STEP_PLAIN 0
 #define LCS_STEP_STAGED_FIELD 1
 #define LCS_STEP_PREFETCH 2
 #define LCS_STEP_DEFERRED 3
+#define LCS_STEP_OWNED_FIELD 4
 
 /* Number of step-kernel configurations lcs_tune tries. */
-#define LCS_TUNE_CONFIGS 11
+#define LCS_TUNE_CONFIGS 13
 
 /* Autotuner: time every step-kernel configuration on steps_per_trial real
  * steps of all ensembles, keep the fastest, and rebuild the step graphs with
  * it.  The configurations, in order, as (threads per block, particles per
  * thread, mode): (256,2,0) (256,1,0) (128,2,0) (256,2,1) (128,2,1)
- * (256,2,2) (128,2,2) (256,1,2) (256,2,3) (128,2,3) (256,1,3).  The first
- * two numbers fix the scan tile.
+ * (256,2,2) (128,2,2) (256,1,2) (256,2,3) (128,2,3) (256,1,3) (256,1,4)
+ * (256,2,4).  The first two numbers fix the scan tile.
  * Configurations of mode LCS_STEP_STAGED_FIELD are skipped for the all-FP64
- * kernel.  The trial steps advance the simulation (steps_per_trial steps per
+ * kernel, every mode but LCS_STEP_DEFERRED for an evolving field or
+ * migration per stage (then with 256 threads only), and every mode but
+ * LCS_STEP_OWNED_FIELD for an owned_field context (and that mode for any
+ * other).  The trial steps advance the simulation (steps_per_trial steps per
  * tried configuration, recorded like any other step); results do not depend
  * on the choice.  *block, *items, *mode (may be NULL) receive the choice;
  * trial_ms (host, LCS_TUNE_CONFIGS doubles, may be NULL) the step-kernel
@@ -272,7 +290,7 @@ lcs_status lcs_tune(lcs_ctx *ctx, int steps_per_trial, int *block, int *items, i
 /* Select one of the LCS_TUNE_CONFIGS step-kernel configurations by hand
  * (the values lcs_tune chooses among); the step graphs are rebuilt.
  * Results do not depend on the choice.  LCS_ERR_ARG for a combination not
- * in the list, or mode LCS_STEP_STAGED_FIELD with the all-FP64 kernel.
+ * in the list or one that lcs_tune skips for this context (see there).
  * Synchronising. */
 lcs_status lcs_set_step_config(lcs_ctx *ctx, int block, int items, int mode);
 

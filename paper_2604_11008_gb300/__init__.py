@@ -24,8 +24,9 @@ LIB_PATH = os.path.join(_HERE, "_build", "liblcs.so")
 
 LCS_OK, LCS_ERR_ARG, LCS_ERR_CUDA, LCS_ERR_OOM, LCS_ERR_CAPACITY = 0, 1, 2, 3, 4
 LCS_ERR_TIMEOUT, LCS_ERR_NONFINITE, LCS_ERR_DISPLACEMENT, LCS_ERR_STATE = 5, 6, 7, 8
-LCS_TUNE_CONFIGS = 11  # step-kernel configurations lcs_tune tries
-STEP_PLAIN, STEP_STAGED_FIELD, STEP_PREFETCH, STEP_DEFERRED = 0, 1, 2, 3  # step-kernel modes
+LCS_TUNE_CONFIGS = 13  # step-kernel configurations lcs_tune tries
+# step-kernel modes
+STEP_PLAIN, STEP_STAGED_FIELD, STEP_PREFETCH, STEP_DEFERRED, STEP_OWNED_FIELD = 0, 1, 2, 3, 4
 STATUS_NAMES = {0: "LCS_OK", 1: "LCS_ERR_ARG", 2: "LCS_ERR_CUDA", 3: "LCS_ERR_OOM",
                 4: "LCS_ERR_CAPACITY", 5: "LCS_ERR_TIMEOUT", 6: "LCS_ERR_NONFINITE",
                 7: "LCS_ERR_DISPLACEMENT", 8: "LCS_ERR_STATE"}
@@ -58,7 +59,7 @@ class Desc(C.Structure):
                 ("track_images", C.c_int), ("ckpt_every", C.c_int), ("drag", C.c_int),
                 ("nu", C.c_double), ("density_ratio", C.c_double), ("field_next", C.c_void_p),
                 ("t_start", C.c_double), ("t_field", C.c_double * 2),
-                ("migrate_per_stage", C.c_int)]
+                ("migrate_per_stage", C.c_int), ("owned_field", C.c_int)]
 
 
 _lib = None
@@ -148,7 +149,7 @@ class Simulator:
                  sub=(1, 1, 1), box=2 * math.pi, field_dtype="f64", kernel="auto", ids=None,
                  sort_every=0, sort_brick=0, track_images=False, ckpt_every=0, stream=None,
                  ensembles=None, drag="stokes", nu=0.0, density_ratio=0.0, field_next=None,
-                 t_start=0.0, t_field=(0.0, 1.0), migrate_per_stage=False):
+                 t_start=0.0, t_field=(0.0, 1.0), migrate_per_stage=False, owned_field=False):
         import torch
         self._keep = []
         self._stream = stream
@@ -157,7 +158,8 @@ class Simulator:
             box=box, field_dtype=field_dtype, kernel=kernel, ids=ids, sort_every=sort_every,
             sort_brick=sort_brick, track_images=track_images, ckpt_every=ckpt_every,
             drag=drag, nu=nu, density_ratio=density_ratio, field_next=field_next,
-            t_start=t_start, t_field=t_field, migrate_per_stage=migrate_per_stage)]
+            t_start=t_start, t_field=t_field, migrate_per_stage=migrate_per_stage,
+            owned_field=owned_field)]
         descs = (Desc * len(specs))()
         self.meta = []
         for k, sp in enumerate(specs):
@@ -192,6 +194,7 @@ class Simulator:
             d.t_start = float(sp.get("t_start", 0.0))
             d.t_field[:] = [float(a) for a in sp.get("t_field", (0.0, 1.0))]
             d.migrate_per_stage = int(bool(sp.get("migrate_per_stage", False)))
+            d.owned_field = int(bool(sp.get("owned_field", False)))
             self.meta.append(dict(n=d.n, np=d.np, P=int(np.prod(d.sub[:])), has_tau=t is not None,
                                   tau_const=d.tau_const, box=d.box))
         self._ctx = C.c_void_p()

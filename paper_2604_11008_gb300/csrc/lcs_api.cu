@@ -49,6 +49,7 @@ struct Ens {
   int max_tiles = 0, max_stiles = 0, step_grid = 1;
   void *field = nullptr;
   void *field_b = nullptr;  // second snapshot (evolving field) or nullptr
+  void *bricks = nullptr;   // owned-field mode: the subdomains' field bricks
   double t_a = 0.0, t_b = 1.0;
   StepArgs a{};
   SortArgs s{};
@@ -81,6 +82,7 @@ struct lcs_ctx {
   bool pf_tau = false, pf_img = false;  // some ensemble has per-particle tau / images
   bool evolve = false;  // some ensemble has an evolving field (mode-3 kernels only)
   bool per_stage = false;  // migration after each Runge-Kutta stage (mode-3 kernels only)
+  bool owned = false;      // owned-field mode (mode-4 kernels only)
   int block = 256, items = 2;   // threads per block, particles per thread (set in setup_batch)
   int step_grid = 1, total_P = 0;
   int64_t total_tiles = 0;      // sum of the ensembles' look-back array sizes
@@ -442,11 +444,14 @@ lcs_status setup_batch(lcs_ctx *c) {
     c->evolve |= e.field_b != nullptr;
     if (e.d.migrate_per_stage != c->ens[0].d.migrate_per_stage)
       return fail(c, LCS_ERR_ARG, "all ensembles of a context need the same migration schedule");
+    if (e.d.owned_field != c->ens[0].d.owned_field)
+      return fail(c, LCS_ERR_ARG, "all ensembles of a context need the same owned_field");
   }
   c->per_stage = c->ens[0].d.migrate_per_stage != 0;
+  c->owned = c->ens[0].d.owned_field != 0;
   // default step kernel (lcs_tune / lcs_set_step_config change it): the
   // deferred scatter, one particle per thread for the FP64-field kernels
-  c->mode = LCS_STEP_DEFERRED;
+  c->mode = c->owned ? LCS_STEP_OWNED_FIELD : LCS_STEP_DEFERRED;
   c->block = 256;
   c->items = (c->kind == FK_DF || c->kind == FK_F64) ? 1 : 2;
   c->total_tiles = 0;
@@ -538,6 +543,12 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
       r = fail(c, LCS_ERR_ARG, "migrate_per_stage: not with field_next or ckpt_every");
       break;
     }
+    if (d.owned_field &&
+        (d.owned_field != 1 || d.field_next || d.ckpt_every > 0 ||
+         (d.field_dtype == LCS_F64 && d.field_kernel == LCS_KERNEL_FP64))) {
+      r = fail(c, LCS_ERR_ARG, "owned_field: not with LCS_KERNEL_FP64, field_next or ckpt_every");
+      break;
+    }
     switch (d.field_dtype) {
       case LCS_F64:
         e.kind = d.field_kernel == LCS_KERNEL_FP64 ? FK_F64 : FK_DF;
@@ -559,7 +570,7 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
     for (int s = 0; s < 3; ++s) {
       g.P[s] = d.sub[s];
       g.W[s] = d.n / d.sub[s];
-      g.Wrcp[s] = (unsigned)(((uint64_t(1) << 32) + g.W[s] - 1) / g.W[s]);
+      g.Wrcp[s] = g.W[s] > 1 ? (unsigned)(((uint64_t(1) << 32) + g.W[s] - 1) / g.W[s]) : 0u;
     }
     e.brick = d.sort_brick ? d.sort_brick : 8;
     int64_t space = (int64_t)e.brick * e.brick * e.brick;
@@ -638,10 +649,15 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
     const int64_t fbytes = e.kind == FK_BF16 ? 8 : e.kind == FK_F32 ? 16 : 32;
     A(dalloc(c, (char **)&e.field, ncell * fbytes));
     if (d.field_next) A(dalloc(c, (char **)&e.field_b, ncell * fbytes));
+    if (d.owned_field) {
+      const int64_t bcell = (int64_t)(g.W[0] + 4) * (g.W[1] + 4) * (g.W[2] + 4);
+      A(dalloc(c, (char **)&e.bricks, (int64_t)P * bcell * fbytes));
+    }
     A(dalloc(c, &m.nstep, 1));
     if (r != LCS_OK) break;
     e.a.field = e.field;
     e.a.field_b = e.field_b;
+    e.a.bricks = e.bricks;
     e.t_a = d.t_field[0];
     e.t_b = d.t_field[1];
     if (e.field_b) {
@@ -672,6 +688,7 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
     C2(cudaMemsetAsync(m.mig_tot, 0, sizeof(int64_t) * P, st));
     C2(launch_field_convert(d.field, d.n, e.kind, e.field, st));
     if (e.field_b) C2(launch_field_convert(d.field_next, d.n, e.kind, e.field_b, st));
+    if (e.bricks) C2(launch_build_bricks(e.field, e.a.geo, e.kind, e.bricks, st));
     C2(cudaMemsetAsync(m.nstep, 0, sizeof(int64_t), st));
     // particles -> buffer 1 compacted as one input segment, then migrate
     Rec &B1 = e.a.buf[1];
@@ -1027,18 +1044,31 @@ lcs_status lcs_profile_steps(lcs_ctx *c, int64_t nsteps, double *ms, int64_t *co
 }
 
 // Step-kernel configurations: (threads per block, particles per thread, kernel mode)
+// Whether a context may use a step-kernel configuration: no staged-field
+// form of the all-FP64 kernel; an evolving field or migration per stage only
+// with the deferred scatter (256 threads for migration per stage); an
+// owned-field context only with mode LCS_STEP_OWNED_FIELD, which no other
+// context uses.
+static bool step_config_allowed(const lcs_ctx *c, int block, int mode) {
+  if (mode == LCS_STEP_STAGED_FIELD && c->kind == FK_F64) return false;
+  const int deferred = c->owned ? LCS_STEP_OWNED_FIELD : LCS_STEP_DEFERRED;
+  if (c->owned != (mode == LCS_STEP_OWNED_FIELD)) return false;
+  if (c->evolve && mode != deferred) return false;
+  if (c->per_stage && (mode != deferred || block != 256)) return false;
+  return true;
+}
+
 static const int kStepConfigs[LCS_TUNE_CONFIGS][3] = {
     {256, 2, 0}, {256, 1, 0}, {128, 2, 0}, {256, 2, 1}, {128, 2, 1}, {256, 2, 2},
-    {128, 2, 2}, {256, 1, 2}, {256, 2, 3}, {128, 2, 3}, {256, 1, 3}};
+    {128, 2, 2}, {256, 1, 2}, {256, 2, 3}, {128, 2, 3}, {256, 1, 3}, {256, 1, 4},
+    {256, 2, 4}};
 
 lcs_status lcs_set_step_config(lcs_ctx *c, int block, int items, int mode) {
   lcs_status r = check_ctx(c);
   if (r != LCS_OK) return r;
   bool known = false;
   for (const auto &k : kStepConfigs) known |= k[0] == block && k[1] == items && k[2] == mode;
-  if (!known || (mode == LCS_STEP_STAGED_FIELD && c->kind == FK_F64) ||
-      (c->evolve && mode != LCS_STEP_DEFERRED) ||
-      (c->per_stage && (mode != LCS_STEP_DEFERRED || block != 256)))
+  if (!known || !step_config_allowed(c, block, mode))
     return reject(c, "lcs_set_step_config: configuration not available");
   CK(cudaStreamSynchronize(c->st));
   c->block = block;
@@ -1075,9 +1105,7 @@ lcs_status lcs_tune(lcs_ctx *c, int steps_per_trial, int *block, int *items, int
   int bi = 0;
   for (int k = 0; k < LCS_TUNE_CONFIGS; ++k) {
     if (trial_ms) trial_ms[k] = -1.0;
-    if (cfg[k][2] == LCS_STEP_STAGED_FIELD && c->kind == FK_F64) continue;  // no FP64 form
-    if (c->evolve && cfg[k][2] != LCS_STEP_DEFERRED) continue;  // no evolving-field form
-    if (c->per_stage && (cfg[k][2] != LCS_STEP_DEFERRED || cfg[k][0] != 256)) continue;
+    if (!step_config_allowed(c, cfg[k][0], cfg[k][2])) continue;
     c->block = cfg[k][0];
     c->items = cfg[k][1];
     c->mode = cfg[k][2];

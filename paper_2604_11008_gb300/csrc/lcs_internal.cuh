@@ -65,7 +65,7 @@ struct Geom {
   int N;
   int P[3];
   int W[3];        // N / P_s (cells per subdomain along s)
-  unsigned Wrcp[3];  // ceil(2^32 / W): c / W = umulhi(c, Wrcp) for 0 <= c < 2^11
+  unsigned Wrcp[3];  // ceil(2^32 / W): c / W = umulhi(c, Wrcp) for 0 <= c < 2^11, W >= 2
   int Ptot;
   double L;
   double inv_dx;   // N / L, one correctly rounded division on the host
@@ -117,6 +117,10 @@ struct StepArgs {
   // of step n's first stage, th = th0 + n dth (second stage th + dth)
   const void *field_b;
   double th0, dth;
+  // owned-field mode: the subdomains' own field bricks (W_s + 4 cells per
+  // axis: the subdomain's cells and a halo of two), subdomain s at cell
+  // s (W_x + 4)(W_y + 4)(W_z + 4); nullptr otherwise
+  const void *bricks;
 };
 
 // The ensembles of one context, as the batched kernels see them.
@@ -274,6 +278,8 @@ __device__ __forceinline__ void layout_from_counts(int P, int step_tile, const i
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_field_convert(const double *src, int N, FieldKind kind, void *dst,
                                  cudaStream_t st);
+cudaError_t launch_build_bricks(const void *field, const Geom &g, FieldKind kind, void *bricks,
+                                cudaStream_t st);
 // evolve: the evolving-field instantiation; stage: 0 whole step, 1/2 the
 // Runge-Kutta stages for migration per stage (both mode 3 only)
 template <int CAP>

@@ -108,6 +108,30 @@ __device__ __forceinline__ int box_base(const FieldBox &b, int i0, int j0, int k
   return (lk * b.ny + lj) * b.nx + li;
 }
 
+// Owned-field mode: a subdomain's own field brick in global memory, cells
+// [p W - 2, p W + W + 2) per axis (its W cells plus a halo of two, wrapped
+// into the periodic grid when the brick is built), x fastest, described by
+// a FieldBox whose s points to the brick.  Cell offset of stencil corner
+// (0,0,0), clamped into the brick so that every load stays inside it (a
+// stencil that does not fit is reported by brick_holds).
+__device__ __forceinline__ int brick_base(const FieldBox &b, int i0, int j0, int k0) {
+  const int li = min(max(i0 - b.ox, 0), b.nx - 2), lj = min(max(j0 - b.oy, 0), b.ny - 2),
+            lk = min(max(k0 - b.oz, 0), b.nz - 2);
+  return (lk * b.ny + lj) * b.nx + li;
+}
+
+// Whether the brick holds the whole stencil of fixed-point position q.
+__device__ __forceinline__ bool brick_holds(const FieldBox &b, const long long q[3]) {
+  bool ok = true;
+  const int o[3] = {b.ox, b.oy, b.oz}, n[3] = {b.nx, b.ny, b.nz};
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const int i0 = (int)((q[s] - (1ll << 51)) >> 52);
+    ok &= (unsigned)(i0 - o[s]) <= (unsigned)(n[s] - 2);
+  }
+  return ok;
+}
+
 // Fixed-point (52 fraction bits) coordinate x N/L of the first stage: one
 // correctly rounded FP64 product, then bit operations.
 __device__ __forceinline__ long long fix_stage1(double x, double inv_dx) {
@@ -147,10 +171,11 @@ __device__ __forceinline__ df mul_un(df a, df b) {
 // Corner weights are float-float products of the per-axis weights; each
 // weight-times-value product is split exactly (fma error), the high parts
 // are summed with two_sum and every small term goes to a compensation sum.
+template <bool OWNED = false>
 __device__ __forceinline__ void interp_df(const float4 *__restrict__ f, int N,
                                           const long long q[3], df U[3], const FieldBox &box) {
   const Axis ax = axis_from_fix(q[0]), ay = axis_from_fix(q[1]), az = axis_from_fix(q[2]);
-  const int sb = box_base(box, ax.i0, ay.i0, az.i0);
+  const int sb = OWNED ? brick_base(box, ax.i0, ay.i0, az.i0) : box_base(box, ax.i0, ay.i0, az.i0);
   const int i0 = wrap_cell(ax.i0, N), j0 = wrap_cell(ay.i0, N), k0 = wrap_cell(az.i0, N);
   const int i1 = i0 + 1 == N ? 0 : i0 + 1, j1 = j0 + 1 == N ? 0 : j0 + 1,
             k1 = k0 + 1 == N ? 0 : k0 + 1;
@@ -170,7 +195,9 @@ __device__ __forceinline__ void interp_df(const float4 *__restrict__ f, int N,
       for (int d = 0; d < 2; ++d) {
         const df w = mul_un(wab, wz[d]);
         float4 A, B;
-        if (sb >= 0) {
+        if (OWNED) {
+          ldg_cell32((const float4 *)box.s + 2 * (sb + a + box.nx * (b + box.ny * d)), A, B);
+        } else if (sb >= 0) {
           const float4 *sm = (const float4 *)box.s + 2 * (sb + a + box.nx * (b + box.ny * d));
           A = sm[0], B = sm[1];
         } else {
@@ -203,11 +230,11 @@ __device__ __forceinline__ void interp_df(const float4 *__restrict__ f, int N,
 
 // Trilinear interpolation (Sec. 2.2) for FP32 / BF16 field storage: weights
 // from the fixed-point coordinates rounded to FP32, FP32 accumulation.
-template <int KIND>
+template <int KIND, bool OWNED = false>
 __device__ __forceinline__ void interp_lo(const void *__restrict__ field, int N,
                                           const long long q[3], df U[3], const FieldBox &box) {
   const Axis ax = axis_from_fix(q[0]), ay = axis_from_fix(q[1]), az = axis_from_fix(q[2]);
-  const int sb = box_base(box, ax.i0, ay.i0, az.i0);
+  const int sb = OWNED ? brick_base(box, ax.i0, ay.i0, az.i0) : box_base(box, ax.i0, ay.i0, az.i0);
   const int i0 = wrap_cell(ax.i0, N), j0 = wrap_cell(ay.i0, N), k0 = wrap_cell(az.i0, N);
   const int i1 = i0 + 1 == N ? 0 : i0 + 1, j1 = j0 + 1 == N ? 0 : j0 + 1,
             k1 = k0 + 1 == N ? 0 : k0 + 1;
@@ -231,10 +258,14 @@ __device__ __forceinline__ void interp_lo(const void *__restrict__ field, int N,
         const int sc = sb + a + box.nx * (b + box.ny * d);
         float f[3];
         if (KIND == FK_F32) {
-          const float4 p = sb >= 0 ? ((const float4 *)box.s)[sc] : __ldg((const float4 *)field + cell);
+          const float4 p = OWNED     ? __ldg((const float4 *)box.s + sc)
+                           : sb >= 0 ? ((const float4 *)box.s)[sc]
+                                     : __ldg((const float4 *)field + cell);
           f[0] = p.x, f[1] = p.y, f[2] = p.z;
         } else {
-          const uint2 p = sb >= 0 ? ((const uint2 *)box.s)[sc] : __ldg((const uint2 *)field + cell);
+          const uint2 p = OWNED     ? __ldg((const uint2 *)box.s + sc)
+                          : sb >= 0 ? ((const uint2 *)box.s)[sc]
+                                    : __ldg((const uint2 *)field + cell);
           f[0] = __uint_as_float((p.x & 0xffffu) << 16);
           f[1] = __uint_as_float(p.x & 0xffff0000u);
           f[2] = __uint_as_float((p.y & 0xffffu) << 16);
@@ -247,11 +278,11 @@ __device__ __forceinline__ void interp_lo(const void *__restrict__ field, int N,
   for (int k = 0; k < 3; ++k) U[k] = {acc[k], 0.f};
 }
 
-template <int KIND>
+template <int KIND, bool OWNED = false>
 __device__ __forceinline__ void interp_any(const void *field, int N, const long long q[3],
                                            df U[3], const FieldBox &box) {
-  if (KIND == FK_DF) interp_df((const float4 *)field, N, q, U, box);
-  else interp_lo<KIND>(field, N, q, U, box);
+  if (KIND == FK_DF) interp_df<OWNED>((const float4 *)field, N, q, U, box);
+  else interp_lo<KIND, OWNED>(field, N, q, U, box);
 }
 
 // Drag factor of Eq. (7): f = 1 + 0.15 Re_p^0.687 with Re_p^2 = c tau |D|^2,
@@ -333,7 +364,7 @@ __device__ __forceinline__ void lerp_field_lo(const StepArgs &a, const long long
 //   [= dt (V + V*)/2], with f = 1 (Stokes) or the factor of Eq. (7);
 // then q' = q + (N/L) dX in fixed point (exact addition), V' = V + dV in
 // float-float, and the periodic wrap.  No FP64 instruction on the Stokes path.
-template <int KIND, bool EVOLVE = false>
+template <int KIND, bool EVOLVE = false, bool OWNED = false>
 __device__ __forceinline__ void heun_step_df(const StepArgs &a, long long q[3], df V[3],
                                              double tau, int img[3], int &bad,
                                              const FieldBox &box = FieldBox{},
@@ -344,7 +375,8 @@ __device__ __forceinline__ void heun_step_df(const StepArgs &a, long long q[3], 
   const df h = df_mul(dt, df_recip(split_d(tau)));
   long long q2[3];
   df U[3], hD1[3], Vs[3], D[3];
-  interp_any<KIND>(a.field, g.N, q, U, box);
+  if (OWNED && !brick_holds(box, q)) bad |= 2;
+  interp_any<KIND, OWNED>(a.field, g.N, q, U, box);
   if (EVOLVE && a.field_b) lerp_field_df<KIND>(a, q, tt.th1, U);
 #pragma unroll
   for (int s = 0; s < 3; ++s) D[s] = df_add(U[s], df_neg(V[s]));
@@ -356,7 +388,8 @@ __device__ __forceinline__ void heun_step_df(const StepArgs &a, long long q[3], 
     Vs[s] = df_add(df_add(V[s], hD1[s]), gd);
     q2[s] = fix_stage2(q[s], V[s], cx);
   }
-  interp_any<KIND>(a.field, g.N, q2, U, box);
+  if (OWNED && !brick_holds(box, q2)) bad |= 2;
+  interp_any<KIND, OWNED>(a.field, g.N, q2, U, box);
   if (EVOLVE && a.field_b) lerp_field_df<KIND>(a, q2, tt.th2, U);
 #pragma unroll
   for (int s = 0; s < 3; ++s) D[s] = df_add(U[s], df_neg(Vs[s]));
@@ -381,7 +414,7 @@ __device__ __forceinline__ void heun_step_df(const StepArgs &a, long long q[3], 
 // formulas as heun_step_df with the increments in FP32 (the field itself
 // carries 2^-24 or 2^-8 relative error), accumulated exactly into the
 // fixed-point position and in float-float into the velocity.
-template <int KIND, bool EVOLVE = false>
+template <int KIND, bool EVOLVE = false, bool OWNED = false>
 __device__ __forceinline__ void heun_step_lo(const StepArgs &a, long long q[3], df V[3],
                                              double tau, int img[3], int &bad,
                                              const FieldBox &box = FieldBox{},
@@ -393,7 +426,8 @@ __device__ __forceinline__ void heun_step_lo(const StepArgs &a, long long q[3], 
   long long q2[3];
   df U[3];
   float hD1[3], Vs[3], D[3];
-  interp_lo<KIND>(a.field, g.N, q, U, box);
+  if (OWNED && !brick_holds(box, q)) bad |= 2;
+  interp_lo<KIND, OWNED>(a.field, g.N, q, U, box);
   if (EVOLVE && a.field_b) lerp_field_lo<KIND>(a, q, (float)tt.th1, U);
 #pragma unroll
   for (int s = 0; s < 3; ++s) D[s] = U[s].h - V[s].h;
@@ -405,7 +439,8 @@ __device__ __forceinline__ void heun_step_lo(const StepArgs &a, long long q[3], 
     Vs[s] = V[s].h + hD1[s] + gd;
     q2[s] = fix_stage2_lo(q[s], V[s].h, cx);
   }
-  interp_lo<KIND>(a.field, g.N, q2, U, box);
+  if (OWNED && !brick_holds(box, q2)) bad |= 2;
+  interp_lo<KIND, OWNED>(a.field, g.N, q2, U, box);
   if (EVOLVE && a.field_b) lerp_field_lo<KIND>(a, q2, (float)tt.th2, U);
 #pragma unroll
   for (int s = 0; s < 3; ++s) D[s] = U[s].h - Vs[s];
@@ -434,14 +469,16 @@ __device__ __forceinline__ void heun_step_lo(const StepArgs &a, long long q[3], 
 //   X' = X* + (dt/2)(V* - V)          [= X + (dt/2)(V + V*)]
 //   V' = (V + V* + h2 D2 + dt g) / 2  [= V + (dt/2)(A1 + A2), dt A1 = V* - V]
 // with D2 = U(X*) - V*.  Same arithmetic pieces as the fused step.
-template <int KIND>
+template <int KIND, bool OWNED = false>
 __device__ __forceinline__ void heun_stage1_df(const StepArgs &a, long long q[3], const df V[3],
-                                               df Vs[3], double tau, int img[3], int &bad) {
+                                               df Vs[3], double tau, int img[3], int &bad,
+                                               const FieldBox &box = FieldBox{}) {
   const Geom &g = a.geo;
   const df dt = {a.dfk[0], a.dfk[1]}, cx = {a.dfk[4], a.dfk[5]};
   const df h = df_mul(dt, df_recip(split_d(tau)));
   df U[3], D[3];
-  interp_any<KIND>(a.field, g.N, q, U, FieldBox{});
+  if (OWNED && !brick_holds(box, q)) bad |= 2;
+  interp_any<KIND, OWNED>(a.field, g.N, q, U, box);
 #pragma unroll
   for (int s = 0; s < 3; ++s) D[s] = df_add(U[s], df_neg(V[s]));
   const df h1 = a.drag ? df_mul(h, drag_factor_df(a.drag_c, tau, D)) : h;
@@ -457,16 +494,18 @@ __device__ __forceinline__ void heun_stage1_df(const StepArgs &a, long long q[3]
   }
 }
 
-template <int KIND>
+template <int KIND, bool OWNED = false>
 __device__ __forceinline__ void heun_stage2_df(const StepArgs &a, long long q[3], df V[3],
                                                const df Vs[3], double tau, int img[3],
-                                               int &bad) {
+                                               int &bad,
+                                               const FieldBox &box = FieldBox{}) {
   const Geom &g = a.geo;
   const df dt = {a.dfk[0], a.dfk[1]}, cx = {a.dfk[4], a.dfk[5]};
   const df hcx = df_scale2(cx, 0.5f);
   const df h = df_mul(dt, df_recip(split_d(tau)));
   df U[3], D[3];
-  interp_any<KIND>(a.field, g.N, q, U, FieldBox{});
+  if (OWNED && !brick_holds(box, q)) bad |= 2;
+  interp_any<KIND, OWNED>(a.field, g.N, q, U, box);
 #pragma unroll
   for (int s = 0; s < 3; ++s) D[s] = df_add(U[s], df_neg(Vs[s]));
   const df h2 = a.drag ? df_mul(h, drag_factor_df(a.drag_c, tau, D)) : h;
@@ -484,16 +523,18 @@ __device__ __forceinline__ void heun_stage2_df(const StepArgs &a, long long q[3]
   }
 }
 
-template <int KIND>
+template <int KIND, bool OWNED = false>
 __device__ __forceinline__ void heun_stage1_lo(const StepArgs &a, long long q[3], const df V[3],
-                                               df Vs[3], double tau, int img[3], int &bad) {
+                                               df Vs[3], double tau, int img[3], int &bad,
+                                               const FieldBox &box = FieldBox{}) {
   const Geom &g = a.geo;
   const float dt = a.dfk[0], cx = a.dfk[4];
   const float taus = split_d(tau).h;
   const float h = dt * __frcp_rn(taus);
   df U[3];
   float D[3];
-  interp_lo<KIND>(a.field, g.N, q, U, FieldBox{});
+  if (OWNED && !brick_holds(box, q)) bad |= 2;
+  interp_lo<KIND, OWNED>(a.field, g.N, q, U, box);
 #pragma unroll
   for (int s = 0; s < 3; ++s) D[s] = U[s].h - V[s].h;
   const float h1 = a.drag ? h * drag_factor_f32((float)a.drag_c, taus, D) : h;
@@ -508,17 +549,19 @@ __device__ __forceinline__ void heun_stage1_lo(const StepArgs &a, long long q[3]
   }
 }
 
-template <int KIND>
+template <int KIND, bool OWNED = false>
 __device__ __forceinline__ void heun_stage2_lo(const StepArgs &a, long long q[3], df V[3],
                                                const df Vs[3], double tau, int img[3],
-                                               int &bad) {
+                                               int &bad,
+                                               const FieldBox &box = FieldBox{}) {
   const Geom &g = a.geo;
   const float dt = a.dfk[0], cx = a.dfk[4];
   const float taus = split_d(tau).h;
   const float h = dt * __frcp_rn(taus);
   df U[3];
   float D[3];
-  interp_lo<KIND>(a.field, g.N, q, U, FieldBox{});
+  if (OWNED && !brick_holds(box, q)) bad |= 2;
+  interp_lo<KIND, OWNED>(a.field, g.N, q, U, box);
 #pragma unroll
   for (int s = 0; s < 3; ++s) D[s] = U[s].h - Vs[s].h;
   const float h2 = a.drag ? h * drag_factor_f32((float)a.drag_c, taus, D) : h;

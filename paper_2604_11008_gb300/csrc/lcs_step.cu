@@ -107,6 +107,48 @@ cudaError_t launch_field_convert(const double *src, int N, FieldKind kind, void 
   return cudaGetLastError();
 }
 
+// Owned-field bricks (the memory pattern of the multi-GPU decomposition):
+// brick p holds, x fastest, the converted field cells p_s W_s - 2 ..
+// p_s W_s + W_s + 1 along each axis s, wrapped into the periodic grid, so
+// that its subdomain's stencils -- with the predictor up to one cell
+// outside -- never leave it.  Subdomain p = p_x + P_x (p_y + P_y p_z).
+__global__ void k_build_bricks(const unsigned char *field, Geom g, int cb, unsigned char *bricks) {
+  const int bx = g.W[0] + 4, by = g.W[1] + 4, bz = g.W[2] + 4;
+  const int64_t per = (int64_t)bx * by * bz, total = per * g.Ptot;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int p = (int)(i / per);
+    const int64_t r = i - (int64_t)p * per;
+    const int lx = (int)(r % bx), ly = (int)((r / bx) % by), lz = (int)(r / ((int64_t)bx * by));
+    const int pc[3] = {p % g.P[0], (p / g.P[0]) % g.P[1], p / (g.P[0] * g.P[1])};
+    const int l[3] = {lx, ly, lz};
+    int gc[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      int c = pc[s] * g.W[s] - 2 + l[s];  // -2 .. N + 1
+      c += c < 0 ? g.N : 0;
+      c -= c >= g.N ? g.N : 0;
+      gc[s] = c;
+    }
+    const int64_t src = ((int64_t)gc[2] * g.N + gc[1]) * g.N + gc[0];
+    if (cb == 8) {
+      ((uint2 *)bricks)[i] = ((const uint2 *)field)[src];
+    } else {
+      for (int k = 0; k < cb / 16; ++k)
+        ((uint4 *)bricks)[i * (cb / 16) + k] = ((const uint4 *)field)[src * (cb / 16) + k];
+    }
+  }
+}
+
+cudaError_t launch_build_bricks(const void *field, const Geom &g, FieldKind kind, void *bricks,
+                                cudaStream_t st) {
+  const int64_t total = (int64_t)(g.W[0] + 4) * (g.W[1] + 4) * (g.W[2] + 4) * g.Ptot;
+  const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
+  k_build_bricks<<<std::max(grid, 1), 256, 0, st>>>((const unsigned char *)field, g,
+                                                    cell_bytes(kind), (unsigned char *)bricks);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_field_expand(const void *src, int N, FieldKind kind, double *dst,
                                 cudaStream_t st) {
   const int64_t ncell = (int64_t)N * N * N;

@@ -133,7 +133,9 @@ __device__ __forceinline__ int dest_bin(const Geom &g, const int ps[3], const lo
     // the containing cell: integer part of the fixed-point coordinate
     int c = (int)(x[s] >> 52);
     c = min(max(c, 0), g.N - 1);
-    const int dc = dir_comp(ps[s], (int)__umulhi((unsigned)c, g.Wrcp[s]), g.P[s]);
+    // c / W by the reciprocal; W = 1 (one cell per subdomain) has none in 32 bits
+    const int pc = g.W[s] == 1 ? c : (int)__umulhi((unsigned)c, g.Wrcp[s]);
+    const int dc = dir_comp(ps[s], pc, g.P[s]);
     if (dc == 2) return -1;
     bin += (dc + 1) * mul;
     mul *= 3;
@@ -515,7 +517,18 @@ __device__ __forceinline__ void park_get(const unsigned char *pk, bool lay_tau, 
 // packed (stay << 16 | leave) count and the block's direction histogram.
 // STAGE 0: the whole Heun step; 1: the predictor stage (x becomes X*, vs
 // receives V*); 2: the corrector stage (reads vs).
-template <int KIND, int ITEMS, bool EVOLVE, int STAGE>
+// The owned-field view of a tile's subdomain (owned-field mode): its brick,
+// whose cell (0, 0, 0) is global cell p W - 2 per axis.
+template <int KIND>
+__device__ __forceinline__ FieldBox owned_view(const StepArgs &a, const TileMeta &mt) {
+  const int bx = a.geo.W[0] + 4, by = a.geo.W[1] + 4, bz = a.geo.W[2] + 4;
+  return FieldBox{(const unsigned char *)a.bricks +
+                      (size_t)mt.seg * bx * by * bz * cell_bytes(KIND),
+                  mt.ps[0] * a.geo.W[0] - 2, mt.ps[1] * a.geo.W[1] - 2,
+                  mt.ps[2] * a.geo.W[2] - 2, bx, by, bz};
+}
+
+template <int KIND, int ITEMS, bool EVOLVE, int STAGE, bool OWNED = false>
 __device__ __forceinline__ unsigned integrate_items(const StepArgs &a, const TileMeta &mt,
                                                     BlockShared &sh, long long x[][3],
                                                     df v[][3], double tau[], uint32_t id[],
@@ -525,6 +538,7 @@ __device__ __forceinline__ unsigned integrate_items(const StepArgs &a, const Til
   unsigned packed = 0;
   int bad = 0;
   const StageTimes tt = EVOLVE ? stage_times(a) : StageTimes{0.0, 0.0};
+  const FieldBox fv = OWNED ? owned_view<KIND>(a, mt) : FieldBox{};
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k) {
     bin[k] = -2;
@@ -533,19 +547,21 @@ __device__ __forceinline__ unsigned integrate_items(const StepArgs &a, const Til
       if (STAGE == 0) {
         if (KIND == FK_F64) heun_step64<EVOLVE>(a, x[k], v[k], tau[k], img[k], bad, tt);
         else if (KIND == FK_DF)
-          heun_step_df<KIND, EVOLVE>(a, x[k], v[k], tau[k], img[k], bad, FieldBox{}, tt);
-        else heun_step_lo<KIND, EVOLVE>(a, x[k], v[k], tau[k], img[k], bad, FieldBox{}, tt);
+          heun_step_df<KIND, EVOLVE, OWNED>(a, x[k], v[k], tau[k], img[k], bad, fv, tt);
+        else heun_step_lo<KIND, EVOLVE, OWNED>(a, x[k], v[k], tau[k], img[k], bad, fv, tt);
       } else if (STAGE == 1) {
         if (KIND == FK_F64) heun_stage1_64(a, x[k], v[k], vs[k], tau[k], img[k], bad);
-        else if (KIND == FK_DF) heun_stage1_df<KIND>(a, x[k], v[k], vs[k], tau[k], img[k], bad);
-        else heun_stage1_lo<KIND>(a, x[k], v[k], vs[k], tau[k], img[k], bad);
+        else if (KIND == FK_DF)
+          heun_stage1_df<KIND, OWNED>(a, x[k], v[k], vs[k], tau[k], img[k], bad, fv);
+        else heun_stage1_lo<KIND, OWNED>(a, x[k], v[k], vs[k], tau[k], img[k], bad, fv);
       } else {
         const int64_t i = mt.bA + l0 + k;
 #pragma unroll
         for (int s = 0; s < 3; ++s) vs[k][s] = df_from2(A.vs[s][i]);
         if (KIND == FK_F64) heun_stage2_64(a, x[k], v[k], vs[k], tau[k], img[k], bad);
-        else if (KIND == FK_DF) heun_stage2_df<KIND>(a, x[k], v[k], vs[k], tau[k], img[k], bad);
-        else heun_stage2_lo<KIND>(a, x[k], v[k], vs[k], tau[k], img[k], bad);
+        else if (KIND == FK_DF)
+          heun_stage2_df<KIND, OWNED>(a, x[k], v[k], vs[k], tau[k], img[k], bad, fv);
+        else heun_stage2_lo<KIND, OWNED>(a, x[k], v[k], vs[k], tau[k], img[k], bad, fv);
       }
       int b = dest_bin(a.geo, mt.ps, x[k]);
       if (b < 0) {
@@ -572,7 +588,7 @@ __device__ __forceinline__ unsigned integrate_items(const StepArgs &a, const Til
 // not stall the block.  The parked tile is then written out with coalesced
 // stores: its stayers form one contiguous run of the output window and its
 // leavers one contiguous run of the pack buffer.
-template <int KIND, int BLOCK, int ITEMS, int CAP, bool EVOLVE, int STAGE>
+template <int KIND, int BLOCK, int ITEMS, int CAP, bool EVOLVE, int STAGE, bool OWNED>
 __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockShared &sh,
                                               const int *s_off, unsigned char *pk) {
   constexpr int T = BLOCK * ITEMS;
@@ -599,8 +615,8 @@ __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockSha
     if (fresh) {
       const int e = CAP == 1 ? 0 : find_ensemble(s_off, n, g);
       m = tile_meta<T>(pb.a[e], g, e, g - s_off[e]);
-      packed = integrate_items<KIND, ITEMS, EVOLVE, STAGE>(pb.a[e], m, sh, x, v, tau, id, img,
-                                                           bin, vs);
+      packed = integrate_items<KIND, ITEMS, EVOLVE, STAGE, OWNED>(pb.a[e], m, sh, x, v, tau, id,
+                                                                  img, bin, vs);
     }
     if (parked) {
       const TileMeta pm = s_park;
@@ -717,9 +733,10 @@ __global__ void __launch_bounds__(BLOCK, (step_min_blocks<KIND, BLOCK, ITEMS>())
     }
     s_off[n] = acc;
   }
-  if (MODE == 3) {
+  if (MODE == 3 || MODE == 4) {
     __syncthreads();
-    step_deferred<KIND, BLOCK, ITEMS, CAP, EVOLVE, STAGE>(pb, sh, s_off, s_dyn);
+    step_deferred<KIND, BLOCK, ITEMS, CAP, EVOLVE, STAGE, MODE == 4 && KIND != FK_F64>(pb, sh,
+                                                                                    s_off, s_dyn);
     return;
   }
   if (MODE != 2) {
@@ -782,18 +799,22 @@ __global__ void __launch_bounds__(BLOCK, (step_min_blocks<KIND, BLOCK, ITEMS>())
 // tuner tries; mode 1 (staged field box) has no all-FP64 form
 // The last two arguments: evolving-field instantiation, Runge-Kutta stage
 // (0: whole step; 1, 2: migration per stage); both exist in mode 3 only.
+// Mode 4 is mode 3 reading the owned-field bricks (no all-FP64 form).
 #define LCS_STEP_CONFIGS(X, K, C)                                                   \
   X(K, 0, 256, 2, C, 0, 0) X(K, 0, 256, 1, C, 0, 0) X(K, 0, 128, 2, C, 0, 0)       \
   X(K, 1, 256, 2, C, 0, 0) X(K, 1, 128, 2, C, 0, 0) X(K, 2, 256, 2, C, 0, 0)       \
   X(K, 2, 128, 2, C, 0, 0) X(K, 2, 256, 1, C, 0, 0) X(K, 3, 256, 2, C, 0, 0)       \
   X(K, 3, 128, 2, C, 0, 0) X(K, 3, 256, 1, C, 0, 0) X(K, 3, 256, 2, C, 1, 0)       \
   X(K, 3, 128, 2, C, 1, 0) X(K, 3, 256, 1, C, 1, 0) X(K, 3, 256, 2, C, 0, 1)       \
-  X(K, 3, 256, 2, C, 0, 2) X(K, 3, 256, 1, C, 0, 1) X(K, 3, 256, 1, C, 0, 2)
+  X(K, 3, 256, 2, C, 0, 2) X(K, 3, 256, 1, C, 0, 1) X(K, 3, 256, 1, C, 0, 2)       \
+  X(K, 4, 256, 1, C, 0, 0) X(K, 4, 256, 2, C, 0, 0) X(K, 4, 256, 1, C, 0, 1)       \
+  X(K, 4, 256, 1, C, 0, 2) X(K, 4, 256, 2, C, 0, 1) X(K, 4, 256, 2, C, 0, 2)
 
 // Dynamic shared memory of a configuration: the staged field box (mode 1),
-// the two record buffers (mode 2) or the parked tile (mode 3).
+// the two record buffers (mode 2) or the parked tile (modes 3 and 4).
 constexpr int step_dyn_smem(int kind, int mode, int tile, bool tau, bool img, bool vs = false) {
-  return mode == 3 && vs ? step_dyn_smem(kind, 3, tile, tau, img) + 3 * tile * 8
+  return mode == 4 ? step_dyn_smem(kind, 3, tile, tau, img, vs)
+         : mode == 3 && vs ? step_dyn_smem(kind, 3, tile, tau, img) + 3 * tile * 8
          : mode == 1 ? (kind != FK_F64 ? STAGE_BYTES : 0)
          : mode == 2 ? 2 * ((6 + (tau ? 1 : 0)) * (tile + 2) * 8 +
                             (1 + (img ? 3 : 0)) * (tile + 4) * 4)
@@ -808,7 +829,7 @@ cudaError_t launch_step_kind(const StepGroup<CAP> &pb, int mode, int block, int 
                              bool evolve, int stage, int grid, cudaStream_t st) {
 #define LCS_LAUNCH(K, M, B, I, C, E, S)                                                    \
   if (mode == M && block == B && items == I && evolve == (E != 0) && stage == S &&        \
-      !(M == 1 && K == FK_F64)) {                                                          \
+      !((M == 1 || M == 4) && K == FK_F64)) {                                              \
     static_assert(PfLayout<B * I>::bytes(true, true) ==                                    \
                       step_dyn_smem(K, 2, B * I, true, true) / 2, "layout");               \
     static_assert(ParkLayout<B * I>::bytes(true, false) ==                                 \
@@ -831,7 +852,7 @@ int step_occupancy_kind(int mode, int block, int items, bool evolve, int stage, 
   int n = 0;
 #define LCS_OCC(K, M, B, I, C, E, S)                                                       \
   if (mode == M && block == B && items == I && evolve == (E != 0) && stage == S &&        \
-      !(M == 1 && K == FK_F64)) {                                                          \
+      !((M == 1 || M == 4) && K == FK_F64)) {                                              \
     auto ker = k_step_block<K, B, I, C, M, (E != 0), S>;                                   \
     const int smem = step_dyn_smem(K, M, B * I, pf_tau, pf_img, pf_vs);                    \
     if (smem) cudaFuncSetAttribute(ker, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \

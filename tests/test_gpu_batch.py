@@ -84,11 +84,12 @@ def test_tune_keeps_results(lcs):
     a = lcs.Simulator(None, None, None, None, ensembles=sp)
     b = lcs.Simulator(None, None, None, None, ensembles=sp)
     a.step(22)
-    cfg = b.tune(2)   # 11 configurations x 2 steps
+    cfg = b.tune(2)   # 11 configurations x 2 steps (the owned-field mode is skipped)
     assert cfg in ((256, 2, 0), (256, 1, 0), (128, 2, 0), (256, 2, 1), (128, 2, 1),
                    (256, 2, 2), (128, 2, 2), (256, 1, 2), (256, 2, 3), (128, 2, 3),
                    (256, 1, 3))
-    assert (b.tune_trials_ms > 0).all()
+    assert (b.tune_trials_ms[:11] > 0).all()
+    assert (b.tune_trials_ms[11:] == -1).all()
     for k in range(len(sp)):
         sa, sb = gpu_state(a, k), gpu_state(b, k)
         for key in ("seg", "ids", "x", "v"):

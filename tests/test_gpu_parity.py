@@ -159,8 +159,9 @@ def one_step_identical_inputs(lcs, N, P, n, tau_median, g, seed, dt=0.01, steps_
 @pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("N,P,n", [(16, (2, 2, 2), 5000), (24, (3, 3, 3), 30011),
                                    (32, (4, 2, 1), 70000), (16, (1, 1, 1), 1500),
-                                   (20, (5, 1, 2), 12345)])
+                                   (20, (5, 1, 2), 12345), (12, (12, 4, 1), 6000)])
 def test_one_step_identical_inputs(lcs, N, P, n, kernel):
+    # (12, (12, 4, 1)): subdomains one cell wide along x
     moved = one_step_identical_inputs(lcs, N, P, n, 0.05, (0.0, 0.0, -9.8), seed=40 + n, dt=0.02,
                                       kernel=kernel)
     if int(np.prod(P)) > 1:
