@@ -58,6 +58,7 @@ def test_sampled_trajectories_against_oracle(final):
     d -= L * np.round(d / L)           # the same point modulo the period
     ex = np.linalg.norm(d) / np.linalg.norm(xs + L * img - x[:, sample])
     ev = np.linalg.norm(st["v"][:, at] - vs) / np.linalg.norm(vs)
+    print(f"scale_256 FP64 field: e_x {ex:.3e}  e_v {ev:.3e}")
     assert ex < 1e-12 and ev < 1e-12, (ex, ev)
 
 
