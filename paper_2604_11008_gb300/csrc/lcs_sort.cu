@@ -119,23 +119,39 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_scan_down(SortArgs s, int D) {
 
 // ---------------------------------------------------------------- stable scatter
 
+// Stable scatter of one digit pass.  Each tile ranks its keys by digit with
+// warp match masks in input order (rank among the equal digits of the warp's
+// earlier rounds), turns the per-(warp, digit) counts into tile-local digit
+// offsets, places every key at its tile-local sorted position in shared
+// memory, and then writes the tile out in that order: consecutive threads
+// write consecutive slots of one digit's output run, so the stores are
+// coalesced instead of landing in one digit bucket per lane.  Output slot =
+// the tile's global offset for the digit (hist_scan) + the key's rank among
+// the tile's keys of that digit, the same slot as a direct scatter.
 template <int MAXD>
-__global__ void __launch_bounds__(SORT_BLOCK) k_downsweep(SortArgs s, const uint32_t *kin,
+__global__ void __launch_bounds__(SORT_BLOCK, 3) k_downsweep(SortArgs s, const uint32_t *kin,
                                                           const uint32_t *pin, uint32_t *kout,
                                                           uint32_t *pout, int shift, int D) {
-  __shared__ int wc[SORT_BLOCK / 32][MAXD];
-  __shared__ int base[MAXD];
+  constexpr int NW = SORT_BLOCK / 32;
+  // per-(warp, digit) counts, then the staged tile (keys, payloads)
+  __shared__ uint32_t pool[2 * SORT_TILE > NW * MAXD ? 2 * SORT_TILE : NW * MAXD];
+  __shared__ int64_t base[MAXD];  // output slot of the tile's first key of each digit
+  __shared__ int toff[MAXD];      // tile-local offset of each digit
+  __shared__ int s_part[SORT_BLOCK / 32];
+  int(*wc)[MAXD] = reinterpret_cast<int(*)[MAXD]>(pool);
+  uint32_t *sk = pool, *sp = pool + SORT_TILE;
   const int total = s.tile_off[s.nseg];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1;
-  constexpr int PER_WARP = SORT_TILE / (SORT_BLOCK / 32);  // 512
+  constexpr int PER_WARP = SORT_TILE / NW;  // 512
   const int64_t n_all = s.cstart[s.nseg];
   for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
     const int seg = find_segment(s.tile_off, s.nseg, tile);
     const int t0 = s.tile_off[seg], nt = s.tile_off[seg + 1] - t0, jt = tile - t0;
     const int64_t a = s.cstart[seg] + (int64_t)jt * SORT_TILE;
     const int64_t e = min(s.cstart[seg + 1], a + SORT_TILE);
-    for (int i = threadIdx.x; i < (SORT_BLOCK / 32) * MAXD; i += blockDim.x) (&wc[0][0])[i] = 0;
+    const int ntile = (int)(e - a);
+    for (int i = threadIdx.x; i < NW * MAXD; i += blockDim.x) (&wc[0][0])[i] = 0;
     for (int d = threadIdx.x; d < D; d += blockDim.x)
       base[d] = s.hist_scan[(int64_t)t0 * D + (int64_t)d * nt + jt];
     __syncthreads();
@@ -157,26 +173,69 @@ __global__ void __launch_bounds__(SORT_BLOCK) k_downsweep(SortArgs s, const uint
       rk[r] = valid ? b + rank : -1;
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < D; d += blockDim.x) {
-      int run = base[d];
-      for (int w = 0; w < SORT_BLOCK / 32; ++w) {
-        const int t = wc[w][d];
-        wc[w][d] = run;
-        run += t;
+    // per digit: exclusive offsets over the warps, and the digit's tile count
+    int cnt[(MAXD + SORT_BLOCK - 1) / SORT_BLOCK];
+#pragma unroll
+    for (int q = 0; q < (MAXD + SORT_BLOCK - 1) / SORT_BLOCK; ++q) {
+      const int d = threadIdx.x + q * SORT_BLOCK;
+      int run = 0;
+      if (d < D) {
+        for (int w = 0; w < NW; ++w) {
+          const int t = wc[w][d];
+          wc[w][d] = run;
+          run += t;
+        }
       }
+      cnt[q] = run;
     }
-    __syncthreads();
+    // tile-local digit offsets: exclusive scan of the counts over the digits
+    // (digit d = threadIdx.x + q * SORT_BLOCK, scanned q-major)
+    int carry = 0;
+#pragma unroll
+    for (int q = 0; q < (MAXD + SORT_BLOCK - 1) / SORT_BLOCK; ++q) {
+      int inc = cnt[q];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+      }
+      if (lane == 31) s_part[warp] = inc;
+      __syncthreads();
+      int wbase = 0, tot = 0;
+      for (int w = 0; w < NW; ++w) {
+        const int t = s_part[w];
+        wbase += w < warp ? t : 0;
+        tot += t;
+      }
+      const int d = threadIdx.x + q * SORT_BLOCK;
+      if (d < MAXD) toff[d] = carry + wbase + inc - cnt[q];
+      carry += tot;
+      __syncthreads();
+    }
+    // tile-local sorted position of every key (in place of its rank), then stage
+#pragma unroll
+    for (int r = 0; r < SORT_ITEMS; ++r) {
+      const int dg = (int)((k[r] >> shift) & (D - 1));
+      if (rk[r] >= 0) rk[r] += toff[dg] + wc[warp][dg];
+    }
+    __syncthreads();  // every read of the counts is done before they are overwritten
 #pragma unroll
     for (int r = 0; r < SORT_ITEMS; ++r) {
       if (rk[r] < 0) continue;
-      const int dg = (int)((k[r] >> shift) & (D - 1));
-      const int64_t pos = (int64_t)wc[warp][dg] + rk[r];
+      sk[rk[r]] = k[r];
+      sp[rk[r]] = p[r];
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < ntile; j += blockDim.x) {
+      const uint32_t key = sk[j];
+      const int dg = (int)((key >> shift) & (D - 1));
+      const int64_t pos = base[dg] + (j - toff[dg]);
       if (pos < 0 || pos >= n_all) {  // inconsistent histogram: report, never write
         if (s.status) latch(s.status, LCS_ERR_STATE);
         continue;
       }
-      kout[pos] = k[r];
-      pout[pos] = p[r];
+      kout[pos] = key;
+      pout[pos] = sp[j];
     }
     __syncthreads();
   }
