@@ -1,0 +1,76 @@
+"""The batching workload at full size, as bench.py runs it (needs a GPU).
+
+48 independent ensembles, grids drawn from {64, 96, 128, 256}^3, 10^4-10^7
+particles each (30.6 M in all), tau uniform in [0.01, 1], FP32 field
+storage, 2x2x2 subdomains each, cell sort every 10 steps, 500 steps, all in
+one context (one persistent step-kernel launch per step for all ensembles,
+autotuned).  Ensembles and particles do not interact, so up to 300 sampled
+particles of every ensemble are checked against the FP64 oracle run on them
+alone on the FP64 field (norm-wise over each ensemble's sample, within the
+FP32-storage bar of 1e-5), and every ensemble keeps its id multiset and puts
+each particle in its subdomain's segment.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import L, gpu_state
+
+pytestmark = pytest.mark.gpu
+
+STEPS = 500
+
+
+@pytest.fixture(scope="module")
+def batch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2604_11008_gb300 as lcs
+    from paper_2604_11008_gb300 import build
+    build.build()
+    ens = synth.batch_ensembles(48, device="cuda")
+    specs = [dict(field=e["field"], x0=e["x0"], v0=e["v0"], dt=e["dt"], tau=e["tau"],
+                  sub=(2, 2, 2), sort_every=10, field_dtype="f32") for e in ens]
+    sim = lcs.Simulator(None, None, None, None, ensembles=specs)
+    sim.tune(2)                        # advances 2 steps per tried configuration
+    done = 2 * int((sim.tune_trials_ms > 0).sum())
+    sim.step(STEPS - done)
+    states = [gpu_state(sim, k) for k in range(len(ens))]
+    sim.close()
+    return ens, states
+
+
+def test_sampled_trajectories_of_every_ensemble(batch):
+    ens, states = batch
+    worst = 0.0
+    for k, (e, st) in enumerate(zip(ens, states)):
+        n = e["n"]
+        rng = np.random.default_rng(480 + k)
+        sample = np.sort(rng.choice(n, min(n, 300), replace=False))
+        xs, vs, ts = e["x0"][:, sample].copy(), e["v0"][:, sample].copy(), e["tau"][sample].copy()
+        img = np.zeros((3, len(sample)), np.int32)
+        oracle.advance(e["field"].cpu().numpy(), L, xs, vs, ts, 0.0, e["dt"], (0.0, 0.0, 0.0),
+                       STEPS, img=img)
+        pos = np.empty(n, np.int64)
+        pos[st["ids"].astype(np.int64)] = np.arange(n)
+        at = pos[sample]
+        d = st["x"][:, at] - xs
+        d -= L * np.round(d / L)
+        ex = np.linalg.norm(d) / np.linalg.norm(xs + L * img - e["x0"][:, sample])
+        ev = np.linalg.norm(st["v"][:, at] - vs) / np.linalg.norm(vs)
+        worst = max(worst, ex, ev)
+        assert ex < 1e-5 and ev < 1e-5, (k, e["N"], n, ex, ev)
+    print(f"batch_48, FP32 fields, 500 steps: worst e_x / e_v over the ensembles {worst:.3e}")
+
+
+def test_ids_and_segments_of_every_ensemble(batch):
+    ens, states = batch
+    for k, (e, st) in enumerate(zip(ens, states)):
+        n = e["n"]
+        assert np.array_equal(np.sort(st["ids"].astype(np.int64)), np.arange(n)), k
+        seg = st["seg"]
+        assert seg[0] == 0 and seg[-1] == n
+        dest, _ = oracle.keys(e["N"], L, (2, 2, 2), 8, st["x"])
+        assert np.array_equal(dest, np.repeat(np.arange(8), np.diff(seg))), k
