@@ -127,7 +127,7 @@ typedef struct {
    * stage velocity V* travels with the particle.  Trajectories equal those of
    * the default single migration after the step up to rounding; only the
    * storage order differs.  All ensembles of a context must agree.  Not with
-   * field_next or ckpt_every (the deferred-scatter step kernel only). */
+   * ckpt_every (the deferred-scatter step kernel with 256 threads only). */
   int migrate_per_stage;
   /* 1: owned-field mode, the memory pattern of the multi-GPU decomposition
    * (Sec. 2.1, 2.3): every subdomain interpolates only from its own copy of

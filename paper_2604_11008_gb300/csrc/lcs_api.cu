@@ -539,8 +539,8 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
       r = fail(c, LCS_ERR_ARG, "lcs_backward supports a frozen field only (ckpt_every > 0)");
       break;
     }
-    if (d.migrate_per_stage && (d.migrate_per_stage != 1 || d.field_next || d.ckpt_every > 0)) {
-      r = fail(c, LCS_ERR_ARG, "migrate_per_stage: not with field_next or ckpt_every");
+    if (d.migrate_per_stage && (d.migrate_per_stage != 1 || d.ckpt_every > 0)) {
+      r = fail(c, LCS_ERR_ARG, "migrate_per_stage: not with ckpt_every");
       break;
     }
     if (d.owned_field &&

@@ -469,16 +469,18 @@ __device__ __forceinline__ void heun_step_lo(const StepArgs &a, long long q[3], 
 //   X' = X* + (dt/2)(V* - V)          [= X + (dt/2)(V + V*)]
 //   V' = (V + V* + h2 D2 + dt g) / 2  [= V + (dt/2)(A1 + A2), dt A1 = V* - V]
 // with D2 = U(X*) - V*.  Same arithmetic pieces as the fused step.
-template <int KIND, bool OWNED = false>
+template <int KIND, bool OWNED = false, bool EVOLVE = false>
 __device__ __forceinline__ void heun_stage1_df(const StepArgs &a, long long q[3], const df V[3],
                                                df Vs[3], double tau, int img[3], int &bad,
-                                               const FieldBox &box = FieldBox{}) {
+                                               const FieldBox &box = FieldBox{},
+                                               StageTimes tt = StageTimes{0.0, 0.0}) {
   const Geom &g = a.geo;
   const df dt = {a.dfk[0], a.dfk[1]}, cx = {a.dfk[4], a.dfk[5]};
   const df h = df_mul(dt, df_recip(split_d(tau)));
   df U[3], D[3];
   if (OWNED && !brick_holds(box, q)) bad |= 2;
   interp_any<KIND, OWNED>(a.field, g.N, q, U, box);
+  if (EVOLVE && a.field_b) lerp_field_df<KIND>(a, q, tt.th1, U);
 #pragma unroll
   for (int s = 0; s < 3; ++s) D[s] = df_add(U[s], df_neg(V[s]));
   const df h1 = a.drag ? df_mul(h, drag_factor_df(a.drag_c, tau, D)) : h;
@@ -494,11 +496,12 @@ __device__ __forceinline__ void heun_stage1_df(const StepArgs &a, long long q[3]
   }
 }
 
-template <int KIND, bool OWNED = false>
+template <int KIND, bool OWNED = false, bool EVOLVE = false>
 __device__ __forceinline__ void heun_stage2_df(const StepArgs &a, long long q[3], df V[3],
                                                const df Vs[3], double tau, int img[3],
                                                int &bad,
-                                               const FieldBox &box = FieldBox{}) {
+                                               const FieldBox &box = FieldBox{},
+                                               StageTimes tt = StageTimes{0.0, 0.0}) {
   const Geom &g = a.geo;
   const df dt = {a.dfk[0], a.dfk[1]}, cx = {a.dfk[4], a.dfk[5]};
   const df hcx = df_scale2(cx, 0.5f);
@@ -506,6 +509,7 @@ __device__ __forceinline__ void heun_stage2_df(const StepArgs &a, long long q[3]
   df U[3], D[3];
   if (OWNED && !brick_holds(box, q)) bad |= 2;
   interp_any<KIND, OWNED>(a.field, g.N, q, U, box);
+  if (EVOLVE && a.field_b) lerp_field_df<KIND>(a, q, tt.th2, U);
 #pragma unroll
   for (int s = 0; s < 3; ++s) D[s] = df_add(U[s], df_neg(Vs[s]));
   const df h2 = a.drag ? df_mul(h, drag_factor_df(a.drag_c, tau, D)) : h;
@@ -523,10 +527,11 @@ __device__ __forceinline__ void heun_stage2_df(const StepArgs &a, long long q[3]
   }
 }
 
-template <int KIND, bool OWNED = false>
+template <int KIND, bool OWNED = false, bool EVOLVE = false>
 __device__ __forceinline__ void heun_stage1_lo(const StepArgs &a, long long q[3], const df V[3],
                                                df Vs[3], double tau, int img[3], int &bad,
-                                               const FieldBox &box = FieldBox{}) {
+                                               const FieldBox &box = FieldBox{},
+                                               StageTimes tt = StageTimes{0.0, 0.0}) {
   const Geom &g = a.geo;
   const float dt = a.dfk[0], cx = a.dfk[4];
   const float taus = split_d(tau).h;
@@ -535,6 +540,7 @@ __device__ __forceinline__ void heun_stage1_lo(const StepArgs &a, long long q[3]
   float D[3];
   if (OWNED && !brick_holds(box, q)) bad |= 2;
   interp_lo<KIND, OWNED>(a.field, g.N, q, U, box);
+  if (EVOLVE && a.field_b) lerp_field_lo<KIND>(a, q, (float)tt.th1, U);
 #pragma unroll
   for (int s = 0; s < 3; ++s) D[s] = U[s].h - V[s].h;
   const float h1 = a.drag ? h * drag_factor_f32((float)a.drag_c, taus, D) : h;
@@ -549,11 +555,12 @@ __device__ __forceinline__ void heun_stage1_lo(const StepArgs &a, long long q[3]
   }
 }
 
-template <int KIND, bool OWNED = false>
+template <int KIND, bool OWNED = false, bool EVOLVE = false>
 __device__ __forceinline__ void heun_stage2_lo(const StepArgs &a, long long q[3], df V[3],
                                                const df Vs[3], double tau, int img[3],
                                                int &bad,
-                                               const FieldBox &box = FieldBox{}) {
+                                               const FieldBox &box = FieldBox{},
+                                               StageTimes tt = StageTimes{0.0, 0.0}) {
   const Geom &g = a.geo;
   const float dt = a.dfk[0], cx = a.dfk[4];
   const float taus = split_d(tau).h;
@@ -562,6 +569,7 @@ __device__ __forceinline__ void heun_stage2_lo(const StepArgs &a, long long q[3]
   float D[3];
   if (OWNED && !brick_holds(box, q)) bad |= 2;
   interp_lo<KIND, OWNED>(a.field, g.N, q, U, box);
+  if (EVOLVE && a.field_b) lerp_field_lo<KIND>(a, q, (float)tt.th2, U);
 #pragma unroll
   for (int s = 0; s < 3; ++s) D[s] = U[s].h - Vs[s].h;
   const float h2 = a.drag ? h * drag_factor_f32((float)a.drag_c, taus, D) : h;
@@ -648,8 +656,10 @@ __device__ __forceinline__ void heun_step64(const StepArgs &a, long long q[3], d
 }
 
 // The two stages in FP64 arithmetic (see heun_stage1_df).
+template <bool EVOLVE = false>
 __device__ __forceinline__ void heun_stage1_64(const StepArgs &a, long long q[3], const df V[3],
-                                               df Vs[3], double tau, int img[3], int &bad) {
+                                               df Vs[3], double tau, int img[3], int &bad,
+                                               StageTimes tt = StageTimes{0.0, 0.0}) {
   const Geom &g = a.geo;
   const double itau = 1.0 / tau;
   double x[3], v[3], u1[3];
@@ -659,6 +669,7 @@ __device__ __forceinline__ void heun_stage1_64(const StepArgs &a, long long q[3]
     v[s] = vel_of_df(V[s]);
   }
   interp64(a.field, g, x[0], x[1], x[2], u1[0], u1[1], u1[2]);
+  if (EVOLVE && a.field_b) lerp_field64(a, x, tt.th1, u1);
   const double f1 = a.drag ? drag_factor64(a.drag_c, tau, u1, v) * itau : itau;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
@@ -672,9 +683,10 @@ __device__ __forceinline__ void heun_stage1_64(const StepArgs &a, long long q[3]
   }
 }
 
+template <bool EVOLVE = false>
 __device__ __forceinline__ void heun_stage2_64(const StepArgs &a, long long q[3], df V[3],
                                                const df Vs[3], double tau, int img[3],
-                                               int &bad) {
+                                               int &bad, StageTimes tt = StageTimes{0.0, 0.0}) {
   const Geom &g = a.geo;
   const double itau = 1.0 / tau;
   double xs[3], v[3], vs[3], u2[3];
@@ -685,6 +697,7 @@ __device__ __forceinline__ void heun_stage2_64(const StepArgs &a, long long q[3]
     vs[s] = vel_of_df(Vs[s]);
   }
   interp64(a.field, g, xs[0], xs[1], xs[2], u2[0], u2[1], u2[2]);
+  if (EVOLVE && a.field_b) lerp_field64(a, xs, tt.th2, u2);
   const double f2 = a.drag ? drag_factor64(a.drag_c, tau, u2, vs) * itau : itau;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {

@@ -550,18 +550,20 @@ __device__ __forceinline__ unsigned integrate_items(const StepArgs &a, const Til
           heun_step_df<KIND, EVOLVE, OWNED>(a, x[k], v[k], tau[k], img[k], bad, fv, tt);
         else heun_step_lo<KIND, EVOLVE, OWNED>(a, x[k], v[k], tau[k], img[k], bad, fv, tt);
       } else if (STAGE == 1) {
-        if (KIND == FK_F64) heun_stage1_64(a, x[k], v[k], vs[k], tau[k], img[k], bad);
+        if (KIND == FK_F64) heun_stage1_64<EVOLVE>(a, x[k], v[k], vs[k], tau[k], img[k], bad, tt);
         else if (KIND == FK_DF)
-          heun_stage1_df<KIND, OWNED>(a, x[k], v[k], vs[k], tau[k], img[k], bad, fv);
-        else heun_stage1_lo<KIND, OWNED>(a, x[k], v[k], vs[k], tau[k], img[k], bad, fv);
+          heun_stage1_df<KIND, OWNED, EVOLVE>(a, x[k], v[k], vs[k], tau[k], img[k], bad, fv, tt);
+        else
+          heun_stage1_lo<KIND, OWNED, EVOLVE>(a, x[k], v[k], vs[k], tau[k], img[k], bad, fv, tt);
       } else {
         const int64_t i = mt.bA + l0 + k;
 #pragma unroll
         for (int s = 0; s < 3; ++s) vs[k][s] = df_from2(A.vs[s][i]);
-        if (KIND == FK_F64) heun_stage2_64(a, x[k], v[k], vs[k], tau[k], img[k], bad);
+        if (KIND == FK_F64) heun_stage2_64<EVOLVE>(a, x[k], v[k], vs[k], tau[k], img[k], bad, tt);
         else if (KIND == FK_DF)
-          heun_stage2_df<KIND, OWNED>(a, x[k], v[k], vs[k], tau[k], img[k], bad, fv);
-        else heun_stage2_lo<KIND, OWNED>(a, x[k], v[k], vs[k], tau[k], img[k], bad, fv);
+          heun_stage2_df<KIND, OWNED, EVOLVE>(a, x[k], v[k], vs[k], tau[k], img[k], bad, fv, tt);
+        else
+          heun_stage2_lo<KIND, OWNED, EVOLVE>(a, x[k], v[k], vs[k], tau[k], img[k], bad, fv, tt);
       }
       int b = dest_bin(a.geo, mt.ps, x[k]);
       if (b < 0) {
@@ -798,7 +800,8 @@ __global__ void __launch_bounds__(BLOCK, (step_min_blocks<KIND, BLOCK, ITEMS>())
 // (kernel mode, threads per block, particles per thread) configurations the
 // tuner tries; mode 1 (staged field box) has no all-FP64 form
 // The last two arguments: evolving-field instantiation, Runge-Kutta stage
-// (0: whole step; 1, 2: migration per stage); both exist in mode 3 only.
+// (0: whole step; 1, 2: migration per stage); both exist in mode 3 only, and
+// together with 256 threads only.
 // Mode 4 is mode 3 reading the owned-field bricks (no all-FP64 form).
 #define LCS_STEP_CONFIGS(X, K, C)                                                   \
   X(K, 0, 256, 2, C, 0, 0) X(K, 0, 256, 1, C, 0, 0) X(K, 0, 128, 2, C, 0, 0)       \
@@ -808,7 +811,9 @@ __global__ void __launch_bounds__(BLOCK, (step_min_blocks<KIND, BLOCK, ITEMS>())
   X(K, 3, 128, 2, C, 1, 0) X(K, 3, 256, 1, C, 1, 0) X(K, 3, 256, 2, C, 0, 1)       \
   X(K, 3, 256, 2, C, 0, 2) X(K, 3, 256, 1, C, 0, 1) X(K, 3, 256, 1, C, 0, 2)       \
   X(K, 4, 256, 1, C, 0, 0) X(K, 4, 256, 2, C, 0, 0) X(K, 4, 256, 1, C, 0, 1)       \
-  X(K, 4, 256, 1, C, 0, 2) X(K, 4, 256, 2, C, 0, 1) X(K, 4, 256, 2, C, 0, 2)
+  X(K, 4, 256, 1, C, 0, 2) X(K, 4, 256, 2, C, 0, 1) X(K, 4, 256, 2, C, 0, 2)       \
+  X(K, 3, 256, 1, C, 1, 1) X(K, 3, 256, 1, C, 1, 2) X(K, 3, 256, 2, C, 1, 1)       \
+  X(K, 3, 256, 2, C, 1, 2)
 
 // Dynamic shared memory of a configuration: the staged field box (mode 1),
 // the two record buffers (mode 2) or the parked tile (modes 3 and 4).

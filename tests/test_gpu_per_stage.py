@@ -70,6 +70,37 @@ def test_per_stage_and_single_migration_agree_up_to_order(lcs):
     assert np.abs(va - vb).max() < 1e-12 * np.abs(va).max()
 
 
+@pytest.mark.parametrize("kernel,dtype,tol,items", [("df", "f64", 1e-12, 1),
+                                                    ("df", "f64", 1e-12, 2),
+                                                    ("fp64", "f64", 1e-12, 1),
+                                                    ("auto", "f32", 1e-5, 2)])
+def test_per_stage_with_evolving_field_against_oracle(lcs, kernel, dtype, tol, items):
+    # stage 1 sees the field at t_n, stage 2 (after the particles moved to
+    # the owner of X*) at t_n + dt; the step counter advances once per step
+    N, P, steps, dt = 24, (2, 3, 2), 16, 0.005
+    field, x, v, tau = case(430, N, 15000, dt=dt)
+    field2 = synth.small_case(431, N, 16, N / 4.0, 1, None)[0]
+    times = (0.0, 0.06)
+    sim = lcs.Simulator(field, x, v, dt, tau=tau, g=G, sub=P, kernel=kernel, field_dtype=dtype,
+                        track_images=True, sort_every=5, sort_brick=4, migrate_per_stage=True,
+                        field_next=field2, t_start=0.01, t_field=times)
+    sim.set_step_config(256, items, 3)
+    sim.step(steps)
+    st = gpu_state(sim)
+    ref = oracle.initial_state(N, L, P, x, v, tau, track_img=True)
+    oracle.run(ref, field, L, P, 0.0, dt, G, steps, sort_every=5, brick=4, per_stage=True,
+               field_b=field2, t_start=0.01, t_field=times)
+    ex, ev, _, _ = traj_errors(st["x"], st["img"], st["v"], st["ids"], ref, x)
+    assert ex < tol and ev < tol, (ex, ev)
+    if tol == 1e-12:
+        assert_same_storage(st, ref, N, P, 4)
+    # the time dependence matters: the frozen field lands far away
+    frozen = oracle.initial_state(N, L, P, x, v, tau, track_img=True)
+    oracle.run(frozen, field, L, P, 0.0, dt, G, steps, sort_every=5, brick=4, per_stage=True)
+    _, ev_f, _, _ = traj_errors(st["x"], st["img"], st["v"], st["ids"], frozen, x)
+    assert ev_f > 1e-3, ev_f
+
+
 def test_per_stage_configurations_and_batches_agree(lcs):
     N = 16
     specs = []
@@ -100,10 +131,10 @@ def test_per_stage_configurations_and_batches_agree(lcs):
 def test_per_stage_arguments(lcs):
     N = 16
     field, x, v, tau = case(420, N, 200)
-    for kw in (dict(field_next=field, t_field=(0.0, 1.0)), dict(ckpt_every=4, track_images=True)):
-        with pytest.raises(lcs.LcsError) as e:
-            lcs.Simulator(field, x, v, 0.01, tau=tau, migrate_per_stage=True, **kw)
-        assert e.value.status == lcs.LCS_ERR_ARG
+    with pytest.raises(lcs.LcsError) as e:
+        lcs.Simulator(field, x, v, 0.01, tau=tau, migrate_per_stage=True, ckpt_every=4,
+                      track_images=True)
+    assert e.value.status == lcs.LCS_ERR_ARG
     sim = lcs.Simulator(field, x, v, 0.01, tau=tau, migrate_per_stage=True)
     for cfg in ((256, 2, 0), (128, 2, 3)):
         with pytest.raises(lcs.LcsError) as e:
