@@ -81,7 +81,7 @@ struct lcs_ctx {
   int mode = 0;  // step kernel: 0 plain, 1 staged field box, 2 prefetched records, 3 deferred
   bool pf_tau = false, pf_img = false;  // some ensemble has per-particle tau / images
   bool evolve = false;  // some ensemble has an evolving field (mode-3 kernels only)
-  bool per_stage = false;  // migration after each Runge-Kutta stage (mode-3 kernels only)
+  bool per_stage = false;  // migration after each Runge-Kutta stage (modes 3 and 4 only)
   bool owned = false;      // owned-field mode (mode-4 kernels only)
   int block = 256, items = 2;   // threads per block, particles per thread (set in setup_batch)
   int step_grid = 1, total_P = 0;

@@ -281,7 +281,8 @@ cudaError_t launch_field_convert(const double *src, int N, FieldKind kind, void 
 cudaError_t launch_build_bricks(const void *field, const Geom &g, FieldKind kind, void *bricks,
                                 cudaStream_t st);
 // evolve: the evolving-field instantiation; stage: 0 whole step, 1/2 the
-// Runge-Kutta stages for migration per stage (both mode 3 only)
+// Runge-Kutta stages for migration per stage (modes 3 and 4; the evolving
+// field in mode 3 only)
 template <int CAP>
 cudaError_t launch_step_group(const StepGroup<CAP> &pb, FieldKind kind, int mode, int block,
                               int items, bool evolve, int stage, int grid, cudaStream_t st);
