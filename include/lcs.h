@@ -349,6 +349,18 @@ lcs_status lcs_partition(const uint32_t *keys, int64_t n, int nbins, uint32_t *p
 lcs_status lcs_partition_noalloc(const uint32_t *keys, int64_t n, int nbins, uint32_t *perm,
                                  int64_t *bin_off, int32_t *status, void *stream);
 
+/* Self-test of the bounded device-side waits (failure detection without a
+ * GPU fault).  Runs, in one small kernel on `stream`, the two waits the step
+ * kernels use against partners that never answer: the decoupled look-back
+ * of a tile whose predecessor never publishes, and an mbarrier wait for
+ * bulk copies that were never issued.  Both waits must give up after their
+ * iteration limits (about a second at most) and report it; the kernel then
+ * returns normally.  *lookback and *mbarrier (host) receive LCS_ERR_TIMEOUT
+ * when the respective wait gave up as designed (LCS_OK if it had not).
+ * Synchronising; LCS_ERR_ARG for NULL outputs, LCS_ERR_CUDA if the launch
+ * failed.  No context is involved. */
+lcs_status lcs_selftest_waits(void *stream, int32_t *lookback, int32_t *mbarrier);
+
 #ifdef __cplusplus
 }
 #endif

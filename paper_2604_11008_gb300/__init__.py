@@ -38,7 +38,7 @@ EXPORTS = ("lcs_init", "lcs_step", "lcs_migrate", "lcs_sort", "lcs_set_state", "
            "lcs_get_field", "lcs_backward", "lcs_sync", "lcs_last_error", "lcs_destroy",
            "lcs_launch_count", "lcs_partition", "lcs_profile_steps", "lcs_partition_noalloc",
            "lcs_tune", "lcs_set_step_config", "lcs_staged_tiles", "lcs_set_field",
-           "lcs_pair_histogram")
+           "lcs_pair_histogram", "lcs_selftest_waits")
 PARTITION_NOALLOC_MAX_N = 1 << 20
 DRAGS = {"stokes": 0, "nonlinear": 1}  # lcs_drag: f = 1, or the factor of Eq. (7)
 PROF_CLASSES = ("step", "finish", "unpack", "flip", "sort")
@@ -97,11 +97,12 @@ def lib():
         L.lcs_staged_tiles.argtypes = [P, P]
         L.lcs_set_field.argtypes = [P, i32, P, C.c_double]
         L.lcs_pair_histogram.argtypes = [P, i32, C.c_double, i32, P]
+        L.lcs_selftest_waits.argtypes = [P, P, P]
         for name in ("lcs_init", "lcs_step", "lcs_migrate", "lcs_sort", "lcs_set_state",
                      "lcs_get_state", "lcs_get_field", "lcs_backward", "lcs_sync",
                      "lcs_partition", "lcs_profile_steps", "lcs_partition_noalloc", "lcs_tune",
                      "lcs_set_step_config", "lcs_staged_tiles", "lcs_set_field",
-                     "lcs_pair_histogram"):
+                     "lcs_pair_histogram", "lcs_selftest_waits"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -386,6 +387,18 @@ def partition(keys, nbins: int, stream=None):
     if st != LCS_OK:
         raise LcsError(st, "lcs_partition failed")
     return perm[:n], off, status
+
+
+def selftest_waits(stream=None):
+    """Run the bounded-wait self-test (lcs_selftest_waits): the look-back and
+    mbarrier waits of the step kernels against partners that never answer.
+    Returns (lookback, mbarrier) statuses; LCS_ERR_TIMEOUT each when the
+    wait gave up as designed."""
+    a, b = C.c_int32(-1), C.c_int32(-1)
+    st = lib().lcs_selftest_waits(_stream(stream), C.byref(a), C.byref(b))
+    if st != LCS_OK:
+        raise LcsError(st, "lcs_selftest_waits failed")
+    return a.value, b.value
 
 
 def _autograd_function():

@@ -48,10 +48,11 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
       : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+// Non-blocking test of the phase with the given parity.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, unsigned parity) {
   unsigned ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
       " selp.u32 %0, 1, 0, p;\n}"
       : "=r"(ok)
       : "r"(smem_addr(bar)), "r"(parity)
@@ -59,10 +60,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
   return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity; false on timeout.
+// Bounded wait for the phase with the given parity; false on timeout.  The
+// barrier is polled without blocking, with a sleep of at most 256 ns between
+// polls, so `limit` polls take a known, bounded time (2^20 polls: well under
+// a second).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, long long limit) {
-  for (long long i = 0; i < limit; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
+  unsigned ns = 16;
+  for (long long i = 0; i < limit; ++i) {
+    if (mbar_test_wait(bar, parity)) return true;
+    __nanosleep(ns);
+    ns = ns < 256 ? 2 * ns : 256;
+  }
   return false;
 }
 
