@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lcs_internal.cuh"
 
 using namespace lcs;
@@ -492,7 +494,17 @@ lcs_status setup_batch(lcs_ctx *c) {
 
 extern "C" {
 
+// An NVTX range around a public entry point: the library's calls appear as
+// named spans on an Nsight timeline (header-only NVTX; no cost without a tool).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out) {
+  NvtxRange nvtx_range("lcs_init");
   if (!out) return LCS_ERR_ARG;
   *out = nullptr;
   if (!ens || n_ens < 1) return LCS_ERR_ARG;
@@ -741,6 +753,7 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
 }
 
 lcs_status lcs_step(lcs_ctx *c, int64_t nsteps) {
+  NvtxRange nvtx_range("lcs_step");
   lcs_status r = check_ctx(c);
   if (r != LCS_OK) return r;
   if (nsteps < 0) return reject(c, "nsteps < 0");
@@ -769,6 +782,7 @@ lcs_status lcs_step(lcs_ctx *c, int64_t nsteps) {
 }
 
 lcs_status lcs_migrate(lcs_ctx *c) {
+  NvtxRange nvtx_range("lcs_migrate");
   lcs_status r = check_ctx(c);
   if (r != LCS_OK) return r;
   for (auto &e : c->ens) {
@@ -779,6 +793,7 @@ lcs_status lcs_migrate(lcs_ctx *c) {
 }
 
 lcs_status lcs_sort(lcs_ctx *c) {
+  NvtxRange nvtx_range("lcs_sort");
   lcs_status r = check_ctx(c);
   if (r != LCS_OK) return r;
   for (auto &e : c->ens) {
@@ -791,6 +806,7 @@ lcs_status lcs_sort(lcs_ctx *c) {
 lcs_status lcs_set_state(lcs_ctx *c, int ens, const double *x, const double *v,
                          const double *tau, const uint32_t *ids, const int32_t *img,
                          const int64_t *seg) {
+  NvtxRange nvtx_range("lcs_set_state");
   lcs_status r = check_ctx(c);
   if (r != LCS_OK) return r;
   if (ens < 0 || ens >= (int)c->ens.size() || !x || !v || !ids || !seg)
@@ -841,6 +857,7 @@ lcs_status lcs_set_state(lcs_ctx *c, int ens, const double *x, const double *v,
 
 lcs_status lcs_get_state(lcs_ctx *c, int ens, double *x, double *v, double *tau,
                          uint32_t *ids, int32_t *img, int64_t *seg) {
+  NvtxRange nvtx_range("lcs_get_state");
   if (!c) return LCS_ERR_ARG;
   if (c->failed) return LCS_ERR_STATE;
   if (ens < 0 || ens >= (int)c->ens.size()) return reject(c, "bad ensemble");
@@ -966,6 +983,7 @@ lcs_status lcs_set_field(lcs_ctx *c, int ens, const double *field, double t) {
 
 lcs_status lcs_backward(lcs_ctx *c, const double *gx, const double *gv, double *gU,
                         double *gx0, double *gv0) {
+  NvtxRange nvtx_range("lcs_backward");
   lcs_status r = check_ctx(c);
   if (r != LCS_OK) return r;
   if (c->ens.size() != 1) return reject(c, "lcs_backward: one ensemble only");
@@ -1005,6 +1023,7 @@ lcs_status lcs_backward(lcs_ctx *c, const double *gx, const double *gv, double *
 }
 
 lcs_status lcs_profile_steps(lcs_ctx *c, int64_t nsteps, double *ms, int64_t *count) {
+  NvtxRange nvtx_range("lcs_profile_steps");
   lcs_status r = check_ctx(c);
   if (r != LCS_OK) return r;
   if (nsteps < 0 || !ms) return reject(c, "lcs_profile_steps: bad argument");
@@ -1097,6 +1116,7 @@ lcs_status lcs_staged_tiles(lcs_ctx *c, int64_t *count) {
 
 lcs_status lcs_tune(lcs_ctx *c, int steps_per_trial, int *block, int *items, int *mode,
                     double *trial_ms) {
+  NvtxRange nvtx_range("lcs_tune");
   lcs_status r = check_ctx(c);
   if (r != LCS_OK) return r;
   if (steps_per_trial < 1) return reject(c, "lcs_tune: steps_per_trial < 1");
