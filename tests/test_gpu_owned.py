@@ -139,3 +139,23 @@ def test_owned_field_arguments(lcs):
     with pytest.raises(lcs.LcsError) as e:
         lcs.Simulator(None, None, None, None, ensembles=[dict(spec, owned_field=True), spec])
     assert e.value.status == lcs.LCS_ERR_ARG
+
+
+def test_owned_field_in_a_batch_of_uneven_ensembles(lcs):
+    # three ensembles of different grids and subdomain shapes in one
+    # context: each reads its own bricks through the shared launches
+    specs = []
+    for k, (N, P) in enumerate(((16, (2, 2, 2)), (24, (3, 2, 1)), (12, (1, 3, 2)))):
+        field, x, v, tau = case(610 + k, N, 3000 + 2000 * k)
+        specs.append(dict(field=field, x0=x, v0=v, dt=0.01, tau=tau, g=G, sub=P, kernel="df",
+                          sort_every=4, track_images=True))
+    out = []
+    for owned in (False, True):
+        sim = lcs.Simulator(None, None, None, None,
+                            ensembles=[dict(sp, owned_field=owned) for sp in specs])
+        sim.step(9)
+        out.append([gpu_state(sim, k) for k in range(len(specs))])
+        sim.close()
+    for k in range(len(specs)):
+        for key in ("seg", "ids", "x", "v", "img"):
+            assert np.array_equal(out[0][k][key], out[1][k][key]), (k, key)
