@@ -135,9 +135,10 @@ typedef struct {
    * (N/P_s + 4) cells per axis, built from the field at lcs_init).  A
    * stencil outside the brick -- a particle moved more than one cell beyond
    * its subdomain within a stage -- is reported as LCS_ERR_DISPLACEMENT.
-   * Results equal those of the shared field bit for bit otherwise.  All
-   * ensembles of a context must agree.  Not with LCS_KERNEL_FP64,
-   * field_next or ckpt_every; the step kernel is then mode
+   * Results equal those of the shared field bit for bit otherwise.  With
+   * field_next the second snapshot has bricks too (rebuilt by
+   * lcs_set_field).  All ensembles of a context must agree.  Not with
+   * LCS_KERNEL_FP64 or ckpt_every; the step kernel is then mode
    * LCS_STEP_OWNED_FIELD.  0: every subdomain reads the one field copy. */
   int owned_field;
 } lcs_desc;

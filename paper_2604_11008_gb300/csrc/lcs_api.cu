@@ -52,6 +52,7 @@ struct Ens {
   void *field = nullptr;
   void *field_b = nullptr;  // second snapshot (evolving field) or nullptr
   void *bricks = nullptr;   // owned-field mode: the subdomains' field bricks
+  void *bricks_b = nullptr; // the same for the second snapshot (evolving field)
   double t_a = 0.0, t_b = 1.0;
   StepArgs a{};
   SortArgs s{};
@@ -556,9 +557,9 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
       break;
     }
     if (d.owned_field &&
-        (d.owned_field != 1 || d.field_next || d.ckpt_every > 0 ||
+        (d.owned_field != 1 || d.ckpt_every > 0 ||
          (d.field_dtype == LCS_F64 && d.field_kernel == LCS_KERNEL_FP64))) {
-      r = fail(c, LCS_ERR_ARG, "owned_field: not with LCS_KERNEL_FP64, field_next or ckpt_every");
+      r = fail(c, LCS_ERR_ARG, "owned_field: not with LCS_KERNEL_FP64 or ckpt_every");
       break;
     }
     switch (d.field_dtype) {
@@ -664,12 +665,14 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
     if (d.owned_field) {
       const int64_t bcell = (int64_t)(g.W[0] + 4) * (g.W[1] + 4) * (g.W[2] + 4);
       A(dalloc(c, (char **)&e.bricks, (int64_t)P * bcell * fbytes));
+      if (d.field_next) A(dalloc(c, (char **)&e.bricks_b, (int64_t)P * bcell * fbytes));
     }
     A(dalloc(c, &m.nstep, 1));
     if (r != LCS_OK) break;
     e.a.field = e.field;
     e.a.field_b = e.field_b;
     e.a.bricks = e.bricks;
+    e.a.bricks_b = e.bricks_b;
     e.t_a = d.t_field[0];
     e.t_b = d.t_field[1];
     if (e.field_b) {
@@ -701,6 +704,7 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
     C2(launch_field_convert(d.field, d.n, e.kind, e.field, st));
     if (e.field_b) C2(launch_field_convert(d.field_next, d.n, e.kind, e.field_b, st));
     if (e.bricks) C2(launch_build_bricks(e.field, e.a.geo, e.kind, e.bricks, st));
+    if (e.bricks_b) C2(launch_build_bricks(e.field_b, e.a.geo, e.kind, e.bricks_b, st));
     C2(cudaMemsetAsync(m.nstep, 0, sizeof(int64_t), st));
     // particles -> buffer 1 compacted as one input segment, then migrate
     Rec &B1 = e.a.buf[1];
@@ -968,6 +972,13 @@ lcs_status lcs_set_field(lcs_ctx *c, int ens, const double *field, double t) {
   std::swap(e.field, e.field_b);  // the newer snapshot becomes the first
   CK(launch_field_convert(field, e.d.n, e.kind, e.field_b, c->st));
   c->launches += 1;
+  if (e.bricks_b) {  // owned field: the bricks follow their snapshots
+    std::swap(e.bricks, e.bricks_b);
+    CK(launch_build_bricks(e.field_b, e.a.geo, e.kind, e.bricks_b, c->st));
+    c->launches += 1;
+    e.a.bricks = e.bricks;
+    e.a.bricks_b = e.bricks_b;
+  }
   e.t_a = e.t_b;
   e.t_b = t;
   e.a.field = e.field;

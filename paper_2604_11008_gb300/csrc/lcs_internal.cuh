@@ -119,8 +119,10 @@ struct StepArgs {
   double th0, dth;
   // owned-field mode: the subdomains' own field bricks (W_s + 4 cells per
   // axis: the subdomain's cells and a halo of two), subdomain s at cell
-  // s (W_x + 4)(W_y + 4)(W_z + 4); nullptr otherwise
+  // s (W_x + 4)(W_y + 4)(W_z + 4); nullptr otherwise.  bricks_b: the same
+  // for the second snapshot of an evolving field (else nullptr)
   const void *bricks;
+  const void *bricks_b;
 };
 
 // The ensembles of one context, as the batched kernels see them.

@@ -334,23 +334,33 @@ __device__ __forceinline__ long long wrap_fix(long long q, long long qL, int &im
   return q;
 }
 
+// The second snapshot's view of an owned-field brick: same geometry, the
+// same subdomain's brick in bricks_b.
+__device__ __forceinline__ FieldBox brick_b_of(const StepArgs &a, const FieldBox &box) {
+  FieldBox b = box;
+  b.s = (const unsigned char *)a.bricks_b +
+        ((const unsigned char *)box.s - (const unsigned char *)a.bricks);
+  return b;
+}
+
 // U <- U + th (U_b - U) with U_b interpolated from the second snapshot
-// (float-float; FP32 for FP32/BF16 storage, whose U carries no low part).
-template <int KIND>
+// (float-float; FP32 for FP32/BF16 storage, whose U carries no low part);
+// OWNED: from the subdomain's brick of the second snapshot.
+template <int KIND, bool OWNED = false>
 __device__ __forceinline__ void lerp_field_df(const StepArgs &a, const long long q[3], double th,
-                                           df U[3]) {
+                                           df U[3], const FieldBox &box = FieldBox{}) {
   df Ub[3];
-  interp_any<KIND>(a.field_b, a.geo.N, q, Ub, FieldBox{});
+  interp_any<KIND, OWNED>(a.field_b, a.geo.N, q, Ub, OWNED ? brick_b_of(a, box) : FieldBox{});
   const df t = split_d(th);
 #pragma unroll
   for (int s = 0; s < 3; ++s) U[s] = df_add(U[s], df_mul(t, df_add(Ub[s], df_neg(U[s]))));
 }
 
-template <int KIND>
+template <int KIND, bool OWNED = false>
 __device__ __forceinline__ void lerp_field_lo(const StepArgs &a, const long long q[3], float th,
-                                           df U[3]) {
+                                           df U[3], const FieldBox &box = FieldBox{}) {
   df Ub[3];
-  interp_lo<KIND>(a.field_b, a.geo.N, q, Ub, FieldBox{});
+  interp_lo<KIND, OWNED>(a.field_b, a.geo.N, q, Ub, OWNED ? brick_b_of(a, box) : FieldBox{});
 #pragma unroll
   for (int s = 0; s < 3; ++s) U[s].h = fmaf(th, Ub[s].h - U[s].h, U[s].h);
 }
@@ -377,7 +387,7 @@ __device__ __forceinline__ void heun_step_df(const StepArgs &a, long long q[3], 
   df U[3], hD1[3], Vs[3], D[3];
   if (OWNED && !brick_holds(box, q)) bad |= 2;
   interp_any<KIND, OWNED>(a.field, g.N, q, U, box);
-  if (EVOLVE && a.field_b) lerp_field_df<KIND>(a, q, tt.th1, U);
+  if (EVOLVE && a.field_b) lerp_field_df<KIND, OWNED>(a, q, tt.th1, U, box);
 #pragma unroll
   for (int s = 0; s < 3; ++s) D[s] = df_add(U[s], df_neg(V[s]));
   const df h1 = a.drag ? df_mul(h, drag_factor_df(a.drag_c, tau, D)) : h;
@@ -390,7 +400,7 @@ __device__ __forceinline__ void heun_step_df(const StepArgs &a, long long q[3], 
   }
   if (OWNED && !brick_holds(box, q2)) bad |= 2;
   interp_any<KIND, OWNED>(a.field, g.N, q2, U, box);
-  if (EVOLVE && a.field_b) lerp_field_df<KIND>(a, q2, tt.th2, U);
+  if (EVOLVE && a.field_b) lerp_field_df<KIND, OWNED>(a, q2, tt.th2, U, box);
 #pragma unroll
   for (int s = 0; s < 3; ++s) D[s] = df_add(U[s], df_neg(Vs[s]));
   const df h2 = a.drag ? df_mul(h, drag_factor_df(a.drag_c, tau, D)) : h;
@@ -428,7 +438,7 @@ __device__ __forceinline__ void heun_step_lo(const StepArgs &a, long long q[3], 
   float hD1[3], Vs[3], D[3];
   if (OWNED && !brick_holds(box, q)) bad |= 2;
   interp_lo<KIND, OWNED>(a.field, g.N, q, U, box);
-  if (EVOLVE && a.field_b) lerp_field_lo<KIND>(a, q, (float)tt.th1, U);
+  if (EVOLVE && a.field_b) lerp_field_lo<KIND, OWNED>(a, q, (float)tt.th1, U, box);
 #pragma unroll
   for (int s = 0; s < 3; ++s) D[s] = U[s].h - V[s].h;
   const float h1 = a.drag ? h * drag_factor_f32((float)a.drag_c, taus, D) : h;
@@ -441,7 +451,7 @@ __device__ __forceinline__ void heun_step_lo(const StepArgs &a, long long q[3], 
   }
   if (OWNED && !brick_holds(box, q2)) bad |= 2;
   interp_lo<KIND, OWNED>(a.field, g.N, q2, U, box);
-  if (EVOLVE && a.field_b) lerp_field_lo<KIND>(a, q2, (float)tt.th2, U);
+  if (EVOLVE && a.field_b) lerp_field_lo<KIND, OWNED>(a, q2, (float)tt.th2, U, box);
 #pragma unroll
   for (int s = 0; s < 3; ++s) D[s] = U[s].h - Vs[s];
   const float h2 = a.drag ? h * drag_factor_f32((float)a.drag_c, taus, D) : h;
@@ -480,7 +490,7 @@ __device__ __forceinline__ void heun_stage1_df(const StepArgs &a, long long q[3]
   df U[3], D[3];
   if (OWNED && !brick_holds(box, q)) bad |= 2;
   interp_any<KIND, OWNED>(a.field, g.N, q, U, box);
-  if (EVOLVE && a.field_b) lerp_field_df<KIND>(a, q, tt.th1, U);
+  if (EVOLVE && a.field_b) lerp_field_df<KIND, OWNED>(a, q, tt.th1, U, box);
 #pragma unroll
   for (int s = 0; s < 3; ++s) D[s] = df_add(U[s], df_neg(V[s]));
   const df h1 = a.drag ? df_mul(h, drag_factor_df(a.drag_c, tau, D)) : h;
@@ -509,7 +519,7 @@ __device__ __forceinline__ void heun_stage2_df(const StepArgs &a, long long q[3]
   df U[3], D[3];
   if (OWNED && !brick_holds(box, q)) bad |= 2;
   interp_any<KIND, OWNED>(a.field, g.N, q, U, box);
-  if (EVOLVE && a.field_b) lerp_field_df<KIND>(a, q, tt.th2, U);
+  if (EVOLVE && a.field_b) lerp_field_df<KIND, OWNED>(a, q, tt.th2, U, box);
 #pragma unroll
   for (int s = 0; s < 3; ++s) D[s] = df_add(U[s], df_neg(Vs[s]));
   const df h2 = a.drag ? df_mul(h, drag_factor_df(a.drag_c, tau, D)) : h;
@@ -540,7 +550,7 @@ __device__ __forceinline__ void heun_stage1_lo(const StepArgs &a, long long q[3]
   float D[3];
   if (OWNED && !brick_holds(box, q)) bad |= 2;
   interp_lo<KIND, OWNED>(a.field, g.N, q, U, box);
-  if (EVOLVE && a.field_b) lerp_field_lo<KIND>(a, q, (float)tt.th1, U);
+  if (EVOLVE && a.field_b) lerp_field_lo<KIND, OWNED>(a, q, (float)tt.th1, U, box);
 #pragma unroll
   for (int s = 0; s < 3; ++s) D[s] = U[s].h - V[s].h;
   const float h1 = a.drag ? h * drag_factor_f32((float)a.drag_c, taus, D) : h;
@@ -569,7 +579,7 @@ __device__ __forceinline__ void heun_stage2_lo(const StepArgs &a, long long q[3]
   float D[3];
   if (OWNED && !brick_holds(box, q)) bad |= 2;
   interp_lo<KIND, OWNED>(a.field, g.N, q, U, box);
-  if (EVOLVE && a.field_b) lerp_field_lo<KIND>(a, q, (float)tt.th2, U);
+  if (EVOLVE && a.field_b) lerp_field_lo<KIND, OWNED>(a, q, (float)tt.th2, U, box);
 #pragma unroll
   for (int s = 0; s < 3; ++s) D[s] = U[s].h - Vs[s].h;
   const float h2 = a.drag ? h * drag_factor_f32((float)a.drag_c, taus, D) : h;

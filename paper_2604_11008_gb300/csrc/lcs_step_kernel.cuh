@@ -800,8 +800,8 @@ __global__ void __launch_bounds__(BLOCK, (step_min_blocks<KIND, BLOCK, ITEMS>())
 // (kernel mode, threads per block, particles per thread) configurations the
 // tuner tries; mode 1 (staged field box) has no all-FP64 form
 // The last two arguments: evolving-field instantiation, Runge-Kutta stage
-// (0: whole step; 1, 2: migration per stage); both exist in mode 3 only, and
-// together with 256 threads only.
+// (0: whole step; 1, 2: migration per stage); both exist in modes 3 and 4
+// only, and together with 256 threads only.
 // Mode 4 is mode 3 reading the owned-field bricks (no all-FP64 form).
 #define LCS_STEP_CONFIGS(X, K, C)                                                   \
   X(K, 0, 256, 2, C, 0, 0) X(K, 0, 256, 1, C, 0, 0) X(K, 0, 128, 2, C, 0, 0)       \
@@ -813,7 +813,9 @@ __global__ void __launch_bounds__(BLOCK, (step_min_blocks<KIND, BLOCK, ITEMS>())
   X(K, 4, 256, 1, C, 0, 0) X(K, 4, 256, 2, C, 0, 0) X(K, 4, 256, 1, C, 0, 1)       \
   X(K, 4, 256, 1, C, 0, 2) X(K, 4, 256, 2, C, 0, 1) X(K, 4, 256, 2, C, 0, 2)       \
   X(K, 3, 256, 1, C, 1, 1) X(K, 3, 256, 1, C, 1, 2) X(K, 3, 256, 2, C, 1, 1)       \
-  X(K, 3, 256, 2, C, 1, 2)
+  X(K, 3, 256, 2, C, 1, 2) X(K, 4, 256, 1, C, 1, 0) X(K, 4, 256, 2, C, 1, 0)       \
+  X(K, 4, 256, 1, C, 1, 1) X(K, 4, 256, 1, C, 1, 2) X(K, 4, 256, 2, C, 1, 1)       \
+  X(K, 4, 256, 2, C, 1, 2)
 
 // Dynamic shared memory of a configuration: the staged field box (mode 1),
 // the two record buffers (mode 2) or the parked tile (modes 3 and 4).

@@ -76,6 +76,28 @@ def test_owned_against_oracle(lcs, items):
     assert_same_storage(st, ref, N, P, 4)
 
 
+@pytest.mark.parametrize("per_stage", [False, True])
+@pytest.mark.parametrize("kernel,dtype", [("df", "f64"), ("auto", "f32")])
+def test_owned_evolving_field_equals_shared(lcs, kernel, dtype, per_stage):
+    # both snapshots have bricks; a snapshot pushed mid-run rebuilds them
+    N, P, dt = 24, (2, 2, 3), 0.005
+    field, x, v, tau = case(605, N, 12000, dt=dt)
+    snaps = [field] + [synth.small_case(606 + k, N, 16, N / 4.0, 1, None)[0] for k in range(2)]
+    out = []
+    for owned in (False, True):
+        sim = lcs.Simulator(snaps[0], x, v, dt, tau=tau, g=G, sub=P, kernel=kernel,
+                            field_dtype=dtype, track_images=True, sort_every=4, sort_brick=4,
+                            migrate_per_stage=per_stage, owned_field=owned, field_next=snaps[1],
+                            t_start=0.0, t_field=(0.0, 0.04))
+        sim.step(8)
+        sim.set_field(snaps[2], 0.08)
+        sim.step(8)
+        out.append(gpu_state(sim))
+        sim.close()
+    for key in ("seg", "ids", "x", "v", "img"):
+        assert np.array_equal(out[0][key], out[1][key]), key
+
+
 def test_thin_subdomains_with_overlapping_halos(lcs):
     # W = 1, 2, 4 cells per subdomain: the halos of neighbours overlap and
     # wrap around the periodic faces
@@ -122,8 +144,7 @@ def test_stencil_outside_the_brick_is_reported(lcs):
 def test_owned_field_arguments(lcs):
     N = 16
     field, x, v, tau = case(604, N, 500)
-    for kw in (dict(kernel="fp64"), dict(field_next=field, t_field=(0.0, 1.0)),
-               dict(ckpt_every=4, track_images=True)):
+    for kw in (dict(kernel="fp64"), dict(ckpt_every=4, track_images=True)):
         with pytest.raises(lcs.LcsError) as e:
             lcs.Simulator(field, x, v, 0.01, tau=tau, sub=(2, 2, 2), owned_field=True, **kw)
         assert e.value.status == lcs.LCS_ERR_ARG, kw
