@@ -63,3 +63,19 @@ def test_null_context_and_bad_arguments_are_rejected_without_gpu_work():
     assert isinstance(L.lcs_last_error(None), bytes)
     L.lcs_destroy(None)
     assert L.lcs_partition(None, -1, 4, None, None, None, None) == lcs.LCS_ERR_ARG
+
+
+def test_header_is_plain_c():
+    """include/lcs.h compiles as C11 (no C++ or torch types in the ABI): the
+    C example that the GPU tests build and run is checked for syntax here."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not found")
+    from paper_2604_11008_gb300 import build
+    cuda = os.path.dirname(os.path.dirname(build.nvcc()))
+    subprocess.run([gcc, "-std=c11", "-Wall", "-Werror", "-fsyntax-only",
+                    os.path.join(ROOT, "tests", "c_abi", "uniform_flow.c"),
+                    "-I", os.path.join(ROOT, "include"), "-I", os.path.join(cuda, "include")],
+                   check=True)
