@@ -367,7 +367,7 @@ def main():
     ap.add_argument("--workload", default="scale_256")
     ap.add_argument("--kernel", default="auto", choices=["auto", "fp64", "df"])
     ap.add_argument("--field", default="f64", choices=["f64", "f32", "bf16"])
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--variants", type=int, default=1,
                     help="also time the nonlinear drag of Eq. (7) and an evolving field")
     ap.add_argument("--no-cpu-baseline", action="store_true")

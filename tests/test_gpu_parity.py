@@ -333,3 +333,53 @@ def test_precision_variant_trajectories(lcs, dtype, tol_q, tol_64):
         oracle.run(ref, f_ref, L, P, 0.0, dt, g, steps)
         ex, ev, _, _ = traj_errors(st["x"], st["img"], st["v"], st["ids"], ref, x)
         assert ex < tol and ev < tol, (dtype, ex, ev)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_positions_on_cell_faces_and_box_edges(lcs, kernel):
+    # degenerate positions: exactly on cell faces (x = k dx), on cell centres,
+    # at 0 and one ulp below L, on subdomain faces; the oracle decides cells
+    # with the same floor(x N/L), so storage and trajectories must agree
+    N, P, dt, steps = 16, (2, 2, 2), 0.005, 6
+    dx = L / N
+    rng = np.random.default_rng(77)
+    pts = [0.0, np.nextafter(L, 0.0), dx, 8 * dx, (N - 1) * dx, 0.5 * dx, 7.5 * dx,
+           np.nextafter(8 * dx, 0.0), np.nextafter(8 * dx, L)]
+    x = np.ascontiguousarray(rng.choice(pts, size=(3, 3000)))
+    field, _, _, _, _ = synth.small_case(78, N, 16, 3.0, 1, None)
+    v = np.ascontiguousarray(rng.standard_normal(x.shape))
+    sim = make(lcs, field, x, v, dt, sub=P, track_images=True, kernel=kernel, sort_every=3,
+               sort_brick=4)
+    st0 = gpu_state(sim)
+    ref0 = oracle.initial_state(N, L, P, x, v, None, track_img=True)
+    assert np.array_equal(st0["seg"], ref0.seg)
+    assert np.array_equal(st0["ids"].astype(np.uint32), ref0.ids)
+    sim.step(steps)
+    st = gpu_state(sim)
+    ref = oracle.initial_state(N, L, P, x, v, None, track_img=True)
+    oracle.run(ref, field, L, P, 0.1, dt, (0.0, 0.0, 0.0), steps, sort_every=3, brick=4)
+    ex, ev, _, _ = traj_errors(st["x"], st["img"], st["v"], st["ids"], ref, x)
+    assert ex < TOL_FP64 and ev < TOL_FP64, (ex, ev)
+    assert_same_storage(st, ref, N, P, 4)
+
+
+def test_capacity_overflow_is_reported(lcs):
+    # 6000 particles of subdomain 0 cross into subdomain 1 (200 particles,
+    # room for 200 + 200/16 + 128) in one step: the arrivals cannot be
+    # placed, which is reported instead of written out of range
+    N, P, dt = 16, (2, 1, 1), 0.01
+    dx = L / N
+    rng = np.random.default_rng(79)
+    xa = np.stack([rng.uniform(7.2 * dx, 7.9 * dx, 6000), rng.uniform(0, L, 6000),
+                   rng.uniform(0, L, 6000)])
+    xb = np.stack([rng.uniform(9 * dx, 15 * dx, 200), rng.uniform(0, L, 200),
+                   rng.uniform(0, L, 200)])
+    x = np.ascontiguousarray(np.concatenate([xa, xb], axis=1))
+    v = np.zeros_like(x)
+    v[0, :6000] = 1.2 * dx / dt
+    field = np.zeros((3, N, N, N))
+    sim = make(lcs, field, x, v, dt, tau_const=1.0, sub=P)
+    with pytest.raises(lcs.LcsError) as e:
+        sim.step(1)
+        sim.sync()
+    assert e.value.status == lcs.LCS_ERR_CAPACITY
