@@ -299,9 +299,10 @@ __global__ void k_keys_cell(StepArgs a, uint32_t *key, uint32_t *pay, int B, int
   const int64_t *base = a.m.lay_base[ph];
   const int P = a.geo.Ptot;
   const int64_t n = a.m.cstart[P];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int seg = find_segment64(a.m.cstart, P, i);
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int seg = i < n ? find_segment64(a.m.cstart, P, i) : 0;  // then tracked: i only grows
+  for (; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    while (seg + 1 < P && a.m.cstart[seg + 1] <= i) ++seg;
     const int64_t slot = base[seg] + (i - a.m.cstart[seg]);
     const int ps[3] = {seg % a.geo.P[0], (seg / a.geo.P[0]) % a.geo.P[1],
                        seg / (a.geo.P[0] * a.geo.P[1])};
@@ -374,21 +375,75 @@ __global__ void __launch_bounds__(1024) k_relayout(StepArgs a, int from_starts) 
 }
 
 // Output rank r (compacted, segment found from cstart) <- input slot pay[r].
-__global__ void k_gather(StepArgs a, const uint32_t *pay) {
+// A thread copies GATHER_ITEMS records per round (ranks r0 + k * stride),
+// issuing all their loads before any store so that many of the scattered
+// reads are in flight at once; the segment of a rank is tracked
+// incrementally (a thread's ranks only grow) instead of a binary search
+// per record.
+constexpr int GATHER_ITEMS = 4;
+__global__ void __launch_bounds__(256) k_gather(StepArgs a, const uint32_t *pay) {
   const int ph = *a.m.phase;
   const Rec A = a.buf[ph], B = a.buf[ph ^ 1];
   const int64_t *baseB = a.m.lay_base[ph ^ 1];
+  const int64_t *cs = a.m.cstart;
   const int P = a.geo.Ptot;
-  const int64_t n = a.m.cstart[P];
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
-       r += (int64_t)gridDim.x * blockDim.x) {
-    const int d = find_segment64(a.m.cstart, P, r);
-    const uint32_t src = pay[r];
-    if (src >= a.cap) {  // corrupt permutation: report, never read out of bounds
-      latch(a.m.status, LCS_ERR_STATE);
-      continue;
+  const int64_t n = cs[P];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t r0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int d = r0 < n ? find_segment64(cs, P, r0) : 0;
+  for (; r0 < n; r0 += stride * GATHER_ITEMS) {
+    int64_t src[GATHER_ITEMS], dst[GATHER_ITEMS];
+#pragma unroll
+    for (int k = 0; k < GATHER_ITEMS; ++k) {
+      const int64_t r = r0 + k * stride;
+      src[k] = -1;
+      dst[k] = 0;
+      if (r < n) {
+        while (d + 1 < P && cs[d + 1] <= r) ++d;
+        const uint32_t s = pay[r];
+        if (s >= a.cap) {  // corrupt permutation: report, never read out of bounds
+          latch(a.m.status, LCS_ERR_STATE);
+        } else {
+          src[k] = s;
+          dst[k] = baseB[d] + (r - cs[d]);
+        }
+      }
     }
-    copy_rec(A, src, B, baseB[d] + (r - a.m.cstart[d]));
+    long long x[GATHER_ITEMS][3];
+    float2 v[GATHER_ITEMS][3];
+    double tau[GATHER_ITEMS];
+    uint32_t id[GATHER_ITEMS];
+#pragma unroll
+    for (int k = 0; k < GATHER_ITEMS; ++k) {
+      if (src[k] < 0) continue;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        x[k][c] = A.x[c][src[k]];
+        v[k][c] = A.v[c][src[k]];
+      }
+      tau[k] = A.tau ? A.tau[src[k]] : 0.0;
+      id[k] = A.id[src[k]];
+    }
+#pragma unroll
+    for (int k = 0; k < GATHER_ITEMS; ++k) {
+      if (src[k] < 0) continue;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        B.x[c][dst[k]] = x[k][c];
+        B.v[c][dst[k]] = v[k][c];
+      }
+      if (A.tau) B.tau[dst[k]] = tau[k];
+      B.id[dst[k]] = id[k];
+      // optional rows (image counts, stage velocities), record by record
+      if (A.img[0]) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) B.img[c][dst[k]] = A.img[c][src[k]];
+      }
+      if (A.vs[0]) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) B.vs[c][dst[k]] = A.vs[c][src[k]];
+      }
+    }
   }
 }
 
