@@ -367,55 +367,58 @@ __device__ __forceinline__ void lerp_field_lo(const StepArgs &a, const long long
 
 // Heun step of Eqs. (5)-(6) (gravity g) with float-float increments, on the
 // fixed-point position q (cell units, 52 fraction bits) and the float-pair
-// velocity V:
-//   h = dt/tau, D1 = U(X) - V, h1 = f(D1) h, V* = V + h1 D1 + dt g,
-//   X* = X + dt V, D2 = U(X*) - V*, h2 = f(D2) h,
-//   dV = (h1 D1 + h2 D2)/2 + dt g, dX = dt V + (dt/2)(h1 D1 + dt g)
-//   [= dt (V + V*)/2], with f = 1 (Stokes) or the factor of Eq. (7);
-// then q' = q + (N/L) dX in fixed point (exact addition), V' = V + dV in
-// float-float, and the periodic wrap.  No FP64 instruction on the Stokes path.
+// velocity V, with h = dt/tau and f = 1 (Stokes) or the factor of Eq. (7):
+//   X* = X + dt V                          (needs only the record: taken first)
+//   a1 = h1 (U(X) - V) + dt g              (dt A1, h1 = f(D1) h)
+//   V* = V + a1,  Vh = V + a1/2
+//   X' = X + dt Vh                         [= X + (dt/2)(V + V*)]
+//   a2 = h2 (U(X*) - V*) + dt g            (dt A2)
+//   V' = Vh + a2/2                         [= V + (dt/2)(A1 + A2)]
+// X' is added to q in fixed point (exact addition of a float-float
+// displacement converted to fixed point) and wrapped before the second
+// interpolation, so only X', V* and Vh stay live across it.  No FP64
+// instruction on the Stokes path.
 template <int KIND, bool EVOLVE = false, bool OWNED = false>
 __device__ __forceinline__ void heun_step_df(const StepArgs &a, long long q[3], df V[3],
                                              double tau, int img[3], int &bad,
                                              const FieldBox &box = FieldBox{},
                                              StageTimes tt = StageTimes{0.0, 0.0}) {
   const Geom &g = a.geo;
-  const df dt = {a.dfk[0], a.dfk[1]}, cx = {a.dfk[4], a.dfk[5]};
-  const df hcx = df_scale2(cx, 0.5f);  // (dt/2) N/L
-  const df h = df_mul(dt, df_recip(split_d(tau)));
+  const df cx = {a.dfk[4], a.dfk[5]};  // dt N/L
+  const df h = df_mul(df{a.dfk[0], a.dfk[1]}, df_recip(split_d(tau)));
   long long q2[3];
-  df U[3], hD1[3], Vs[3], D[3];
+  df U[3], Vs[3], Vh[3];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) q2[s] = fix_stage2(q[s], V[s], cx);
   if (OWNED && !brick_holds(box, q)) bad |= 2;
   interp_any<KIND, OWNED>(a.field, g.N, q, U, box);
   if (EVOLVE && a.field_b) lerp_field_df<KIND, OWNED>(a, q, tt.th1, U, box);
 #pragma unroll
-  for (int s = 0; s < 3; ++s) D[s] = df_add(U[s], df_neg(V[s]));
-  const df h1 = a.drag ? df_mul(h, drag_factor_df(a.drag_c, tau, D)) : h;
+  for (int s = 0; s < 3; ++s) U[s] = df_add(U[s], df_neg(V[s]));  // D1
+  const df h1 = a.drag ? df_mul(h, drag_factor_df(a.drag_c, tau, U)) : h;
+  const float half_box = 0.5f * (float)g.N;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     const df gd = {a.dfk[6 + 2 * s], a.dfk[7 + 2 * s]};
-    hD1[s] = df_mul(h1, D[s]);
-    Vs[s] = df_add(df_add(V[s], hD1[s]), gd);
-    q2[s] = fix_stage2(q[s], V[s], cx);
+    const df a1 = df_add(df_mul(h1, U[s]), gd);
+    Vs[s] = df_add(V[s], a1);
+    Vh[s] = df_add(V[s], df_scale2(a1, 0.5f));
+    const df dXc = df_mul(cx, Vh[s]);  // displacement in cell units
+    if (!(fabsf(dXc.h) < half_box)) bad |= isfinite(dXc.h) ? 2 : 1;
+    q[s] = wrap_fix(q[s] + f_to_fix52_cvt(dXc.h) + f_to_fix52_cvt(dXc.l), g.qL, img[s]);
   }
   if (OWNED && !brick_holds(box, q2)) bad |= 2;
   interp_any<KIND, OWNED>(a.field, g.N, q2, U, box);
   if (EVOLVE && a.field_b) lerp_field_df<KIND, OWNED>(a, q2, tt.th2, U, box);
 #pragma unroll
-  for (int s = 0; s < 3; ++s) D[s] = df_add(U[s], df_neg(Vs[s]));
-  const df h2 = a.drag ? df_mul(h, drag_factor_df(a.drag_c, tau, D)) : h;
-  const float half_box = 0.5f * (float)g.N;
+  for (int s = 0; s < 3; ++s) U[s] = df_add(U[s], df_neg(Vs[s]));  // D2
+  const df h2 = a.drag ? df_mul(h, drag_factor_df(a.drag_c, tau, U)) : h;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     const df gd = {a.dfk[6 + 2 * s], a.dfk[7 + 2 * s]};
-    const df hD2 = df_mul(h2, D[s]);
-    const df dV = df_add(df_scale2(df_add(hD1[s], hD2), 0.5f), gd);
-    // displacement in cell units: (dt N/L) V + (dt/2 N/L)(h1 D1 + dt g)
-    const df dXc = df_add(df_mul(cx, V[s]), df_mul(hcx, df_add(hD1[s], gd)));
-    const df vn = df_add(V[s], dV);
-    if (!(fabsf(dXc.h) < half_box)) bad |= isfinite(dXc.h) ? 2 : 1;
+    const df a2 = df_add(df_mul(h2, U[s]), gd);
+    const df vn = df_add(Vh[s], df_scale2(a2, 0.5f));
     if (!isfinite(vn.h)) bad |= 1;
-    q[s] = wrap_fix(q[s] + f_to_fix52_cvt(dXc.h) + f_to_fix52_cvt(dXc.l), g.qL, img[s]);
     V[s] = vn;
   }
 }
@@ -435,19 +438,23 @@ __device__ __forceinline__ void heun_step_lo(const StepArgs &a, long long q[3], 
   const float h = dt * __frcp_rn(taus);
   long long q2[3];
   df U[3];
-  float hD1[3], Vs[3], D[3];
+  float a1[3], Vs[3], D[3];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) q2[s] = fix_stage2_lo(q[s], V[s].h, cx);
   if (OWNED && !brick_holds(box, q)) bad |= 2;
   interp_lo<KIND, OWNED>(a.field, g.N, q, U, box);
   if (EVOLVE && a.field_b) lerp_field_lo<KIND, OWNED>(a, q, (float)tt.th1, U, box);
 #pragma unroll
   for (int s = 0; s < 3; ++s) D[s] = U[s].h - V[s].h;
   const float h1 = a.drag ? h * drag_factor_f32((float)a.drag_c, taus, D) : h;
+  const float half_box = 0.5f * (float)g.N;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
-    const float gd = a.dfk[6 + 2 * s];
-    hD1[s] = h1 * D[s];
-    Vs[s] = V[s].h + hD1[s] + gd;
-    q2[s] = fix_stage2_lo(q[s], V[s].h, cx);
+    a1[s] = h1 * D[s] + a.dfk[6 + 2 * s];
+    Vs[s] = V[s].h + a1[s];
+    const float dXc = cx * (V[s].h + 0.5f * a1[s]);  // cell units
+    if (!(fabsf(dXc) < half_box)) bad |= isfinite(dXc) ? 2 : 1;
+    q[s] = wrap_fix(q[s] + f_to_fix52(dXc), g.qL, img[s]);
   }
   if (OWNED && !brick_holds(box, q2)) bad |= 2;
   interp_lo<KIND, OWNED>(a.field, g.N, q2, U, box);
@@ -455,17 +462,11 @@ __device__ __forceinline__ void heun_step_lo(const StepArgs &a, long long q[3], 
 #pragma unroll
   for (int s = 0; s < 3; ++s) D[s] = U[s].h - Vs[s];
   const float h2 = a.drag ? h * drag_factor_f32((float)a.drag_c, taus, D) : h;
-  const float half_box = 0.5f * (float)g.N;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
-    const float gd = a.dfk[6 + 2 * s];
-    const float hD2 = h2 * D[s];
-    const float dV = 0.5f * (hD1[s] + hD2) + gd;
-    const float dXc = cx * (V[s].h + 0.5f * (hD1[s] + gd));  // cell units
-    const df vn = df_add(V[s], df{dV, 0.f});
-    if (!(fabsf(dXc) < half_box)) bad |= isfinite(dXc) ? 2 : 1;
+    const float a2 = h2 * D[s] + a.dfk[6 + 2 * s];
+    const df vn = df_add(V[s], df{0.5f * (a1[s] + a2), 0.f});
     if (!isfinite(vn.h)) bad |= 1;
-    q[s] = wrap_fix(q[s] + f_to_fix52(dXc), g.qL, img[s]);
     V[s] = vn;
   }
 }

@@ -111,6 +111,17 @@ __device__ __forceinline__ void load_rec(const Rec &R, int64_t i, long long x[3]
   id = R.id[i];
 }
 
+// The part of a record the integration needs: position, velocity, tau_p.
+__device__ __forceinline__ void load_motion(const Rec &R, int64_t i, long long x[3], df v[3],
+                                            double &tau, double tau_c) {
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    x[s] = R.x[s][i];
+    v[s] = df_from2(R.v[s][i]);
+  }
+  tau = R.tau ? R.tau[i] : tau_c;
+}
+
 __device__ __forceinline__ void store_rec(const Rec &R, int64_t i, const long long x[3],
                                           const df v[3], double tau, uint32_t id,
                                           const int img[3]) {
@@ -190,6 +201,53 @@ __device__ __forceinline__ TileMeta tile_meta(const StepArgs &a, int gtile, int 
   m.o8 = (int)(g0 & 1);
   m.o4 = (int)(g0 & 3);
   return m;
+}
+
+// The same placement computed by one whole warp and written to shared
+// memory, so the other warps of the block hold none of it in registers.
+// The segment of the tile is the number of segments s < P whose first tile
+// tile_off[s] is at most `tile`, minus one (tile_off is non-decreasing, so
+// those segments form a prefix): every lane counts a slice of tile_off
+// with independent loads, one warp sum adds the slices.
+template <int T>
+__device__ __forceinline__ void tile_meta_warp(const StepArgs &a, int gtile, int e, int tile,
+                                               TileMeta &out) {
+  const int lane = threadIdx.x & 31;
+  const int P = a.geo.Ptot;
+  const int *off = a.m.tile_off;
+  int c = 0;
+  for (int s0 = 0; s0 < P; s0 += 128) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int s = s0 + 32 * k + lane;
+      c += (s < P && __ldg(off + s) <= tile) ? 1 : 0;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) {
+    TileMeta m;
+    m.gtile = gtile;
+    m.e = e;
+    m.tile = tile;
+    m.ph = *a.m.phase;
+    m.seg = max(c - 1, 0);
+    const int P0 = a.geo.P[0], P1 = a.geo.P[1];
+    m.ps[0] = m.seg % P0;
+    m.ps[1] = (m.seg / P0) % P1;
+    m.ps[2] = m.seg / (P0 * P1);
+    m.t0 = off[m.seg];
+    m.ntile = off[m.seg + 1] - m.t0;
+    m.cnt = a.m.cnt[m.seg];
+    m.bA = a.m.lay_base[m.ph][m.seg];
+    m.first = (int64_t)(tile - m.t0) * T;
+    const int64_t rem = m.cnt - m.first;
+    m.n = (int)(rem < 0 ? 0 : (rem > T ? T : rem));
+    const int64_t g0 = m.bA + m.first;
+    m.o8 = (int)(g0 & 1);
+    m.o4 = (int)(g0 & 3);
+    out = m;
+  }
 }
 
 // Prefetched records of one tile in shared memory: rows x0 x1 x2 v0 v1 v2
@@ -543,7 +601,11 @@ __device__ __forceinline__ unsigned integrate_items(const StepArgs &a, const Til
   for (int k = 0; k < ITEMS; ++k) {
     bin[k] = -2;
     if (l0 + k < mt.cnt) {
-      load_rec(A, mt.bA + l0 + k, x[k], v[k], tau[k], id[k], img[k], a.tau_const);
+      // id, tau_p and the image counts are read again after the integration
+      // (reload_rest), so that they hold no registers across the gathers;
+      // img counts the images crossed in this step until then
+      load_motion(A, mt.bA + l0 + k, x[k], v[k], tau[k], a.tau_const);
+      img[k][0] = img[k][1] = img[k][2] = 0;
       if (STAGE == 0) {
         if (KIND == FK_F64) heun_step64<EVOLVE>(a, x[k], v[k], tau[k], img[k], bad, tt);
         else if (KIND == FK_DF)
@@ -584,6 +646,26 @@ __device__ __forceinline__ unsigned integrate_items(const StepArgs &a, const Til
   return packed;
 }
 
+// The rest of the integrated records: id and tau_p as stored, image counts
+// as stored plus the images crossed in this step.
+template <int ITEMS>
+__device__ __forceinline__ void reload_rest(const StepArgs &a, const TileMeta &mt,
+                                            double tau[], uint32_t id[], int img[][3],
+                                            const int bin[]) {
+  const Rec &A = a.buf[mt.ph];
+  const int64_t i0 = mt.bA + mt.first + (int64_t)threadIdx.x * ITEMS;
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k) {
+    if (bin[k] == -2) continue;
+    id[k] = A.id[i0 + k];
+    if (A.tau) tau[k] = A.tau[i0 + k];
+    if (A.img[0]) {
+#pragma unroll
+      for (int s = 0; s < 3; ++s) img[k][s] += A.img[s][i0 + k];
+    }
+  }
+}
+
 // Mode 3, deferred scatter: a block integrates its next tile while its
 // previous tile waits, parked in shared memory, for the look-back; by then
 // every predecessor has long published its aggregate, so the look-back does
@@ -594,35 +676,48 @@ template <int KIND, int BLOCK, int ITEMS, int CAP, bool EVOLVE, int STAGE, bool 
 __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockShared &sh,
                                               const int *s_off, unsigned char *pk) {
   constexpr int T = BLOCK * ITEMS;
-  __shared__ TileMeta s_park;
+  // Placement of the block's tiles, alternating between two slots: the tile
+  // taken in iteration i sits in slot i & 1 and stays there, parked, through
+  // iteration i + 1 (every iteration passes block barriers, so no warp reads
+  // a slot after the next-but-one iteration has started to rewrite it).
+  __shared__ TileMeta s_meta[2];
   __shared__ unsigned s_park_tot;
   const int n = pb.n, total = s_off[n];
   const bool lay_tau = pb.pf_tau != 0, lay_img = pb.pf_img != 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   bool parked = false;
   if (threadIdx.x < NBIN) sh.hist[threadIdx.x] = 0;
-  for (;;) {
-    if (threadIdx.x == 0) sh.tile = (int)atomicAdd(pb.counter, 1u);
+  for (int it = 0;; ++it) {
+    TileMeta &cur = s_meta[it & 1];
+    if (warp == 0) {
+      int g = 0;
+      if (lane == 0) g = (int)atomicAdd(pb.counter, 1u);
+      g = __shfl_sync(0xffffffffu, g, 0);
+      if (g < total) {
+        const int e = CAP == 1 ? 0 : find_ensemble(s_off, n, g);
+        tile_meta_warp<T>(pb.a[e], g, e, g - s_off[e], cur);
+      } else if (lane == 0) {
+        cur.gtile = g;
+      }
+    }
     __syncthreads();
-    const int g = sh.tile;
-    const bool fresh = g < total;
+    const bool fresh = cur.gtile < total;
     long long x[ITEMS][3];
-  df v[ITEMS][3];
-  double tau[ITEMS];
+    df v[ITEMS][3];
+    double tau[ITEMS];
     uint32_t id[ITEMS];
     int img[ITEMS][3], bin[ITEMS];
     df vs[ITEMS][3];
     unsigned packed = 0;
-    TileMeta m;
     if (fresh) {
-      const int e = CAP == 1 ? 0 : find_ensemble(s_off, n, g);
-      m = tile_meta<T>(pb.a[e], g, e, g - s_off[e]);
-      packed = integrate_items<KIND, ITEMS, EVOLVE, STAGE, OWNED>(pb.a[e], m, sh, x, v, tau, id,
-                                                                  img, bin, vs);
+      const int e = CAP == 1 ? 0 : cur.e;
+      packed = integrate_items<KIND, ITEMS, EVOLVE, STAGE, OWNED>(pb.a[e], cur, sh, x, v, tau,
+                                                                  id, img, bin, vs);
+      reload_rest<ITEMS>(pb.a[e], cur, tau, id, img, bin);
     }
     if (parked) {
-      const TileMeta pm = s_park;
-      const StepArgs &pa = pb.a[pm.e];
+      const TileMeta &pm = s_meta[(it - 1) & 1];
+      const StepArgs &pa = pb.a[CAP == 1 ? 0 : pm.e];
       const unsigned tot = s_park_tot;
       if (warp == 0) {
         const unsigned long long agg = pack_sm(tot >> 16, tot & 0xffffu);
@@ -648,8 +743,9 @@ __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockSha
         if (stay0 + j < cB) park_get<T>(pk, lay_tau, lay_img, j, B, bB + stay0 + j, nullptr);
         else latch(pa.m.status, LCS_ERR_CAPACITY);
       }
+      const int64_t bA = pm.bA;
       for (int j = threadIdx.x; j < nmig; j += BLOCK)
-        park_get<T>(pk, lay_tau, lay_img, T - 1 - j, pa.pack, pm.bA + mig0 + j, pa.pack_bin);
+        park_get<T>(pk, lay_tau, lay_img, T - 1 - j, pa.pack, bA + mig0 + j, pa.pack_bin);
       __syncthreads();
     }
     if (!fresh) break;
@@ -673,22 +769,21 @@ __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockSha
       if (lane < BLOCK / 32) sh.warp[lane] = wi - wv;
       if (lane == BLOCK / 32 - 1) {
         sh.tot = wi;
-        const StepArgs &a = pb.a[m.e];
-        publish_aggregate(a.m.tile_status, m.tile, m.t0, pack_sm(wi >> 16, wi & 0xffffu));
-        s_park = m;
+        const StepArgs &a = pb.a[CAP == 1 ? 0 : cur.e];
+        publish_aggregate(a.m.tile_status, cur.tile, cur.t0, pack_sm(wi >> 16, wi & 0xffffu));
         s_park_tot = wi;
       }
     }
     __syncthreads();
-    const StepArgs &a = pb.a[m.e];
+    const StepArgs &a = pb.a[CAP == 1 ? 0 : cur.e];
     if (threadIdx.x < NBIN) {
       if (threadIdx.x != BIN_STAY && sh.hist[threadIdx.x])
-        atomicAdd(&a.m.bincnt[m.seg * NBIN + threadIdx.x], sh.hist[threadIdx.x]);
+        atomicAdd(&a.m.bincnt[cur.seg * NBIN + threadIdx.x], sh.hist[threadIdx.x]);
       sh.hist[threadIdx.x] = 0;
     }
     const unsigned excl = incl - packed + sh.warp[warp];
     int rs = (int)(excl >> 16), rm = (int)(excl & 0xffffu);
-    const Rec &A = a.buf[m.ph];
+    const Rec &A = a.buf[cur.ph];
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
       if (bin[k] == -2) continue;
@@ -705,9 +800,14 @@ __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockSha
 // Resident threads per SM asked of the compiler (so registers per thread,
 // measured): 512 for the all-FP64 kernel (128 registers), 768 for the
 // float-float kernel with two particles per thread (80), 1024 otherwise (64).
+#ifndef LCS_DF1_THREADS
+#define LCS_DF1_THREADS 1024
+#endif
 template <int KIND, int BLOCK, int ITEMS>
 constexpr int step_min_blocks() {
-  return KIND == FK_F64 ? 512 / BLOCK : (KIND == FK_DF && ITEMS == 2 ? 768 : 1024) / BLOCK;
+  return KIND == FK_F64 ? 512 / BLOCK
+         : KIND == FK_DF ? (ITEMS == 2 ? 768 : LCS_DF1_THREADS) / BLOCK
+                         : 1024 / BLOCK;
 }
 
 constexpr long long PF_WAIT_LIMIT = 1LL << 20;  // bounded wait for a tile's bulk copies
