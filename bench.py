@@ -78,11 +78,12 @@ def library_source_hash() -> str:
     return h.hexdigest()
 
 
-def measured_traffic(workload: str, field: str, kernel: str, n: int, cfg):
-    """DRAM bytes per step-kernel launch from the committed ncu capture, or
-    None when no capture matches this run or the kernels changed since."""
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles",
-                        "step_traffic.json")
+def measured_counters(workload: str, field: str, kernel: str, n: int, cfg):
+    """Counters of one step-kernel launch from the committed ncu captures
+    (profiles/step_counters.json): DRAM bytes per launch, warp instructions
+    and FP64-pipe warp instructions per particle update.  None when no
+    capture matches this run or the step-kernel sources changed since."""
+    path = os.path.join(ROOT, "profiles", "step_counters.json")
     try:
         with open(path) as fh:
             rec = json.load(fh)
@@ -91,10 +92,58 @@ def measured_traffic(workload: str, field: str, kernel: str, n: int, cfg):
     if rec.get("source_sha256") != library_source_hash():
         return None
     for e in rec.get("entries", []):
-        if (e["workload"], e["field"], e["kernel"], e["particles"], list(e["step_config"])) == \
-                (workload, field, kernel, n, list(cfg)):
-            return e["dram_bytes_per_launch"]
+        if (e["workload"], e["field"], e["kernel"], list(e["step_config"])) == \
+                (workload, field, kernel, list(cfg)):
+            out = dict(e)
+            # DRAM bytes scale with the particle count of the run (the field
+            # term is fixed): per-update and field parts as captured
+            if e.get("particles") != n and "dram_bytes_per_update" not in e:
+                out.pop("dram_bytes_per_launch", None)
+            return out
     return None
+
+
+def step_roofline(workload, field, kernel, n, N, has_tau, cfg, prof, hbm_peak, peak_kind, clk,
+                  sms):
+    """Roofline of the step kernel: algorithmic bytes per launch (every record
+    read and written once, every field value read once) over its mean
+    CUDA-event duration, against the measured HBM copy bandwidth; beside it
+    the instruction-issue ceiling (warp instructions per update from the ncu
+    capture, at the SM clock sampled during the timed region)."""
+    step_ms, step_n = prof["step"]
+    rec_bytes = 48 + (8 if has_tau else 0) + 4
+    field_bytes_cell = {"f64": 24, "f32": 12, "bf16": 6}[field]
+    alg = n * 2 * rec_bytes + field_bytes_cell * N ** 3
+    t = step_ms / step_n * 1e-3
+    achieved = alg / t / 1e9
+    cnt = measured_counters(workload, field, kernel, n, cfg) or {}
+    traffic = cnt.get("dram_bytes_per_launch")
+    if traffic is None and "dram_bytes_per_update" in cnt:
+        traffic = int(cnt["dram_bytes_per_update"] * n + cnt.get("dram_field_bytes", 0))
+    r = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+         "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
+         "algorithmic_bytes": int(alg), "kernel": "k_step", "peak_source": peak_kind,
+         "kernel_ms_per_launch": round(step_ms / step_n, 4),
+         "kernel_share": round(step_ms / sum(p[0] for p in prof.values()), 3)}
+    wipu = cnt.get("warp_inst_per_update")
+    if wipu:
+        mhz = (clk or {}).get("sm_mhz") or 2070.0
+        peak_issue = sms * 4 * mhz * 1e6  # one warp instruction per scheduler per cycle
+        ach = wipu * n / t
+        r["issue"] = {"bound": "issue", "achieved": round(ach / 1e12, 4),
+                      "peak": round(peak_issue / 1e12, 4), "unit": "T warp-instructions/s",
+                      "frac": round(ach / peak_issue, 4), "warp_inst_per_update": wipu,
+                      "peak_source": f"{sms} SMs x 4 schedulers x {mhz:.0f} MHz sampled"}
+    f64pu = cnt.get("fp64_warp_inst_per_update")
+    if f64pu:
+        peak_f64 = 0.625e12 / 32  # nominal 1.25 TFLOP/s = 0.625 T FMA lanes/s, in warp instructions
+        ach = f64pu * n / t
+        r["fp64_pipe"] = {"bound": "alu", "achieved": round(ach * 32 / 1e12, 4),
+                          "peak": 0.625, "unit": "T FP64 lane-instructions/s",
+                          "frac": round(ach / peak_f64, 4),
+                          "fp64_warp_inst_per_update": f64pu,
+                          "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (FMA = 2 FLOP)"}
+    return r
 
 
 # ---------------------------------------------------------------- ranks
@@ -167,18 +216,71 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- CPU oracle leg
 
-def oracle_rate(w, field_np, dt, x, v, tau, n_sample: int, steps: int):
-    """Particle-updates/s of the CPU oracle (single thread) on a sample."""
+def cpu_info():
+    """(cores the OS reports, CPU model string) of this machine."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        import platform
+        model = platform.processor() or platform.machine()
+    return os.cpu_count(), model
+
+
+def oracle_rate(w, field_np, dt, x, v, tau, n_sample: int, steps: int, threads=None,
+                migrate=True):
+    """Particle-updates/s of the CPU oracle on the first n_sample particles:
+    threads None = the plain single-threaded oracle, else its OpenMP build
+    (particle loop on `threads` cores, 0 = all; migration and sort stay
+    sequential).  migrate=False times the particle advance alone (the
+    sampled-ID form of the precision workload).  Returns (rate, seconds,
+    threads used) or None when the OpenMP build is unavailable."""
     import oracle
-    L = synth.L_BOX
-    xs, vs = x[:, :n_sample].copy(), v[:, :n_sample].copy()
-    ts = None if tau is None else tau[:n_sample].copy()
-    st = oracle.initial_state(w.N, L, w.sub, xs, vs, ts)
-    t0 = time.perf_counter()
-    oracle.run(st, field_np, L, w.sub, w.tau_const, dt, w.g, steps,
-               sort_every=w.sort_every, brick=8)
-    t = time.perf_counter() - t0
-    return n_sample * steps / t, t
+    used = oracle.use_threads(threads)
+    if used is None:
+        return None
+    try:
+        L = synth.L_BOX
+        xs, vs = x[:, :n_sample].copy(), v[:, :n_sample].copy()
+        ts = None if tau is None else tau[:n_sample].copy()
+        if migrate:
+            st = oracle.initial_state(w.N, L, w.sub, xs, vs, ts)
+            t0 = time.perf_counter()
+            oracle.run(st, field_np, L, w.sub, w.tau_const, dt, w.g, steps,
+                       sort_every=w.sort_every, brick=8)
+        else:
+            t0 = time.perf_counter()
+            oracle.advance(field_np, L, xs, vs, ts, w.tau_const, dt, w.g, steps)
+        t = time.perf_counter() - t0
+    finally:
+        oracle.use_threads(None)
+    return n_sample * steps / t, t, used
+
+
+def cpu_baseline_leg(w, field_np, dt, x, v, tau, n_sample, steps, migrate=True, what=""):
+    """The oracle timed single-threaded (the baseline proper, as it stands)
+    and on all host cores (OpenMP build), with the core count and CPU model."""
+    nproc, model = cpu_info()
+    one = oracle_rate(w, field_np, dt, x, v, tau, n_sample, steps, None, migrate)
+    rate, secs, _ = one
+    out = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{what}first {n_sample} particles of the workload, {steps} steps"
+                     f"{' incl. migration and the cell sort' if migrate else ' (advance only)'}"
+                     f", {secs:.1f} s", "nproc": nproc, "cpu_model": model}
+    many = oracle_rate(w, field_np, dt, x, v, tau, n_sample, steps, 0, migrate)
+    if many is not None:
+        r2, s2, used = many
+        out["all_cores"] = {"value": r2, "unit": UNIT, "cores": used,
+                            "sample": f"same sample, OpenMP over particles, {s2:.1f} s"}
+    else:
+        out["all_cores"] = None
+    return out
 
 
 # ---------------------------------------------------------------- adjoint
@@ -267,17 +369,85 @@ def batch_throughput(lcs, torch, steps=500, n_ens=48):
             "tuned_block": block, "tuned_items": items, "tuned_mode": mode, "unit": UNIT}
 
 
+# ---------------------------------------------------------------- end to end
+
+def e2e_leg(sim, torch, n, has_tau, steps, dist=None):
+    """The same metric through the public API with host buffers: every bench
+    step copies the state in from pinned host memory (lcs_set_state), runs 10
+    time steps and copies it back (lcs_get_state)."""
+    stream = torch.cuda.current_stream()
+    st_host = sim.get_state(device="cpu")
+    h2d = n * (24 + 24 + (8 if has_tau else 0) + 4) + 8 * (len(st_host["seg"]))
+    d2h = h2d
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        sim.set_state(st_host["x"], st_host["v"], st_host["ids"], st_host["seg"],
+                      tau=st_host["tau"] if has_tau else None)
+        sim.step(STEPS_PER_BENCH_STEP)
+        st_host = sim.get_state(device="cpu", out={k: st_host[k] for k in
+                                                   ("x", "v", "tau", "ids")})
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e_ms, e_units = aggregate_over_ranks(e0.elapsed_time(e1), n * STEPS_PER_BENCH_STEP * steps,
+                                         dist, "cuda")
+    return {"value": e_units / (e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "steps": steps,
+            "wall_s": round(time.perf_counter() - t0, 3)}
+
+
+def timed_rate(sim, torch, n, steps):
+    """Particle-updates/s over `steps` time steps (CUDA events on the stream)."""
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    sim.step(steps)
+    e1.record(st)
+    sim.sync()
+    return n * steps / (e0.elapsed_time(e1) * 1e-3)
+
+
+# ---------------------------------------------------------------- all-FP64 kernel
+
+def fp64_kernel_leg(lcs, torch, args, w, field, dt, x, v, tau, hbm_peak, peak_kind, clk):
+    """The bench workload with the all-FP64-arithmetic step kernel
+    (LCS_KERNEL_FP64: the paper's arithmetic, every operation on the FP64
+    pipe), deferred scatter with one particle per thread."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sim = lcs.Simulator(field, x, v, dt, tau=tau, tau_const=w.tau_const, g=w.g, sub=w.sub,
+                        field_dtype="f64", kernel="fp64", sort_every=w.sort_every)
+    cfg = (256, 1, 3)
+    sim.set_step_config(*cfg)
+    sim.step(STEPS_PER_BENCH_STEP)
+    sim.sync()
+    n = x.shape[1]
+    rate = timed_rate(sim, torch, n, 2 * STEPS_PER_BENCH_STEP)
+    prof = sim.profile_steps(STEPS_PER_BENCH_STEP)
+    sim.close()
+    return {"value": rate, "unit": UNIT, "steps": 2 * STEPS_PER_BENCH_STEP,
+            "config": f"{w.name}, LCS_KERNEL_FP64 (all arithmetic FP64), step config "
+                      f"{list(cfg)}",
+            "roofline": step_roofline(w.name, "f64", "fp64", n, w.N, tau is not None, cfg,
+                                      prof, hbm_peak, peak_kind, clk, sms)}
+
+
 # ---------------------------------------------------------------- precision variants
 
-def precision_throughput(lcs, torch, steps=20):
+def precision_throughput(lcs, torch, hbm_peak, peak_kind, clk, steps=20, cpu=True):
     """The precision workload (512^3 field, 10^8 particles, 8x8x8, gravity,
     sort every 10): particle-updates/s with the field stored in FP64
-    (float-float kernel), FP32 and BF16, and the FP32-over-FP64 speedup."""
+    (float-float kernel), FP32 and BF16, the FP32-over-FP64 speedup, and for
+    each the step kernel's roofline; for the FP64 field also the end-to-end
+    rate through the API with host buffers and the CPU oracle on the 10^5-ID
+    subsample of the precision test (advance only: particles are independent)."""
     w = synth.WORKLOADS["precision_512"]
     field, _ = synth.make_field(w, device="cuda")
     dt = synth.cfl_dt(synth.max_speed(field), w.N)
     x, v, tau = synth.make_particles(w, dt)
-    st = torch.cuda.current_stream()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     out = {"workload": "precision_512 (512^3, 1e8 particles, 8x8x8, sort every 10)",
            "steps": steps, "unit": UNIT}
     for dtype in ("f64", "f32", "bf16"):
@@ -285,16 +455,25 @@ def precision_throughput(lcs, torch, steps=20):
                             sort_every=w.sort_every)
         sim.step(10)
         sim.sync()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        sim.step(steps)
-        e1.record(st)
-        sim.sync()
-        out[dtype] = w.np_ * steps / (e0.elapsed_time(e1) * 1e-3)
+        out[dtype] = timed_rate(sim, torch, w.np_, steps)
+        prof = sim.profile_steps(STEPS_PER_BENCH_STEP)
+        cfg = (256, 1, 3) if dtype == "f64" else (256, 2, 3)
+        out[f"{dtype}_roofline"] = step_roofline(w.name, dtype, "auto", w.np_, w.N, True, cfg,
+                                                 prof, hbm_peak, peak_kind, clk, sms)
+        if dtype == "f64":
+            out["f64_e2e"] = e2e_leg(sim, torch, w.np_, True, 2)
         sim.close()
         torch.cuda.empty_cache()
     out["f32_speedup_vs_f64"] = round(out["f32"] / out["f64"], 3)
     out["bf16_speedup_vs_f64"] = round(out["bf16"] / out["f64"], 3)
+    if cpu:
+        sample = np.sort(np.random.default_rng(700).choice(w.np_, 100_000, replace=False))
+        out["f64_cpu_baseline"] = cpu_baseline_leg(
+            w, field.cpu().numpy(), dt, np.ascontiguousarray(x[:, sample]),
+            np.ascontiguousarray(v[:, sample]), tau[sample].copy(), 100_000, 20, migrate=False,
+            what="the 10^5 sampled ids of the precision test: ")
+    del field
+    torch.cuda.empty_cache()
     return out
 
 
@@ -382,6 +561,10 @@ def main():
                     help="threads,items,mode of the step kernel instead of autotuning")
     ap.add_argument("--np", type=int, default=0,
                     help="particle count override (small profiling cases only)")
+    ap.add_argument("--reps", type=int, default=5,
+                    help="timed repetitions of K bench steps (the median is reported)")
+    ap.add_argument("--fp64-kernel", type=int, default=1,
+                    help="also time the all-FP64-arithmetic step kernel (LCS_KERNEL_FP64)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -404,7 +587,7 @@ def main():
     sim = lcs.Simulator(field, x, v, dt, tau=tau, tau_const=w.tau_const, g=w.g, sub=w.sub,
                         field_dtype=args.field, kernel=args.kernel, sort_every=w.sort_every)
     n = x.shape[1]
-    K, W = args.steps, args.warmup
+    K, W, R = args.steps, args.warmup, max(1, args.reps)
     if args.step_config:
         tuned = tuple(int(t) for t in args.step_config.split(","))
         sim.set_step_config(*tuned)
@@ -417,71 +600,47 @@ def main():
         sim.step(STEPS_PER_BENCH_STEP)
     sim.sync()
     stream = torch.cuda.current_stream()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(torch.cuda.current_device())
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
     clocks.start()
     l0 = sim.launches
-    ev0.record(stream)
-    for _ in range(K):
-        sim.step(STEPS_PER_BENCH_STEP)
-    ev1.record(stream)
-    ev1.synchronize()
-    sim.sync()
-    torch.cuda.synchronize()
-    launches = sim.launches - l0
+    reps_ms = []
+    for _ in range(R):  # R repetitions of exactly K bench steps; the median is reported
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(K):
+            sim.step(STEPS_PER_BENCH_STEP)
+        ev1.record(stream)
+        ev1.synchronize()
+        sim.sync()
+        torch.cuda.synchronize()
+        ms_r, updates = aggregate_over_ranks(ev0.elapsed_time(ev1), n * STEPS_PER_BENCH_STEP * K,
+                                             dist, "cuda")
+        reps_ms.append(ms_r)
+    launches = (sim.launches - l0) // R
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    ms, updates = aggregate_over_ranks(ms, n * STEPS_PER_BENCH_STEP * K, dist, "cuda")
+    ms = float(np.median(reps_ms))
     value = updates / (ms * 1e-3)
 
     # per-kernel device time (un-graphed replay of one sort period, events
     # around every kernel class on the launching stream)
     prof = sim.profile_steps(STEPS_PER_BENCH_STEP)
-    step_ms, step_n = prof["step"]
     hbm_peak, peak_kind, peaks = load_peaks()
-    N = w.N
-    rec_bytes = 48 + (8 if tau is not None else 0) + 4
-    field_bytes_cell = {"f64": 24, "f32": 12, "bf16": 6}[args.field]
-    # algorithmic bytes of one step-kernel launch: every record read and
-    # written once, every field value read once
-    alg_bytes = n * 2 * rec_bytes + field_bytes_cell * N ** 3
-    achieved = alg_bytes / (step_ms / step_n * 1e-3) / 1e9
-    traffic = measured_traffic(args.workload, args.field, args.kernel, n, tuned)
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
-                "algorithmic_bytes": int(alg_bytes),
-                "kernel": "k_step", "peak_source": peak_kind,
-                "kernel_ms_per_launch": round(step_ms / step_n, 4),
-                "kernel_share": round(step_ms / sum(p[0] for p in prof.values()), 3)}
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    roofline = step_roofline(args.workload, args.field, args.kernel, n, w.N, tau is not None,
+                             tuned, prof, hbm_peak, peak_kind, clk, sms)
 
     # end to end through the public API with host buffers
     e2e = None
     if args.e2e_steps > 0:
-        st_host = sim.get_state(device="cpu")
-        h2d = n * (24 + 24 + (8 if tau is not None else 0) + 4) + 8 * (len(st_host["seg"]))
-        d2h = h2d
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.e2e_steps):
-            sim.set_state(st_host["x"], st_host["v"], st_host["ids"], st_host["seg"],
-                          tau=st_host["tau"] if tau is not None else None)
-            sim.step(STEPS_PER_BENCH_STEP)
-            st_host = sim.get_state(device="cpu", out={k: st_host[k] for k in
-                                                       ("x", "v", "tau", "ids")})
-        e1.record(stream)
-        torch.cuda.synchronize()
-        e_ms, e_units = aggregate_over_ranks(e0.elapsed_time(e1),
-                                             n * STEPS_PER_BENCH_STEP * args.e2e_steps, dist,
-                                             "cuda")
-        e2e = {"value": e_units / (e_ms * 1e-3),
-               "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "wall_s": round(time.perf_counter() - t0, 3)}
+        e2e = e2e_leg(sim, torch, n, tau is not None, args.e2e_steps, dist)
 
+    fp64_kernel = None
+    if rank == 0 and args.fp64_kernel and args.field == "f64" and args.kernel == "auto":
+        fp64_kernel = fp64_kernel_leg(lcs, torch, args, w, field, dt, x, v, tau, hbm_peak,
+                                      peak_kind, clk)
     adjoint = None
     if rank == 0 and args.adjoint:
         adjoint = adjoint_ratio(lcs, torch)
@@ -490,7 +649,8 @@ def main():
         batch = batch_throughput(lcs, torch)
     precision = None
     if rank == 0 and args.precision:
-        precision = precision_throughput(lcs, torch)
+        precision = precision_throughput(lcs, torch, hbm_peak, peak_kind, clk,
+                                         cpu=not args.no_cpu_baseline)
     variants = None
     if rank == 0 and args.variants:
         variants = variants_throughput(lcs, torch, w, field, dt, x, v, tau)
@@ -499,29 +659,36 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         field_np = field.cpu().numpy() if args.field == "f64" else None
         if field_np is not None:
-            steps_cpu = STEPS_PER_BENCH_STEP
             xs, vs = x, v
-            rate, secs = oracle_rate(w, field_np, dt, xs, vs, tau, args.cpu_sample, steps_cpu)
-            cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"first {args.cpu_sample} particles of the workload, "
-                             f"{steps_cpu} steps incl. migration and one sort, {secs:.1f} s"}
+            cpu = cpu_baseline_leg(w, field_np, dt, xs, vs, tau, min(args.cpu_sample, n),
+                                   STEPS_PER_BENCH_STEP)
 
     sim.close()
     if rank == 0:
+        arith = {"f64": "float-float (FP32 pairs, 48-bit) on int64 fixed-point positions",
+                 "f32": "FP32 field and increments on int64 fixed-point positions",
+                 "bf16": "BF16 field, FP32 increments on int64 fixed-point positions"}
+        if args.kernel == "fp64":
+            arith["f64"] = "FP64"
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
                "warmup": W, "ms_per_step": ms / K, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.field == "f64"
-               else args.field, "data": "synthetic",
-               "config": {"workload": w.name, "grid": f"{N}^3", "modes": w.M,
+               "scaling": "weak", "vs_baseline": None,
+               "dtype": "f64" if args.kernel == "fp64" else
+                        {"f64": "f32x2+i64", "f32": "f32+i64", "bf16": "bf16/f32+i64"}[args.field],
+               "data": "synthetic",
+               "config": {"workload": w.name, "grid": f"{w.N}^3", "modes": w.M,
                           "particles_per_gpu": n, "subdomains": "x".join(map(str, w.sub)),
                           "sort_every": w.sort_every, "dt": dt,
                           "time_steps_per_bench_step": STEPS_PER_BENCH_STEP,
                           "field_storage": args.field, "kernel": args.kernel,
+                          "arithmetic": arith[args.field],
                           "tuned_block_items_mode": list(tuned),
                           "tune_trials_ms": [round(float(t), 3) for t in sim.tune_trials_ms],
+                          "repetitions": R, "reps_ms": [round(t, 3) for t in reps_ms],
                           "l2": "inputs larger than L2 (state ~1 GB, field 0.54 GB)",
                           "parallelism": f"replicas{world}"},
-               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "adjoint": adjoint, "batch": batch,
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+               "fp64_kernel": fp64_kernel, "adjoint": adjoint, "batch": batch,
                "precision": precision, "model_variants": variants,
                "gpu_launches": int(launches), "clocks": clk,
                "kernel_profile_ms": {k: round(v_[0], 4) for k, v_ in prof.items()}}
@@ -550,6 +717,7 @@ def run_reference(args, world, rank):
         done += STEPS_PER_BENCH_STEP
     t = time.perf_counter() - t0
     value = n * done / t
+    nproc, model = cpu_info()
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -559,7 +727,8 @@ def run_reference(args, world, rank):
                       "dt": dt, "time_steps_per_bench_step": STEPS_PER_BENCH_STEP},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": f"first {n} particles of the workload (bounded sample), "
-                                      f"{done} time steps"},
+                                      f"{done} time steps", "nproc": nproc,
+                            "cpu_model": model},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out))

@@ -79,8 +79,12 @@ typedef enum {
   LCS_KERNEL_AUTO = 0,   /* library choice: LCS_KERNEL_DF for LCS_F64 */
   LCS_KERNEL_FP64 = 1,   /* FP64 field, all arithmetic in FP64 */
   LCS_KERNEL_DF = 2      /* FP64 field stored as an unevaluated float pair
-                            (hi + lo, 48 significant bits); interpolation in
-                            float-float arithmetic, integration in FP64 */
+                            (hi + lo, 48 significant bits); interpolation and
+                            the Heun increments in float-float arithmetic
+                            (error-free FP32 transformations), added exactly
+                            to the fixed-point positions and in float-float to
+                            the velocity pairs: no FP64 instruction on the
+                            Stokes path */
 } lcs_kernel;
 
 typedef enum {
@@ -92,14 +96,16 @@ typedef enum {
 
 /* One ensemble: a field, its particles and its parameters. */
 typedef struct {
-  int n;                  /* grid points per axis N (the grid is N^3), >= 2 */
+  int n;                  /* grid points per axis N (the grid is N^3), 2 <= N <= 1024
+                             (the fixed-point positions hold N 2^52 < 2^63) */
   double box;             /* side L of the periodic cube (> 0) */
   int sub[3];             /* virtual subdomains (Px, Py, Pz); N % P_s == 0 */
-  int64_t np;             /* number of particles, >= 0 */
+  int64_t np;             /* number of particles, 0 <= np < 2^31 */
   lcs_dtype field_dtype;  /* storage precision of the library's field copy */
   lcs_kernel field_kernel;/* arithmetic of the step for LCS_F64 */
   const double *field;    /* device [3][N][N][N]; read during lcs_init only */
-  const double *x0;       /* device [3][np] positions, each in [0, L) */
+  const double *x0;       /* device [3][np] finite positions; values outside
+                             [0, L) are folded into the box (see lcs_init) */
   const double *v0;       /* device [3][np] velocities */
   const double *tau;      /* device [np] relaxation times tau_p > 0, or NULL */
   double tau_const;       /* tau_p of every particle when tau == NULL */
@@ -149,9 +155,15 @@ typedef struct {
  * particles into library-owned device memory, converts the field into the
  * library's layout and precision, and places every particle in the segment
  * of its subdomain: the particles of a subdomain keep the order in which
- * they were given (a stable partition by subdomain).  Validates N % P_s,
- * tau_p >= dt, positions inside [0, L) (LCS_ERR_ARG otherwise).  On success
- * *out owns all device memory until lcs_destroy. */
+ * they were given (a stable partition by subdomain).  A position outside
+ * [0, L) is folded into the periodic box (Sec. 2.1): x - k L with
+ * k = floor(x / L), one rounding, moved by one more image if that rounding
+ * lands on L or below 0; with track_images, k starts the particle's image
+ * count, so unwrapped positions read back (lcs_get_state_by_id) continue
+ * from the positions given.  Validates 2 <= N <= 1024, 0 <= np < 2^31,
+ * N % P_s == 0, P <= 4096, tau_p >= dt, finite positions no more than 2^30
+ * boxes away (LCS_ERR_ARG otherwise).  On success *out owns all device
+ * memory until lcs_destroy. */
 lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out);
 
 /* Enqueue nsteps time steps (asynchronous).  One step of every ensemble:
@@ -180,7 +192,8 @@ lcs_status lcs_sort(lcs_ctx *ctx);
  * created with per-particle tau_p and ignored otherwise; img ([3][np]
  * int32) may be NULL (zeros).  seg (host, Ptot+1 int64) gives
  * the segments; particles need not lie in their segment's subdomain until
- * the next lcs_migrate.  Synchronising. */
+ * the next lcs_migrate.  Positions outside [0, L) are folded as in lcs_init,
+ * the folds added to img.  Synchronising. */
 lcs_status lcs_set_state(lcs_ctx *ctx, int ens, const double *x, const double *v,
                          const double *tau, const uint32_t *ids, const int32_t *img,
                          const int64_t *seg);
@@ -191,6 +204,19 @@ lcs_status lcs_set_state(lcs_ctx *ctx, int ens, const double *x, const double *v
  * Synchronising; returns the latched device status. */
 lcs_status lcs_get_state(lcs_ctx *ctx, int ens, double *x, double *v, double *tau,
                          uint32_t *ids, int32_t *img, int64_t *seg);
+
+/* Copy the current particles of ensemble `ens` ordered by particle id
+ * (ascending; equal ids keep their storage order).  Pointers are "any" and
+ * may be NULL to skip an array: x and v are [3][np], ids [np] receives the
+ * ids in that order.  With track_images the positions are unwrapped,
+ * RN(x + RN(L img)) with img the periodic images crossed since the
+ * positions were given (lcs_init / lcs_set_state, including the folds of
+ * positions given outside the box); without, they are the positions in
+ * [0, L) that lcs_get_state returns.  This is the final state X_T, V_T of
+ * the problem statement (Sec. 2.2) in the order the particles were given
+ * (ids NULL at lcs_init numbers them 0..np-1).  Synchronising; returns the
+ * latched device status. */
+lcs_status lcs_get_state_by_id(lcs_ctx *ctx, int ens, double *x, double *v, uint32_t *ids);
 
 /* Copy the field as the kernels of ensemble `ens` see it (after rounding to
  * the storage precision), expanded to FP64 [3][N][N][N] ("any" pointer).
@@ -341,8 +367,10 @@ lcs_status lcs_partition(const uint32_t *keys, int64_t n, int nbins, uint32_t *p
  * Limits: n <= LCS_PARTITION_NOALLOC_MAX_N (larger n returns LCS_ERR_ARG
  * before any work is enqueued), 1 <= nbins <= 65536.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture on that device.  All calls share the one array, so two
+ * (cudaGetSymbolAddress) and caches it with the id of the device's current
+ * context; a call in a different context (after cudaDeviceReset, say) looks
+ * it up again.  Make the first call on a device, and the first call after
+ * such a change, before any stream capture on that device.  All calls share the one array, so two
  * calls that may run at the same time on the GPU (different streams without
  * ordering, or different host threads) race and corrupt each other's
  * results; order them on one stream.  The paper has no counterpart of this

@@ -23,29 +23,55 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lcs_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liblcs_oracle.so")
+_SO_OMP = os.path.join(_BUILD, "liblcs_oracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_omp = False  # load the OpenMP build (timed CPU baseline on all cores)
 
 ORC_OK, ORC_ERR_DISPLACEMENT, ORC_ERR_ARG, ORC_ERR_NOMEM = 0, 1, 2, 3
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle shared library (idempotent); returns its path."""
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle shared library (idempotent); returns its path.
+    openmp: the same source built with -fopenmp (the particle loop of
+    orc_advance on all cores; identical arithmetic per particle)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
-        tmp = _SO + f".{os.getpid()}.tmp"
+    so = _SO_OMP if openmp else _SO
+    if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(_SRC):
+        tmp = so + f".{os.getpid()}.tmp"
+        extra = ["-fopenmp"] if openmp else []
         subprocess.check_call(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _SO)
-    return _SO
+                               *extra, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, so)
+    return so
+
+
+def use_threads(n: int | None):
+    """Select the build the following calls use: n = None the plain
+    single-threaded oracle, else the OpenMP build with n threads (0: all
+    cores).  Returns the threads the particle loop uses, or None when the
+    OpenMP build is not available on this machine."""
+    global _lib, _omp
+    with _lock:
+        want = n is not None
+        if want:
+            try:
+                build(openmp=True)
+            except (OSError, subprocess.CalledProcessError):
+                return None
+        if want != _omp:
+            _lib, _omp = None, want
+    lib = _load()
+    lib.orc_threads.argtypes = [C.c_int]
+    lib.orc_threads.restype = C.c_int
+    return int(lib.orc_threads(int(n or 0))) if want else 1
 
 
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            lib = C.CDLL(_SO)
+            lib = C.CDLL(build(openmp=_omp))
             P = C.c_void_p
             i64, i32, dbl = C.c_int64, C.c_int, C.c_double
             lib.orc_interp_many.argtypes = [P, i32, dbl, i64, P, P, P, P, P, P]

@@ -38,7 +38,7 @@ EXPORTS = ("lcs_init", "lcs_step", "lcs_migrate", "lcs_sort", "lcs_set_state", "
            "lcs_get_field", "lcs_backward", "lcs_sync", "lcs_last_error", "lcs_destroy",
            "lcs_launch_count", "lcs_partition", "lcs_profile_steps", "lcs_partition_noalloc",
            "lcs_tune", "lcs_set_step_config", "lcs_staged_tiles", "lcs_set_field",
-           "lcs_pair_histogram", "lcs_selftest_waits")
+           "lcs_pair_histogram", "lcs_selftest_waits", "lcs_get_state_by_id")
 PARTITION_NOALLOC_MAX_N = 1 << 20
 DRAGS = {"stokes": 0, "nonlinear": 1}  # lcs_drag: f = 1, or the factor of Eq. (7)
 PROF_CLASSES = ("step", "finish", "unpack", "flip", "sort")
@@ -80,6 +80,7 @@ def lib():
         L.lcs_sort.argtypes = [P]
         L.lcs_set_state.argtypes = [P, i32, P, P, P, P, P, P]
         L.lcs_get_state.argtypes = [P, i32, P, P, P, P, P, P]
+        L.lcs_get_state_by_id.argtypes = [P, i32, P, P, P]
         L.lcs_get_field.argtypes = [P, i32, P]
         L.lcs_backward.argtypes = [P, P, P, P, P, P]
         L.lcs_sync.argtypes = [P]
@@ -102,7 +103,7 @@ def lib():
                      "lcs_get_state", "lcs_get_field", "lcs_backward", "lcs_sync",
                      "lcs_partition", "lcs_profile_steps", "lcs_partition_noalloc", "lcs_tune",
                      "lcs_set_step_config", "lcs_staged_tiles", "lcs_set_field",
-                     "lcs_pair_histogram", "lcs_selftest_waits"):
+                     "lcs_pair_histogram", "lcs_selftest_waits", "lcs_get_state_by_id"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -335,14 +336,20 @@ class Simulator:
         self._check(lib().lcs_set_state(self._ctx, ens, _ptr(xs), _ptr(vs), _ptr(tt), _ptr(ii),
                                         _ptr(im), _ptr(seg)))
 
-    def final_state_by_id(self, ens: int = 0):
-        """(X, V) as (3, np) CUDA tensors in particle-id order, X unwrapped (x + L img)."""
+    def final_state_by_id(self, ens: int = 0, device: str = "cuda", ids: bool = False):
+        """(X, V) as (3, np) tensors in particle-id order (lcs_get_state_by_id):
+        X unwrapped across the periodic boundary when images are tracked.
+        With ids=True also the sorted ids."""
         import torch
-        st = self.get_state(ens=ens)
-        order = torch.argsort(st["ids"].long())
-        box = self.meta[ens]["box"]
-        x = st["x"][:, order] + box * st["img"][:, order].to(torch.float64)
-        return x, st["v"][:, order]
+        n = self.meta[ens]["np"]
+        kw = dict(device=device)
+        if device == "cpu":
+            kw["pin_memory"] = torch.cuda.is_available()
+        x = torch.empty((3, n), dtype=torch.float64, **kw)
+        v = torch.empty((3, n), dtype=torch.float64, **kw)
+        i = torch.empty(n, dtype=torch.int32, **kw) if ids else None
+        self._check(lib().lcs_get_state_by_id(self._ctx, ens, _ptr(x), _ptr(v), _ptr(i)))
+        return (x, v, i) if ids else (x, v)
 
     def backward(self, gx, gv, gU=None):
         """Adjoint of the recorded steps (lcs_backward).
@@ -407,27 +414,22 @@ def _autograd_function():
     class ParticleAdvect(torch.autograd.Function):
         """(U, X0, V0) -> (X_T unwrapped, V_T) after `steps` steps, differentiable.
 
-        U: [3,N,N,N] FP64 field; X0, V0: (3, np) in particle-id order (X0 may lie
-        outside [0, L): it is wrapped on entry and the image shift is added back
-        to X_T).  The backward pass is the library's hand-written adjoint
-        (lcs_backward) with checkpoints every `ckpt_every` steps."""
+        U: [3,N,N,N] FP64 field; X0, V0: (3, np) in particle-id order.  X0 may
+        lie outside [0, L): the library folds it into the box and counts the
+        folds as periodic images, so X_T comes back unwrapped relative to X0.
+        The backward pass is the library's hand-written adjoint (lcs_backward)
+        with checkpoints every `ckpt_every` steps."""
 
         @staticmethod
         def forward(ctx, U, X0, V0, opts):
-            box = float(opts.get("box", 2 * math.pi))
-            x0 = X0.detach().to(torch.float64)
-            shift = torch.floor(x0 / box)
-            xw = x0 - box * shift
-            xw = torch.where(xw >= box, xw - box, xw)
-            xw = torch.where(xw < 0, torch.zeros_like(xw), xw)
             kw = {k: v for k, v in opts.items() if k not in ("steps",)}
             kw.setdefault("ckpt_every", 20)
             kw["track_images"] = True
-            sim = Simulator(U.detach(), xw, V0.detach(), **kw)
+            sim = Simulator(U.detach(), X0.detach(), V0.detach(), **kw)
             sim.step(int(opts["steps"]))
             xt, vt = sim.final_state_by_id()
             ctx.sim = sim
-            return xt + box * shift.to(xt.device), vt
+            return xt, vt
 
         @staticmethod
         def backward(ctx, gX, gV):

@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs p) {
 // ---------------------------------------------------------------- launchers
 
 cudaError_t launch_tape_store(const StepArgs &a, const TapeSlot &t, int64_t np, cudaStream_t st) {
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((np + 255) / 256, 152 * 8));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((np + 255) / 256, device_sms() * 8));
   k_tape_store<<<grid, 256, 0, st>>>(a, t, np);
   return cudaGetLastError();
 }
@@ -383,7 +383,7 @@ cudaError_t launch_recompute(const StepArgs &a, FieldKind kind, const TapeSlot &
 
 cudaError_t launch_lam_permute(const uint32_t *id, const double *src, double *dst, int64_t np,
                                int to_storage, int *status, cudaStream_t st) {
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((np + 255) / 256, 152 * 8));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((np + 255) / 256, device_sms() * 8));
   k_lam_permute<<<grid, 256, 0, st>>>(id, src, dst, np, to_storage, status);
   return cudaGetLastError();
 }

@@ -30,6 +30,8 @@ __global__ void k_iota(uint32_t *p, const int64_t *cstart, int P);
 __global__ void k_compact(StepArgs a, Rec out);
 __global__ void k_import(Rec R, int64_t n, Geom g, int *status);
 __global__ void k_export(Rec R, int64_t n, Geom g);
+__global__ void k_id_keys(Rec R, int64_t n, uint32_t *key, uint32_t *pay);
+__global__ void k_by_id(Rec S, const uint32_t *pay, int64_t n, Rec D, double L);
 __global__ void k_partition_in(const uint32_t *keys, int64_t n, uint32_t nbins, uint32_t *k,
                                uint32_t *p, int32_t *status);
 __global__ void k_partition_tables(int64_t n, int64_t *cs1, int *to1, int32_t *status);
@@ -59,6 +61,7 @@ struct Ens {
   int64_t *cs1 = nullptr;
   int *to1 = nullptr;
   int64_t steps = 0;
+  int id_bits = 32;  // key width of the id sort (ceil log2 np for the default ids)
   // adjoint tape: checkpoint k holds the state after k*ckpt_every steps
   std::vector<TapeSlot> tape;
   bool tape_ok = false;
@@ -78,7 +81,7 @@ struct lcs_ctx {
   // captured step graphs, keyed by which ensembles sort after that step
   std::map<std::vector<bool>, cudaGraphExec_t> graphs;
   int64_t launches = 0;
-  int sms = 152;
+  int sms = 0;  // streaming multiprocessors of the context's device
   // batched step over all ensembles (one launch per kernel per step)
   FieldKind kind = FK_F64;
   int mode = 0;  // step kernel: 0 plain, 1 staged field box, 2 prefetched records, 3 deferred
@@ -515,9 +518,7 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
     delete c;
     return LCS_ERR_CUDA;
   }
-  int dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
+  c->sms = device_sms();
   c->ens.resize(n_ens);
   lcs_status r = LCS_OK;
   for (int k = 0; k < n_ens && r == LCS_OK; ++k) {
@@ -722,6 +723,7 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
     C2(cudaMallocAsync((void **)&seg_dev, sizeof(int64_t) * (P + 1), st));
     C2(cudaMemcpyAsync(seg_dev, seg.data(), sizeof(int64_t) * (P + 1), cudaMemcpyHostToDevice, st));
     k_input_meta<<<1, 1024, 0, st>>>(e.a, seg_dev);
+    e.id_bits = d.ids ? 32 : std::max(1, ceil_log2(e.np));
     if (d.ids && e.np > 0) {
       C2(cudaMemcpyAsync(B1.id, d.ids, e.np * 4, cudaMemcpyDefault, st));
     } else {
@@ -901,6 +903,42 @@ lcs_status lcs_get_state(lcs_ctx *c, int ens, double *x, double *v, double *tau,
   }
   if (ids && e.np > 0) CK(cudaMemcpyAsync(ids, tmp.id, e.np * 4, cudaMemcpyDefault, st));
   if (seg) CK(cudaMemcpyAsync(seg, e.a.m.cstart, sizeof(int64_t) * (P + 1), cudaMemcpyDefault, st));
+  CK(cudaStreamSynchronize(st));
+  return read_status(c);
+}
+
+lcs_status lcs_get_state_by_id(lcs_ctx *c, int ens, double *x, double *v, uint32_t *ids) {
+  NvtxRange nvtx_range("lcs_get_state_by_id");
+  if (!c) return LCS_ERR_ARG;
+  if (c->failed) return LCS_ERR_STATE;
+  if (ens < 0 || ens >= (int)c->ens.size()) return reject(c, "bad ensemble");
+  Ens &e = c->ens[ens];
+  cudaStream_t st = c->st;
+  if (e.np > 0) {
+    // the output buffer of the next step is free between steps: it stages
+    // the id-ordered rows (the input buffer is the one the phase names)
+    int ph = 0;
+    CK(cudaMemcpyAsync(&ph, e.a.m.phase, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    Rec tmp = e.a.pack, out = e.a.buf[ph ^ 1];
+    const int gs = grid_for(e.np, 256, c->sms * 8);
+    k_compact<<<gs, 256, 0, st>>>(e.a, tmp);
+    k_export<<<gs, 256, 0, st>>>(tmp, e.np, e.a.geo);
+    k_id_keys<<<gs, 256, 0, st>>>(tmp, e.np, e.s.key[0], e.s.pay[0]);
+    k_one_segment<<<1, 1, 0, st>>>(e.a.m.cstart, e.a.geo.Ptot, e.cs1, e.to1);
+    SortArgs s = e.s;
+    s.nseg = 1, s.cstart = e.cs1, s.tile_off = e.to1;
+    int ob = 0;
+    CK(radix_sort(s, e.id_bits, &ob, st, &c->launches));
+    k_by_id<<<gs, 256, 0, st>>>(tmp, s.pay[ob], e.np, out, e.a.geo.L);
+    c->launches += 5;
+    CK(cudaGetLastError());
+    for (int q = 0; q < 3; ++q) {
+      if (x) CK(cudaMemcpyAsync(x + q * e.np, out.x[q], e.np * 8, cudaMemcpyDefault, st));
+      if (v) CK(cudaMemcpyAsync(v + q * e.np, out.v[q], e.np * 8, cudaMemcpyDefault, st));
+    }
+    if (ids) CK(cudaMemcpyAsync(ids, out.id, e.np * 4, cudaMemcpyDefault, st));
+  }
   CK(cudaStreamSynchronize(st));
   return read_status(c);
 }
@@ -1215,7 +1253,7 @@ lcs_status lcs_partition(const uint32_t *keys, int64_t n, int nbins, uint32_t *p
   int *to1 = (int *)take(8);
   s.nseg = 1, s.cstart = cs1, s.tile_off = to1, s.max_tiles = max_tiles;
   (void)take(0);
-  const int gs = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
+  const int gs = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, device_sms() * 8));
   k_partition_tables<<<1, 1, 0, st>>>(n, cs1, to1, status);
   if (n > 0) k_partition_in<<<gs, 256, 0, st>>>(keys, n, (uint32_t)nbins, s.key[0], s.pay[0], status);
   int ob = 0;

@@ -277,6 +277,10 @@ __device__ __forceinline__ void layout_from_counts(int P, int step_tile, const i
   }
 }
 
+// Streaming multiprocessors of the current device (queried once per device
+// and cached; grids of the grid-stride kernels are sized from it).
+int device_sms();
+
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_field_convert(const double *src, int N, FieldKind kind, void *dst,
                                  cudaStream_t st);

@@ -13,10 +13,14 @@
 // (about 13.6 MB), sized for n <= LCS_PARTITION_NOALLOC_MAX_N keys.  Every
 // GPU that loads the library holds it until the process exits.  Host code
 // must not pass the array's name to a kernel (on the host it is only a
-// stand-in symbol); the device address is obtained once per device with
-// cudaGetSymbolAddress, during the first call on that device.
+// stand-in symbol); the device address is obtained with cudaGetSymbolAddress
+// during the first call on a device, and again whenever that device's
+// current context has changed since (after cudaDeviceReset the module is
+// loaded anew and the array may sit elsewhere).
 #include <algorithm>
 #include <mutex>
+
+#include <cuda.h>  // CUcontext / CUresult types; the functions come through the runtime
 
 #include "lcs_internal.cuh"
 
@@ -53,19 +57,56 @@ __device__ __align__(256) unsigned char g_scratch[NOALLOC_BYTES];
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mutex;
 void *g_scratch_addr[MAX_DEVICES] = {};
+unsigned long long g_scratch_ctx[MAX_DEVICES] = {};  // context id the address belongs to
 
-// Device address of g_scratch on the current device (set up once per device).
+using CtxGetCurrent = CUresult (*)(CUcontext *);
+using CtxGetId = CUresult (*)(CUcontext, unsigned long long *);
+
+// Unique id of the calling thread's current context (cuCtxGetId, reached
+// through the runtime's driver entry points; ids are never reused within a
+// process), or 0 if it cannot be read.  Call with g_mutex held.
+unsigned long long current_context_id() {
+  static CtxGetCurrent get_current = nullptr;
+  static CtxGetId get_id = nullptr;
+  static bool resolved = false;
+  if (!resolved) {
+    resolved = true;
+    void *f = nullptr, *g = nullptr;
+    cudaDriverEntryPointQueryResult q1{}, q2{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q1) ==
+            cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &g, 12000, cudaEnableDefault, &q2) ==
+            cudaSuccess &&
+        q2 == cudaDriverEntryPointSuccess) {
+      get_current = (CtxGetCurrent)f;
+      get_id = (CtxGetId)g;
+    }
+  }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx ||
+      get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
+
+// Device address of g_scratch in the current device's current context:
+// looked up on the first call on a device and again when the context has
+// changed since (or its id cannot be read).
 cudaError_t scratch_address(void **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_addr[dev]) {
+  const unsigned long long ctx = current_context_id();
+  if (!g_scratch_addr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_scratch);
     if (e != cudaSuccess) return e;
     g_scratch_addr[dev] = p;
+    g_scratch_ctx[dev] = current_context_id();  // the lookup may have created the context
   }
   *out = g_scratch_addr[dev];
   return cudaSuccess;
@@ -103,7 +144,7 @@ extern "C" lcs_status lcs_partition_noalloc(const uint32_t *keys, int64_t n, int
   s.max_tiles = (int)(n / SORT_TILE + 2);
   // Nothing in the scratch needs to start at zero: the tables, histograms,
   // scans and key/payload buffers are fully written before they are read.
-  const int gs = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
+  const int gs = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, device_sms() * 8));
   k_partition_tables<<<1, 1, 0, st>>>(n, cs1, to1, status);
   if (n > 0) k_partition_in<<<gs, 256, 0, st>>>(keys, n, (uint32_t)nbins, s.key[0], s.pay[0], status);
   int ob = 0;

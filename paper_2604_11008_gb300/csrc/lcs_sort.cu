@@ -252,7 +252,7 @@ cudaError_t radix_sort(const SortArgs &s, int bits, int *out_buf, cudaStream_t s
   if (bits > 0) {
     const int passes = (bits + SORT_MAX_BITS - 1) / SORT_MAX_BITS;
     const int b = (bits + passes - 1) / passes;
-    const int grid = max(1, min(s.max_tiles, 152 * 8));
+    const int grid = max(1, min(s.max_tiles, device_sms() * 8));
     const int64_t maxn = (int64_t)s.max_tiles * SORT_MAX_D;
     const int sgrid = (int)((maxn + SCAN_CHUNK - 1) / SCAN_CHUNK);
     for (int p = 0, shift = 0; p < passes; ++p, shift += b) {
@@ -497,19 +497,41 @@ __global__ void k_compact(StepArgs a, Rec out) {
 // The C ABI's FP64 state <-> the records' fixed-point positions and
 // float-pair velocities, in place on the first n records of R (the FP64
 // values occupy the same 8-byte slots).
-//   import: q = RN(x N/L) 2^52 exactly (the product has at most 53 bits, of
-//           which at least 42 are fraction bits for N <= 1024); a position
-//           outside [0, L) or non-finite latches LCS_ERR_ARG; a product that
-//           rounds up to N maps to the last fixed-point value below N, so
-//           that the cell is min(floor(x N/L), N-1) as before;
+//   import: a position outside [0, L) is first folded into the periodic box
+//           (Sec. 2.1): x' = x - k L with k = floor(x / L), one FMA rounding,
+//           a result below 0 or at L moved by one more image; k is added to
+//           the particle's image count when images are tracked.  A
+//           non-finite position, or one more than 2^30 boxes away, latches
+//           LCS_ERR_ARG.  Then q = RN(x' N/L) 2^52 exactly (the product has at
+//           most 53 bits, of which at least 42 are fraction bits for
+//           N <= 1024); a product that rounds up to N maps to the last
+//           fixed-point value below N, so that the cell is
+//           min(floor(x' N/L), N-1);
 //           v -> (RN32(v), RN32(v - hi)) (a non-finite velocity is reported
 //           as LCS_ERR_NONFINITE by the next step).
 //   export: x = RN(RN(q) L/N 2^-52), kept below L; v = hi + lo exactly.
-__device__ __forceinline__ unsigned long long import_pos(double x, const Geom &g, int *status) {
-  if (!(x >= 0.0 && x < g.L)) {
+__device__ __forceinline__ double fold_pos(double x, double L, int &img, int *status) {
+  if (x >= 0.0 && x < L) return x;
+  double k = floor(x / L);
+  if (!(fabs(k) < 1073741824.0)) {  // also catches NaN and infinities
     latch(status, LCS_ERR_ARG);
-    return 0ull;
+    return 0.0;
   }
+  double y = fma(-k, L, x);
+  if (y < 0.0) {
+    y += L;
+    k -= 1.0;
+  }
+  if (y >= L) {
+    y -= L;
+    k += 1.0;
+  }
+  if (!(y >= 0.0 && y < L)) y = 0.0;  // not reached for finite x; keeps q in range
+  img += (int)k;
+  return y;
+}
+
+__device__ __forceinline__ unsigned long long import_pos(double x, const Geom &g) {
   long long q = d_to_fix52(__dmul_rn(x, g.inv_dx));
   if (q >= g.qL) q = g.qL - 1;
   return (unsigned long long)q;
@@ -520,8 +542,11 @@ __global__ void k_import(Rec R, int64_t n, Geom g, int *status) {
        i += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
-      const double x = __longlong_as_double((long long)R.x[s][i]);
-      R.x[s][i] = (int64_t)import_pos(x, g, status);
+      int img = R.img[s] ? R.img[s][i] : 0;
+      const double x =
+          fold_pos(__longlong_as_double((long long)R.x[s][i]), g.L, img, status);
+      if (R.img[s]) R.img[s][i] = img;
+      R.x[s][i] = (int64_t)import_pos(x, g);
       const double v = __longlong_as_double(*(const long long *)&R.v[s][i]);
       const float h = __double2float_rn(v);  // non-finite values surface in the next step
       R.v[s][i] = make_float2(h, __double2float_rn(v - (double)h));
@@ -538,6 +563,35 @@ __global__ void k_export(Rec R, int64_t n, Geom g) {
       const float2 p = R.v[s][i];
       *(double *)&R.v[s][i] = (double)p.x + (double)p.y;
     }
+  }
+}
+
+// Sort keys of the id-ordered export: the ids of the compacted records,
+// with their positions as payload.
+__global__ void k_id_keys(Rec R, int64_t n, uint32_t *key, uint32_t *pay) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    key[i] = R.id[i];
+    pay[i] = (uint32_t)i;
+  }
+}
+
+// Id-ordered export: record r of D is record pay[r] of the exported
+// (FP64) records S; with images, the position is unwrapped, x + L img (in
+// FP64: RN(x + RN(L img))).  D's position and velocity rows receive FP64
+// values, its id row the ids.
+__global__ void k_by_id(Rec S, const uint32_t *pay, int64_t n, Rec D, double L) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = pay[r];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      double x = __longlong_as_double((long long)S.x[s][i]);
+      if (S.img[s]) x = __dadd_rn(x, __dmul_rn(L, (double)S.img[s][i]));
+      D.x[s][r] = __double_as_longlong(x);
+      D.v[s][r] = S.v[s][i];
+    }
+    D.id[r] = S.id[i];
   }
 }
 

@@ -14,10 +14,25 @@
 //   Sec. 3.2.2: unpack = compaction of the stayers plus appending the
 //     arrivals, ordered by source subdomain.
 #include <algorithm>
+#include <atomic>
 
 #include "lcs_physics.cuh"
 
 namespace lcs {
+
+// ---------------------------------------------------------------- device
+
+int device_sms() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  int n = cache[dev].load(std::memory_order_relaxed);
+  if (n > 0) return n;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+    return 1;
+  cache[dev].store(n, std::memory_order_relaxed);
+  return n;
+}
 
 // ---------------------------------------------------------------- field
 
@@ -102,7 +117,7 @@ __global__ void k_field_expand(const void *src, int64_t ncell, int kind, double 
 cudaError_t launch_field_convert(const double *src, int N, FieldKind kind, void *dst,
                                  cudaStream_t st) {
   const int64_t ncell = (int64_t)N * N * N;
-  const int grid = (int)std::min<int64_t>((ncell + 255) / 256, 152 * 32);
+  const int grid = (int)std::min<int64_t>((ncell + 255) / 256, device_sms() * 32);
   k_field_convert<<<grid, 256, 0, st>>>(src, ncell, (int)kind, dst);
   return cudaGetLastError();
 }
@@ -143,7 +158,7 @@ __global__ void k_build_bricks(const unsigned char *field, Geom g, int cb, unsig
 cudaError_t launch_build_bricks(const void *field, const Geom &g, FieldKind kind, void *bricks,
                                 cudaStream_t st) {
   const int64_t total = (int64_t)(g.W[0] + 4) * (g.W[1] + 4) * (g.W[2] + 4) * g.Ptot;
-  const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
+  const int grid = (int)std::min<int64_t>((total + 255) / 256, device_sms() * 32);
   k_build_bricks<<<std::max(grid, 1), 256, 0, st>>>((const unsigned char *)field, g,
                                                     cell_bytes(kind), (unsigned char *)bricks);
   return cudaGetLastError();
@@ -152,7 +167,7 @@ cudaError_t launch_build_bricks(const void *field, const Geom &g, FieldKind kind
 cudaError_t launch_field_expand(const void *src, int N, FieldKind kind, double *dst,
                                 cudaStream_t st) {
   const int64_t ncell = (int64_t)N * N * N;
-  const int grid = (int)std::min<int64_t>((ncell + 255) / 256, 152 * 32);
+  const int grid = (int)std::min<int64_t>((ncell + 255) / 256, device_sms() * 32);
   k_field_expand<<<grid, 256, 0, st>>>(src, ncell, (int)kind, dst);
   return cudaGetLastError();
 }

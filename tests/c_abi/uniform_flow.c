@@ -3,6 +3,10 @@
  * (Eqs. 5-6 with U - V = 0 and no gravity), so after n steps of dt every
  * particle sits at X0 + n dt U0, unwrapped with its periodic image counts,
  * while it has migrated between the 2x2x2 subdomains and been cell-sorted.
+ * Some particles are released in other periodic images of the box (the
+ * library folds them in and counts the folds as images).  The final state is
+ * read twice: in storage order (lcs_get_state, with image counts) and in
+ * particle-id order, unwrapped (lcs_get_state_by_id).
  * Exit status 0 and "ok" on success. */
 #include <math.h>
 #include <stdint.h>
@@ -41,7 +45,8 @@ int main(void) {
   for (int c = 0; c < 3; ++c) {
     for (size_t i = 0; i < ncell; ++i) field[c * ncell + i] = U0[c];
     for (int64_t p = 0; p < np; ++p) {
-      x0[c * np + p] = L * uniform01(&seed);
+      /* images -2 .. 2 of the box by particle index */
+      x0[c * np + p] = L * uniform01(&seed) + L * (double)((p + c) % 5 - 2);
       v0[c * np + p] = U0[c];
     }
   }
@@ -100,9 +105,25 @@ int main(void) {
       ev = fmax(ev, fabs(v[c * np + i] - U0[c]));
     }
   }
+  /* the same final state in particle-id order, unwrapped */
+  double *xi = malloc(3 * (size_t)np * sizeof(double));
+  double *vi = malloc(3 * (size_t)np * sizeof(double));
+  uint32_t *idi = malloc((size_t)np * sizeof(uint32_t));
+  CHECK(lcs_get_state_by_id(ctx, 0, xi, vi, idi));
+  for (int64_t p = 0; p < np; ++p) {
+    if (idi[p] != (uint32_t)p) bad |= 16;
+    for (int c = 0; c < 3; ++c) {
+      const double want = x0[c * np + p] + steps * dt * U0[c];
+      ex = fmax(ex, fabs(xi[c * np + p] - want));
+      ev = fmax(ev, fabs(vi[c * np + p] - U0[c]));
+    }
+  }
   if (!(ex < 1e-11)) bad |= 4;
   if (!(ev < 1e-13)) bad |= 8;
   lcs_destroy(ctx);
+  free(xi);
+  free(vi);
+  free(idi);
   cudaFree(d_field);
   cudaFree(d_x0);
   cudaFree(d_v0);

@@ -199,8 +199,8 @@ def test_plain_32_full_trajectory(kernel):
     st = gpu_state(sim)
     ref = oracle.initial_state(w.N, L, w.sub, x, v, None, track_img=True)
     oracle.run(ref, field, L, w.sub, w.tau_const, w.dt, w.g, w.steps)
-    ex, ev, _, _ = traj_errors(st["x"], st["img"], st["v"], st["ids"], ref, x)
-    assert ex < TOL_FP64 and ev < TOL_FP64, (ex, ev)
+    ex, ev, px, pv = traj_errors(st["x"], st["img"], st["v"], st["ids"], ref, x)
+    assert max(ex, ev, px, pv) < TOL_FP64, (ex, ev, px, pv)
     assert_same_storage(st, ref, w.N, w.sub)
     assert np.array_equal(np.sort(st["ids"]), np.arange(w.np_))
 
@@ -213,8 +213,8 @@ def test_trajectory_with_gravity_and_sort(lcs, P, sort_every, brick, kernel):
     st, ref, x0 = run_pair(lcs, N, 32, 6.0, 20000, P, 0.005, 30, tau_median=0.05,
                            g=(0.0, 0.0, -9.8), sort_every=sort_every, brick=brick, seed=60,
                            kernel=kernel)
-    ex, ev, _, _ = traj_errors(st["x"], st["img"], st["v"], st["ids"], ref, x0)
-    assert ex < TOL_FP64 and ev < TOL_FP64, (ex, ev)
+    ex, ev, px, pv = traj_errors(st["x"], st["img"], st["v"], st["ids"], ref, x0)
+    assert max(ex, ev, px, pv) < TOL_FP64, (ex, ev, px, pv)
     assert_same_storage(st, ref, N, P, brick)
 
 
@@ -289,11 +289,63 @@ def test_invalid_arguments(lcs):
     with pytest.raises(lcs.LcsError) as e:
         make(lcs, field, x, v, 0.5, tau_const=0.1)       # dt > tau
     assert e.value.status == lcs.LCS_ERR_ARG
-    xb = x.copy()
-    xb[1, 3] = L                                         # outside [0, L)
-    with pytest.raises(lcs.LcsError) as e:
-        make(lcs, field, xb, v, 0.01)
-    assert e.value.status == lcs.LCS_ERR_ARG
+    for bad in (np.nan, np.inf, -np.inf, 1e300):         # not a position in any image
+        xb = x.copy()
+        xb[1, 3] = bad
+        with pytest.raises(lcs.LcsError) as e:
+            make(lcs, field, xb, v, 0.01)
+        assert e.value.status == lcs.LCS_ERR_ARG
+
+
+def test_positions_outside_the_box_are_folded(lcs):
+    """Initial positions given in other periodic images (Sec. 2.1) start the
+    same trajectories as their images in [0, L); with images tracked, the
+    id-ordered export returns them unwrapped relative to the positions given."""
+    N, P, dt, steps = 16, (2, 2, 2), 0.01, 20
+    field, _, x, v, _ = synth.small_case(95, N, 16, 4.0, 4000, None, dt=dt)
+    shift = np.random.default_rng(96).integers(-3, 4, size=x.shape).astype(np.float64)
+    xs = x + L * shift
+    xs[0, 0], xs[1, 1], xs[2, 2] = L, -L, 2 * L   # exactly on images of 0
+    x[0, 0], x[1, 1], x[2, 2] = 0.0, 0.0, 0.0
+    shift[0, 0], shift[1, 1], shift[2, 2] = 1.0, -1.0, 2.0
+    a = make(lcs, field, x, v, dt, sub=P, track_images=True, sort_every=5)
+    b = make(lcs, field, xs, v, dt, sub=P, track_images=True, sort_every=5)
+    # the fold x - k L is one FMA rounding away from the image in [0, L)
+    xa0, _ = a.final_state_by_id(device="cpu")
+    xb0, _ = b.final_state_by_id(device="cpu")
+    assert np.abs(xb0.numpy() - xs).max() <= 8 * np.spacing(4 * L)
+    assert np.abs(xa0.numpy() - x).max() <= np.spacing(L)
+    a.step(steps)
+    b.step(steps)
+    xa, va, ia = a.final_state_by_id(device="cpu", ids=True)
+    xb, vb, ib = b.final_state_by_id(device="cpu", ids=True)
+    assert np.array_equal(ia.numpy(), np.arange(4000)) and np.array_equal(ib.numpy(), ia.numpy())
+    dx = np.abs(xb.numpy() - L * shift - xa.numpy()).max()
+    assert dx < 1e-12, dx
+    assert np.abs(vb.numpy() - va.numpy()).max() < 1e-12
+    # the oracle from the folded positions, unwrapped by its own image counts
+    ref = oracle.initial_state(N, L, P, x, v, None, track_img=True)
+    oracle.run(ref, field, L, P, 0.1, dt, (0.0, 0.0, 0.0), steps, sort_every=5, brick=8)
+    xr, vr, ir = by_id(ref.ids, ref.x, ref.v, ref.img)
+    assert np.abs(xa.numpy() - (xr + L * ir)).max() < 1e-12
+    assert np.abs(va.numpy() - vr).max() < 1e-12
+
+
+def test_state_by_id_without_images_and_with_custom_ids(lcs):
+    """Without image tracking the id-ordered export returns the wrapped
+    positions of lcs_get_state; custom ids come back in ascending order."""
+    N, P = 12, (3, 2, 2)
+    field, _, x, v, _ = synth.small_case(97, N, 8, 2.0, 3000, None)
+    ids = np.random.default_rng(98).choice(10 ** 9, 3000, replace=False).astype(np.uint32)
+    sim = lcs.Simulator(field, x, v, 0.01, tau_const=0.1, sub=P, ids=ids.astype(np.int32),
+                        sort_every=2)
+    sim.step(5)
+    st = gpu_state(sim)
+    xb, vb, ib = sim.final_state_by_id(device="cpu", ids=True)
+    order = np.argsort(st["ids"].astype(np.uint32), kind="stable")
+    assert np.array_equal(ib.numpy().astype(np.uint32), np.sort(ids))
+    assert np.array_equal(xb.numpy(), st["x"][:, order])
+    assert np.array_equal(vb.numpy(), st["v"][:, order])
 
 
 # ---------------------------------------------------------------- precision variants
@@ -331,8 +383,8 @@ def test_precision_variant_trajectories(lcs, dtype, tol_q, tol_64):
     for f_ref, tol in ((fq, tol_q), (field, tol_64)):
         ref = oracle.initial_state(N, L, P, x, v, tau, track_img=True)
         oracle.run(ref, f_ref, L, P, 0.0, dt, g, steps)
-        ex, ev, _, _ = traj_errors(st["x"], st["img"], st["v"], st["ids"], ref, x)
-        assert ex < tol and ev < tol, (dtype, ex, ev)
+        ex, ev, px, pv = traj_errors(st["x"], st["img"], st["v"], st["ids"], ref, x)
+        assert max(ex, ev, px, pv) < tol, (dtype, ex, ev, px, pv)
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -358,8 +410,8 @@ def test_positions_on_cell_faces_and_box_edges(lcs, kernel):
     st = gpu_state(sim)
     ref = oracle.initial_state(N, L, P, x, v, None, track_img=True)
     oracle.run(ref, field, L, P, 0.1, dt, (0.0, 0.0, 0.0), steps, sort_every=3, brick=4)
-    ex, ev, _, _ = traj_errors(st["x"], st["img"], st["v"], st["ids"], ref, x)
-    assert ex < TOL_FP64 and ev < TOL_FP64, (ex, ev)
+    ex, ev, px, pv = traj_errors(st["x"], st["img"], st["v"], st["ids"], ref, x)
+    assert max(ex, ev, px, pv) < TOL_FP64, (ex, ev, px, pv)
     assert_same_storage(st, ref, N, P, 4)
 
 

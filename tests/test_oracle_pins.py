@@ -622,3 +622,23 @@ def test_round_bf16_matches_torch_on_float_inputs():
     a = (g.standard_normal(20000) * 10.0 ** g.integers(-20, 20, 20000)).astype(np.float32)
     ref = torch.from_numpy(a).to(torch.bfloat16).to(torch.float64).numpy()
     assert np.array_equal(oracle.round_bf16(a.astype(np.float64)), ref)
+
+
+def test_openmp_build_of_the_oracle_gives_identical_bits():
+    """The all-cores build (OpenMP over particles, used only to time the CPU
+    baseline) computes every particle with the same arithmetic: trajectories,
+    image counts and the migration after them equal the plain build's bit
+    for bit."""
+    field, _, x, v, tau = synth.small_case(9, 16, 8, 3.0, 5000, 0.05, dt=0.01)
+    out = []
+    for threads in (None, 0):
+        if oracle.use_threads(threads) is None:
+            pytest.skip("no OpenMP build on this machine")
+        st = oracle.initial_state(16, L, (2, 2, 2), x, v, tau, track_img=True)
+        oracle.run(st, field, L, (2, 2, 2), 0.0, 0.01, (0.0, 0.0, -9.8), 12, sort_every=5,
+                   brick=4)
+        out.append(st)
+    oracle.use_threads(None)
+    a, b = out
+    for k in ("x", "v", "img", "ids", "seg"):
+        assert np.array_equal(getattr(a, k), getattr(b, k)), k

@@ -44,7 +44,8 @@ def noalloc(torch, lcs, keys_np, nbins):
 def test_noalloc_matches_allocating_partition_on_two_calls(env):
     torch, lcs = env
     g = np.random.default_rng(2024)
-    for n, nbins in ((lcs.PARTITION_NOALLOC_MAX_N, 1000), (77777, 2)):
+    for n, nbins in ((lcs.PARTITION_NOALLOC_MAX_N, 1000), (77777, 2),
+                     (lcs.PARTITION_NOALLOC_MAX_N, 65536), (0, 5), (1, 1)):
         keys = g.integers(0, nbins, n)
         rc, perm, off, status = noalloc(torch, lcs, keys, nbins)
         assert rc == lcs.LCS_OK
