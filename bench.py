@@ -345,9 +345,16 @@ def batch_throughput(lcs, torch, steps=500, n_ens=48):
     spec = lambda e, dtype: dict(field=e["field"], x0=e["x0"], v0=e["v0"], dt=e["dt"],
                                  tau=e["tau"], sub=(2, 2, 2), sort_every=10, field_dtype=dtype)
     sim = lcs.Simulator(None, None, None, None, ensembles=[spec(e, "f32") for e in ens])
-    block, items, mode = sim.tune(2)  # 22 steps: 11 configurations x 2
-    timed(sim, 8)  # graph capture; the timed steps start on a sort period
+    block, items, mode = sim.tune(2)  # 2 steps per tried configuration
+    done = 2 * int((sim.tune_trials_ms > 0).sum())
+    timed(sim, 10 - done % 10)  # graph capture; the timed steps start on a sort period
+    g0 = sim.graph_launches
     ms_batch = timed(sim, steps)
+    graph_launches = sim.graph_launches - g0
+    configs = {}
+    for k in range(len(ens)):
+        key = "x".join(map(str, sim.step_config_of(k)))
+        configs[key] = configs.get(key, 0) + 1
     launches = sim.launches
     sim.close()
     solo = {}
@@ -366,7 +373,9 @@ def batch_throughput(lcs, torch, steps=500, n_ens=48):
             "value_one_by_one_f64": rate(solo["f64"]), "value_one_by_one_f32": rate(solo["f32"]),
             "speedup_vs_one_by_one_f64": round(solo["f64"] / ms_batch, 3),
             "speedup_vs_one_by_one_f32": round(solo["f32"] / ms_batch, 3),
-            "tuned_block": block, "tuned_items": items, "tuned_mode": mode, "unit": UNIT}
+            "tuned_block": block, "tuned_items": items, "tuned_mode": mode,
+            "configs_per_ensemble": configs,
+            "graph_launches_per_step": round(graph_launches / steps, 4), "unit": UNIT}
 
 
 # ---------------------------------------------------------------- end to end

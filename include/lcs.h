@@ -171,8 +171,14 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
  * destination subdomain, and migrate (prefix scan, pack, unpack); after
  * steps whose 1-based count is a multiple of sort_every, sort every
  * subdomain's particles stably by cell.  All ensembles run in the same four
- * persistent kernel launches per step (their tiles share one work counter),
- * recorded once in a CUDA graph and replayed. */
+ * persistent kernel launches per step (their tiles share one work counter).
+ * Runs of consecutive steps are recorded as CUDA graphs and replayed: with a
+ * step period Q (the least common multiple of the ensembles' sort_every and
+ * ckpt_every, stretched to at least 8, at most 64) a run ends at the next
+ * multiple of Q, at a checkpoint step or at the end of the call, so a call
+ * of n steps costs about n / Q graph launches (one per sort period); with
+ * no such period, one graph launch per step.  The first run of each kind is
+ * recorded when it is first needed. */
 lcs_status lcs_step(lcs_ctx *ctx, int64_t nsteps);
 
 /* Standalone migration pass on the current state (asynchronous): a stable
@@ -256,18 +262,16 @@ lcs_status lcs_backward(lcs_ctx *ctx, const double *gx, const double *gv, double
 /* Kernel classes reported by lcs_profile_steps. */
 enum {
   LCS_PROF_STEP = 0,    /* fused interpolate + integrate + scan + pack kernel */
-  LCS_PROF_FINISH = 1,  /* arrival offsets and next layout (one block) */
-  LCS_PROF_UNPACK = 2,  /* placement of the arrivals */
-  LCS_PROF_FLIP = 3,    /* buffer swap (one block) and scan-status reset */
-  LCS_PROF_SORT = 4,    /* the whole cell-sort pass */
-  LCS_PROF_N = 5
+  LCS_PROF_TAIL = 1,    /* step tail: unpack, next layout, buffer swap (one kernel) */
+  LCS_PROF_SORT = 2,    /* the whole cell-sort pass */
+  LCS_PROF_N = 3
 };
 
 /* Tracing: enqueue nsteps steps like lcs_step but without the graph, with
  * a CUDA event pair around every kernel (class) on the context's stream.
  * Synchronising.  ms[k] (host, LCS_PROF_N doubles) receives the summed
  * device time of class k in milliseconds, count[k] (host, may be NULL) the
- * number of launches.  The particle state advances exactly as lcs_step. */
+ * number of timed intervals (for LCS_PROF_STEP: step-kernel launches).  The particle state advances exactly as lcs_step. */
 lcs_status lcs_profile_steps(lcs_ctx *ctx, int64_t nsteps, double *ms, int64_t *count);
 
 /* Step-kernel modes (all give identical results):
@@ -293,29 +297,41 @@ lcs_status lcs_profile_steps(lcs_ctx *ctx, int64_t nsteps, double *ms, int64_t *
 #define LCS_STEP_OWNED_FIELD 4
 
 /* Number of step-kernel configurations lcs_tune tries. */
-#define LCS_TUNE_CONFIGS 13
+#define LCS_TUNE_CONFIGS 14
 
 /* Autotuner: time every step-kernel configuration on steps_per_trial real
- * steps of all ensembles, keep the fastest, and rebuild the step graphs with
- * it.  The configurations, in order, as (threads per block, particles per
+ * steps of all ensembles and keep, for every class of ensembles, the fastest
+ * for that class; then rebuild the step graphs.  A class is the ensembles of
+ * one grid size N whose particle counts lie in the same decade (10^k <= np <
+ * 10^(k+1)).  During the trials every class runs in launches of its own, so
+ * that each class's step kernel is timed alone; afterwards the ensembles
+ * that share a configuration share launches (at most 42 ensembles per
+ * launch), so a context runs one step-kernel launch per configuration in
+ * use (and per 42 ensembles).  The configurations, in order, as (threads per block, particles per
  * thread, mode): (256,2,0) (256,1,0) (128,2,0) (256,2,1) (128,2,1)
- * (256,2,2) (128,2,2) (256,1,2) (256,2,3) (128,2,3) (256,1,3) (256,1,4)
- * (256,2,4).  The first two numbers fix the scan tile.
+ * (256,2,2) (128,2,2) (256,1,2) (256,2,3) (128,2,3) (256,1,3) (128,1,3)
+ * (256,1,4) (256,2,4).  The first two numbers fix the scan tile.
  * Configurations of mode LCS_STEP_STAGED_FIELD are skipped for the all-FP64
  * kernel, every mode but LCS_STEP_DEFERRED for an evolving field or
  * migration per stage (then with 256 threads only), and every mode but
  * LCS_STEP_OWNED_FIELD for an owned_field context (and that mode for any
  * other).  The trial steps advance the simulation (steps_per_trial steps per
  * tried configuration, recorded like any other step); results do not depend
- * on the choice.  *block, *items, *mode (may be NULL) receive the choice;
+ * on the choice.  *block, *items, *mode (may be NULL) receive the choice
+ * for the class of ensemble 0 (lcs_step_config_of reports any ensemble's);
  * trial_ms (host, LCS_TUNE_CONFIGS doubles, may be NULL) the step-kernel
- * milliseconds of each configuration in that order, -1 for one skipped.
- * Synchronising. */
+ * milliseconds of each configuration in that order, summed over all
+ * classes, -1 for one skipped.  Synchronising. */
 lcs_status lcs_tune(lcs_ctx *ctx, int steps_per_trial, int *block, int *items, int *mode,
                     double *trial_ms);
 
-/* Select one of the LCS_TUNE_CONFIGS step-kernel configurations by hand
- * (the values lcs_tune chooses among); the step graphs are rebuilt.
+/* Step-kernel configuration of ensemble `ens` (host outputs, may be NULL):
+ * threads per block, particles per thread, mode. */
+lcs_status lcs_step_config_of(lcs_ctx *ctx, int ens, int *block, int *items, int *mode);
+
+/* Select one of the LCS_TUNE_CONFIGS step-kernel configurations by hand for
+ * every ensemble (the values lcs_tune chooses among); the step graphs are
+ * rebuilt.
  * Results do not depend on the choice.  LCS_ERR_ARG for a combination not
  * in the list or one that lcs_tune skips for this context (see there).
  * Synchronising. */
@@ -340,6 +356,10 @@ void lcs_destroy(lcs_ctx *ctx);
 
 /* Number of kernel launches enqueued by ctx since lcs_init. */
 int64_t lcs_launch_count(lcs_ctx *ctx);
+
+/* Number of CUDA graph launches lcs_step has issued since lcs_init (one per
+ * recorded run of steps, see lcs_step). */
+int64_t lcs_graph_launch_count(lcs_ctx *ctx);
 
 /* Stable partition of n keys into nbins bins -- a counting sort; the
  * paper's mask -> prefix scan -> parallel pack (Sec. 2.3.3) is the case

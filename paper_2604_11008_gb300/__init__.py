@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "liblcs.so")
 
 LCS_OK, LCS_ERR_ARG, LCS_ERR_CUDA, LCS_ERR_OOM, LCS_ERR_CAPACITY = 0, 1, 2, 3, 4
 LCS_ERR_TIMEOUT, LCS_ERR_NONFINITE, LCS_ERR_DISPLACEMENT, LCS_ERR_STATE = 5, 6, 7, 8
-LCS_TUNE_CONFIGS = 13  # step-kernel configurations lcs_tune tries
+LCS_TUNE_CONFIGS = 14  # step-kernel configurations lcs_tune tries
 # step-kernel modes
 STEP_PLAIN, STEP_STAGED_FIELD, STEP_PREFETCH, STEP_DEFERRED, STEP_OWNED_FIELD = 0, 1, 2, 3, 4
 STATUS_NAMES = {0: "LCS_OK", 1: "LCS_ERR_ARG", 2: "LCS_ERR_CUDA", 3: "LCS_ERR_OOM",
@@ -38,10 +38,11 @@ EXPORTS = ("lcs_init", "lcs_step", "lcs_migrate", "lcs_sort", "lcs_set_state", "
            "lcs_get_field", "lcs_backward", "lcs_sync", "lcs_last_error", "lcs_destroy",
            "lcs_launch_count", "lcs_partition", "lcs_profile_steps", "lcs_partition_noalloc",
            "lcs_tune", "lcs_set_step_config", "lcs_staged_tiles", "lcs_set_field",
-           "lcs_pair_histogram", "lcs_selftest_waits", "lcs_get_state_by_id")
+           "lcs_pair_histogram", "lcs_selftest_waits", "lcs_get_state_by_id",
+           "lcs_step_config_of", "lcs_graph_launch_count")
 PARTITION_NOALLOC_MAX_N = 1 << 20
 DRAGS = {"stokes": 0, "nonlinear": 1}  # lcs_drag: f = 1, or the factor of Eq. (7)
-PROF_CLASSES = ("step", "finish", "unpack", "flip", "sort")
+PROF_CLASSES = ("step", "tail", "sort")
 
 
 class LcsError(RuntimeError):
@@ -81,6 +82,7 @@ def lib():
         L.lcs_set_state.argtypes = [P, i32, P, P, P, P, P, P]
         L.lcs_get_state.argtypes = [P, i32, P, P, P, P, P, P]
         L.lcs_get_state_by_id.argtypes = [P, i32, P, P, P]
+        L.lcs_step_config_of.argtypes = [P, i32, P, P, P]
         L.lcs_get_field.argtypes = [P, i32, P]
         L.lcs_backward.argtypes = [P, P, P, P, P, P]
         L.lcs_sync.argtypes = [P]
@@ -90,6 +92,8 @@ def lib():
         L.lcs_destroy.restype = None
         L.lcs_launch_count.argtypes = [P]
         L.lcs_launch_count.restype = i64
+        L.lcs_graph_launch_count.argtypes = [P]
+        L.lcs_graph_launch_count.restype = i64
         L.lcs_partition.argtypes = [P, i64, i32, P, P, P, P]
         L.lcs_profile_steps.argtypes = [P, i64, P, P]
         L.lcs_partition_noalloc.argtypes = [P, i64, i32, P, P, P, P]
@@ -103,7 +107,8 @@ def lib():
                      "lcs_get_state", "lcs_get_field", "lcs_backward", "lcs_sync",
                      "lcs_partition", "lcs_profile_steps", "lcs_partition_noalloc", "lcs_tune",
                      "lcs_set_step_config", "lcs_staged_tiles", "lcs_set_field",
-                     "lcs_pair_histogram", "lcs_selftest_waits", "lcs_get_state_by_id"):
+                     "lcs_pair_histogram", "lcs_selftest_waits", "lcs_get_state_by_id",
+                     "lcs_step_config_of"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -288,6 +293,13 @@ class Simulator:
         g = np.divide(counts, expected, out=np.zeros(len(counts)), where=expected > 0)
         return 0.5 * (edges[1:] + edges[:-1]), g, counts
 
+    def step_config_of(self, ens: int = 0):
+        """(threads per block, particles per thread, mode) of ensemble `ens`."""
+        b, it, md = C.c_int(), C.c_int(), C.c_int()
+        self._check(lib().lcs_step_config_of(self._ctx, int(ens), C.byref(b), C.byref(it),
+                                             C.byref(md)))
+        return b.value, it.value, md.value
+
     def set_step_config(self, block: int, items: int, mode: int = STEP_PLAIN):
         """Pin one of the step-kernel configurations lcs_tune chooses among."""
         self._check(lib().lcs_set_step_config(self._ctx, int(block), int(items), int(mode)))
@@ -302,6 +314,11 @@ class Simulator:
     @property
     def launches(self) -> int:
         return int(lib().lcs_launch_count(self._ctx))
+
+    @property
+    def graph_launches(self) -> int:
+        """CUDA graph launches issued by step() so far (one per recorded run of steps)."""
+        return int(lib().lcs_graph_launch_count(self._ctx))
 
     def get_state(self, ens: int = 0, device: str = "cuda", out=None):
         """Current particles in storage order: dict of x, v (3, np), tau, ids, img, seg."""

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -69,6 +70,18 @@ struct Ens {
   double *lam_id = nullptr, *lam_s = nullptr;
 };
 
+// Step-kernel configuration: threads per block, particles per thread, mode.
+struct StepCfg {
+  int block = 256, items = 1, mode = LCS_STEP_DEFERRED;
+};
+
+// One step-kernel launch: its ensembles (at most GROUP_ENS) and configuration.
+struct Group {
+  std::vector<int> ens;
+  StepCfg cfg;
+  int64_t tiles = 0;  // look-back array size of the launch
+};
+
 }  // namespace
 
 struct lcs_ctx {
@@ -79,31 +92,65 @@ struct lcs_ctx {
   std::string err;
   std::vector<void *> allocs;
   // captured step graphs, keyed by which ensembles sort after that step
+  // (contexts without a step period, see below)
   std::map<std::vector<bool>, cudaGraphExec_t> graphs;
+  // Step period Q: the least common multiple of the ensembles' sort_every and
+  // ckpt_every (0 when it exceeds MAX_PERIOD).  With Q > 0 lcs_step records
+  // runs of consecutive steps that end at multiples of Q, checkpoint steps
+  // or the end of the call as one graph each, keyed by (step count mod Q at
+  // the start, number of steps): the same run of sorts repeats every Q steps.
+  int64_t period = 0;
+  std::map<std::pair<int64_t, int64_t>, cudaGraphExec_t> chunk_graphs;
   int64_t launches = 0;
+  int64_t graph_launches = 0;  // cudaGraphLaunch calls of lcs_step
   int sms = 0;  // streaming multiprocessors of the context's device
   // batched step over all ensembles (one launch per kernel per step)
   FieldKind kind = FK_F64;
-  int mode = 0;  // step kernel: 0 plain, 1 staged field box, 2 prefetched records, 3 deferred
   bool pf_tau = false, pf_img = false;  // some ensemble has per-particle tau / images
   bool evolve = false;  // some ensemble has an evolving field (mode-3 kernels only)
   bool per_stage = false;  // migration after each Runge-Kutta stage (modes 3 and 4 only)
   bool owned = false;      // owned-field mode (mode-4 kernels only)
-  int block = 256, items = 2;   // threads per block, particles per thread (set in setup_batch)
   int step_grid = 1, total_P = 0;
   int64_t total_tiles = 0;      // sum of the ensembles' look-back array sizes
   unsigned long long *tile_status = nullptr;
   BatchArgs bt{};
   StepArgs *d_args = nullptr;
   int *d_ens_P_off = nullptr;
-  unsigned *d_counter = nullptr;           // one tile counter per step group
-  std::vector<std::pair<int, int>> groups;  // (first ensemble, count), count <= GROUP_ENS
-  std::vector<int64_t> group_tiles;         // look-back array size of each group
+  unsigned *d_counter = nullptr;  // one tile counter per step group (n_ens + 1 of them)
+  std::vector<StepCfg> cfg;       // step-kernel configuration of every ensemble
+  std::vector<Group> groups;      // the step-kernel launches of one step
 };
 
 namespace {
 
 thread_local std::string g_last_init_error = "no error";
+
+// Ensembles that share a step-kernel configuration are advanced by one
+// launch per GROUP_ENS of them; during lcs_tune also split by class.
+void regroup(lcs_ctx *c, const std::vector<int> *cls) {
+  const int n = (int)c->ens.size();
+  std::vector<int> order(n);
+  for (int k = 0; k < n; ++k) order[k] = k;
+  auto key = [&](int k) {
+    return std::make_tuple(cls ? (*cls)[k] : 0, c->cfg[k].mode, c->cfg[k].block,
+                           c->cfg[k].items);
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key(a) < key(b); });
+  c->groups.clear();
+  for (int i = 0; i < n;) {
+    Group g;
+    g.cfg = c->cfg[order[i]];
+    int j = i;
+    while (j < n && key(order[j]) == key(order[i]) && (int)g.ens.size() < GROUP_ENS) {
+      g.ens.push_back(order[j]);
+      g.tiles += c->ens[order[j]].max_tiles;
+      ++j;
+    }
+    c->groups.push_back(std::move(g));
+    i = j;
+  }
+  c->bt.ngroups = (int)c->groups.size();
+}
 
 lcs_status fail(lcs_ctx *c, lcs_status s, const std::string &msg) {
   if (c) {
@@ -226,34 +273,41 @@ lcs_status enqueue_sort(lcs_ctx *c, Ens &e, cudaStream_t st) {
   return LCS_OK;
 }
 
-// The step kernel of every group of ensembles (one launch per GROUP_ENS ensembles).
-lcs_status launch_steps(lcs_ctx *c, cudaStream_t st, int stage) {
+struct Prof;
+void prof_mark(Prof *pf, cudaStream_t st, int cls);
+
+// The step kernel of every group of ensembles (one launch per group; with
+// pf, an event pair around each launch, class 1000 + group index).
+lcs_status launch_steps(lcs_ctx *c, cudaStream_t st, int stage, Prof *pf = nullptr) {
   static thread_local StepGroup<GROUP_ENS> big;
   for (size_t gi = 0; gi < c->groups.size(); ++gi) {
-    const int first = c->groups[gi].first, cnt = c->groups[gi].second;
+    const Group &gr = c->groups[gi];
+    const StepCfg &k = gr.cfg;
+    const int cnt = (int)gr.ens.size();
     const int occ = std::max(
-        1, step_kernel_occupancy(c->kind, c->mode, c->block, c->items, c->evolve, stage,
+        1, step_kernel_occupancy(c->kind, k.mode, k.block, k.items, c->evolve, stage,
                                  c->pf_tau, c->pf_img, c->per_stage));
-    const int grid = (int)std::max<int64_t>(
-        1, std::min<int64_t>(c->group_tiles[gi], (int64_t)occ * c->sms));
+    const int grid =
+        (int)std::max<int64_t>(1, std::min<int64_t>(gr.tiles, (int64_t)occ * c->sms));
+    if (pf) prof_mark(pf, st, 1000 + (int)gi);
     if (cnt == 1) {
       StepGroup<1> one;
-      one.a[0] = c->ens[first].a;
+      one.a[0] = c->ens[gr.ens[0]].a;
       one.n = 1;
       one.pf_tau = c->pf_tau;
       one.pf_img = c->pf_img;
       one.pf_vs = c->per_stage;
       one.counter = c->d_counter + gi;
-      CK(launch_step_group<1>(one, c->kind, c->mode, c->block, c->items, c->evolve, stage, grid,
+      CK(launch_step_group<1>(one, c->kind, k.mode, k.block, k.items, c->evolve, stage, grid,
                               st));
     } else {
-      for (int k = 0; k < cnt; ++k) big.a[k] = c->ens[first + k].a;
+      for (int j = 0; j < cnt; ++j) big.a[j] = c->ens[gr.ens[j]].a;
       big.n = cnt;
       big.pf_tau = c->pf_tau;
       big.pf_img = c->pf_img;
       big.pf_vs = c->per_stage;
       big.counter = c->d_counter + gi;
-      CK(launch_step_group<GROUP_ENS>(big, c->kind, c->mode, c->block, c->items, c->evolve, stage,
+      CK(launch_step_group<GROUP_ENS>(big, c->kind, k.mode, k.block, k.items, c->evolve, stage,
                                       grid, st));
     }
     c->launches += 1;
@@ -261,20 +315,19 @@ lcs_status launch_steps(lcs_ctx *c, cudaStream_t st, int stage) {
   return LCS_OK;
 }
 
-// One step of every ensemble: 1 memset + (step groups + 3) launches, whatever
-// the number of ensembles (one step group per GROUP_ENS ensembles); twice
-// that with migration per stage (the predictor pass, then the corrector).
+// One step of every ensemble: (launch groups + 1) launches -- the step
+// kernel of every group, then the step tail (unpack, next layout, buffer
+// swap, look-back words cleared for the next step) -- whatever the number
+// of ensembles; twice that with migration per stage (the predictor pass,
+// then the corrector).
 lcs_status enqueue_step(lcs_ctx *c, cudaStream_t st) {
   const int passes = c->per_stage ? 2 : 1;
   for (int p = 0; p < passes; ++p) {
     const int stage = c->per_stage ? p + 1 : 0;
-    CK(cudaMemsetAsync(c->tile_status, 0, sizeof(unsigned long long) * c->total_tiles, st));
     lcs_status rs = launch_steps(c, st, stage);
     if (rs != LCS_OK) return rs;
-    CK(launch_finish(c->bt, st));
-    CK(launch_unpack(c->bt, c->total_P, st));
-    CK(launch_flip(c->bt, st, p == passes - 1));
-    c->launches += 3;
+    CK(launch_tail(c->bt, c->total_P, st, p == passes - 1));
+    c->launches += 1;
   }
   return LCS_OK;
 }
@@ -291,6 +344,12 @@ struct Prof {
   }
 };
 
+// Record an event opening the interval of class `cls` (up to the next mark).
+void prof_mark(Prof *pf, cudaStream_t st, int cls) {
+  cudaEventRecord(pf->get(), st);
+  pf->cls.push_back(cls);
+}
+
 lcs_status enqueue_step_profiled(lcs_ctx *c, const std::vector<bool> &sorts, Prof &pf) {
   cudaStream_t st = c->st;
   auto mark = [&](int cls) {
@@ -300,18 +359,11 @@ lcs_status enqueue_step_profiled(lcs_ctx *c, const std::vector<bool> &sorts, Pro
   };
   const int passes = c->per_stage ? 2 : 1;
   for (int p = 0; p < passes; ++p) {
-    mark(LCS_PROF_FLIP);
-    CK(cudaMemsetAsync(c->tile_status, 0, sizeof(unsigned long long) * c->total_tiles, st));
-    mark(LCS_PROF_STEP);
-    lcs_status rs = launch_steps(c, st, c->per_stage ? p + 1 : 0);
+    lcs_status rs = launch_steps(c, st, c->per_stage ? p + 1 : 0, &pf);
     if (rs != LCS_OK) return rs;
-    mark(LCS_PROF_FINISH);
-    CK(launch_finish(c->bt, st));
-    mark(LCS_PROF_UNPACK);
-    CK(launch_unpack(c->bt, c->total_P, st));
-    mark(LCS_PROF_FLIP);
-    CK(launch_flip(c->bt, st, p == passes - 1));
-    c->launches += 3;
+    mark(LCS_PROF_TAIL);
+    CK(launch_tail(c->bt, c->total_P, st, p == passes - 1));
+    c->launches += 1;
   }
   bool any = false;
   for (bool b : sorts) any |= b;
@@ -327,16 +379,22 @@ lcs_status enqueue_step_profiled(lcs_ctx *c, const std::vector<bool> &sorts, Pro
   return LCS_OK;
 }
 
-// Record one step of every ensemble, followed by the cell sort of the
-// ensembles flagged in `sorts`, as a CUDA graph.
-lcs_status capture(lcs_ctx *c, const std::vector<bool> &sorts, cudaGraphExec_t *out) {
+std::vector<bool> sort_set(lcs_ctx *c, int64_t next);
+
+// Record `len` consecutive steps of every ensemble as one CUDA graph, the
+// first of them step number first_step (1-based), each followed by the cell
+// sort of the ensembles that sort after it.
+lcs_status capture(lcs_ctx *c, int64_t first_step, int64_t len, cudaGraphExec_t *out) {
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(c->cap_st, cudaStreamCaptureModeThreadLocal));
   lcs_status r = LCS_OK;
   const int64_t l0 = c->launches;
-  r = enqueue_step(c, c->cap_st);
-  for (size_t k = 0; k < c->ens.size(); ++k)
-    if (r == LCS_OK && sorts[k]) r = enqueue_sort(c, c->ens[k], c->cap_st);
+  for (int64_t j = 0; j < len && r == LCS_OK; ++j) {
+    const std::vector<bool> sorts = sort_set(c, first_step + j);
+    r = enqueue_step(c, c->cap_st);
+    for (size_t k = 0; k < c->ens.size(); ++k)
+      if (r == LCS_OK && sorts[k]) r = enqueue_sort(c, c->ens[k], c->cap_st);
+  }
   c->launches = l0;  // counted again at each replay
   cudaError_t ee = cudaStreamEndCapture(c->cap_st, &g);
   if (r != LCS_OK) {
@@ -363,10 +421,12 @@ std::vector<bool> sort_set(lcs_ctx *c, int64_t next) {
 void drop_graphs(lcs_ctx *c) {
   for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
   c->graphs.clear();
+  for (auto &kv : c->chunk_graphs) cudaGraphExecDestroy(kv.second);
+  c->chunk_graphs.clear();
 }
 
 int64_t launches_per_step(lcs_ctx *c, const std::vector<bool> &sorts) {
-  int64_t n = (3 + (int64_t)c->groups.size()) * (c->per_stage ? 2 : 1);
+  int64_t n = (1 + (int64_t)c->groups.size()) * (c->per_stage ? 2 : 1);
   for (size_t k = 0; k < c->ens.size(); ++k) {
     const Ens &e = c->ens[k];
     if (sorts[k]) {
@@ -427,8 +487,9 @@ lcs_status upload_args(lcs_ctx *c) {
 
 // Step-tile tables of every ensemble for the current tile size.
 lcs_status retile(lcs_ctx *c) {
-  for (auto &e : c->ens) {
-    e.a.step_tile = c->block * c->items;
+  for (size_t k = 0; k < c->ens.size(); ++k) {
+    Ens &e = c->ens[k];
+    e.a.step_tile = c->cfg[k].block * c->cfg[k].items;
     k_relayout<<<1, 1024, 0, c->st>>>(e.a, 0);
     c->launches += 1;
   }
@@ -454,12 +515,35 @@ lcs_status setup_batch(lcs_ctx *c) {
       return fail(c, LCS_ERR_ARG, "all ensembles of a context need the same owned_field");
   }
   c->per_stage = c->ens[0].d.migrate_per_stage != 0;
+  // step period of the recorded runs: lcm of the sort and checkpoint
+  // intervals, stretched to at least 8 steps (a multiple of a period is a
+  // period), none above MAX_PERIOD
+  {
+    constexpr int64_t MAX_PERIOD = 64;
+    int64_t q = 1;
+    auto lcm = [](int64_t a, int64_t b) {
+      int64_t x = a, y = b;
+      while (y) {
+        const int64_t t = x % y;
+        x = y;
+        y = t;
+      }
+      return a / x * b;
+    };
+    for (auto &e : c->ens) {
+      if (e.d.sort_every > 0 && q <= MAX_PERIOD) q = lcm(q, e.d.sort_every);
+      if (e.d.ckpt_every > 0 && q <= MAX_PERIOD) q = lcm(q, e.d.ckpt_every);
+    }
+    if (q < 8) q *= (8 + q - 1) / q;
+    c->period = q <= MAX_PERIOD ? q : 0;
+  }
   c->owned = c->ens[0].d.owned_field != 0;
   // default step kernel (lcs_tune / lcs_set_step_config change it): the
-  // deferred scatter, one particle per thread for the FP64-field kernels
-  c->mode = c->owned ? LCS_STEP_OWNED_FIELD : LCS_STEP_DEFERRED;
-  c->block = 256;
-  c->items = (c->kind == FK_DF || c->kind == FK_F64) ? 1 : 2;
+  // deferred scatter, one particle per thread (two for BF16 fields), the
+  // fastest of the configurations on the 16.8M-particle workload
+  c->cfg.assign(c->ens.size(),
+                StepCfg{256, c->kind == FK_BF16 ? 2 : 1,
+                        c->owned ? LCS_STEP_OWNED_FIELD : LCS_STEP_DEFERRED});
   c->total_tiles = 0;
   c->total_P = 0;
   std::vector<int> poff(n + 1, 0);
@@ -469,28 +553,21 @@ lcs_status setup_batch(lcs_ctx *c) {
   }
   c->total_P = poff[n];
   CK(dalloc(c, &c->tile_status, c->total_tiles));
+  // zero once: after that every step tail clears the words its step used
+  CK(cudaMemsetAsync(c->tile_status, 0, sizeof(unsigned long long) * c->total_tiles, c->st));
   int64_t off = 0;
   for (auto &e : c->ens) {
     e.a.m.tile_status = c->tile_status + off;
     off += e.max_tiles;
   }
-  c->groups.clear();
-  c->group_tiles.clear();
-  for (int k = 0; k < n; k += GROUP_ENS) {
-    const int cnt = std::min(GROUP_ENS, n - k);
-    c->groups.emplace_back(k, cnt);
-    int64_t t = 0;
-    for (int j = k; j < k + cnt; ++j) t += c->ens[j].max_tiles;
-    c->group_tiles.push_back(t);
-  }
-  const int ng = (int)c->groups.size();
   CK(dalloc(c, &c->d_args, n));
   CK(dalloc(c, &c->d_ens_P_off, n + 1));
-  CK(dalloc(c, &c->d_counter, ng));
+  CK(dalloc(c, &c->d_counter, n + 1));  // at most one launch group per ensemble
   CK(cudaMemcpyAsync(c->d_ens_P_off, poff.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice,
                      c->st));
-  CK(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned) * ng, c->st));
-  c->bt = BatchArgs{c->d_args, n, c->d_ens_P_off, c->d_counter, ng};
+  CK(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned) * (n + 1), c->st));
+  c->bt = BatchArgs{c->d_args, n, c->d_ens_P_off, c->d_counter, 0};
+  regroup(c, nullptr);
   return retile(c);
 }
 
@@ -599,7 +676,7 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
     e.key_bits = ceil_log2(space);
     e.mig_bits = std::max(1, ceil_log2(2 * (int64_t)P));
     e.max_tiles = (int)(e.np / 32 + P + 2);  // 32 = smallest step tile of any config
-    e.a.step_tile = c->block * c->items;
+    e.a.step_tile = 256;  // the configuration's tile, set by setup_batch (retile)
     e.max_stiles = (int)(e.np / SORT_TILE + P + 2);
     e.a.dt = d.dt;
     e.a.half_dt = 0.5 * d.dt;
@@ -647,7 +724,7 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
     A(dalloc(c, &m.staged, 1));
     A(dalloc(c, &m.fin_tab, (int64_t)P * (NBIN - 1)));
     A(dalloc(c, &m.bincnt, (int64_t)P * NBIN));
-    A(dalloc(c, &m.off_in, (int64_t)P * NBIN));
+    A(dalloc(c, &m.tail_done, 1));
     A(dalloc(c, &m.stay_tot, P));
     A(dalloc(c, &m.mig_tot, P));
     for (int b = 0; b < 2; ++b) {
@@ -700,6 +777,7 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
       C2(cudaMemcpy(m.fin_tab, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice));
     }
     C2(cudaMemsetAsync(m.bincnt, 0, sizeof(int) * P * NBIN, st));
+    C2(cudaMemsetAsync(m.tail_done, 0, sizeof(unsigned), st));
     C2(cudaMemsetAsync(m.stay_tot, 0, sizeof(int64_t) * P, st));
     C2(cudaMemsetAsync(m.mig_tot, 0, sizeof(int64_t) * P, st));
     C2(launch_field_convert(d.field, d.n, e.kind, e.field, st));
@@ -763,21 +841,44 @@ lcs_status lcs_step(lcs_ctx *c, int64_t nsteps) {
   lcs_status r = check_ctx(c);
   if (r != LCS_OK) return r;
   if (nsteps < 0) return reject(c, "nsteps < 0");
-  if (nsteps == 0) return LCS_OK;
-  for (int64_t k = 0; k < nsteps; ++k) {
+  int64_t done = 0;
+  while (done < nsteps) {
     // all ensembles of a context share the step count
-    const std::vector<bool> sorts = sort_set(c, c->ens[0].steps + 1);
-    auto it = c->graphs.find(sorts);
-    if (it == c->graphs.end()) {
-      cudaGraphExec_t ge = nullptr;
-      r = capture(c, sorts, &ge);
-      if (r != LCS_OK) return r;
-      it = c->graphs.emplace(sorts, ge).first;
+    const int64_t S = c->ens[0].steps;
+    int64_t len = 1;
+    cudaGraphExec_t ge = nullptr;
+    if (c->period > 0) {
+      // a run of steps up to the next multiple of the period, the next
+      // checkpoint step of any ensemble, or the end of the call
+      const int64_t Q = c->period, phase = S % Q;
+      len = std::min(nsteps - done, Q - phase);
+      for (auto &e : c->ens)
+        if (e.d.ckpt_every > 0)
+          len = std::min<int64_t>(len, e.d.ckpt_every - S % e.d.ckpt_every);
+      const auto key = std::make_pair(phase, len);
+      auto it = c->chunk_graphs.find(key);
+      if (it == c->chunk_graphs.end()) {
+        r = capture(c, S + 1, len, &ge);
+        if (r != LCS_OK) return r;
+        it = c->chunk_graphs.emplace(key, ge).first;
+      }
+      ge = it->second;
+    } else {
+      const std::vector<bool> sorts = sort_set(c, S + 1);
+      auto it = c->graphs.find(sorts);
+      if (it == c->graphs.end()) {
+        r = capture(c, S + 1, 1, &ge);
+        if (r != LCS_OK) return r;
+        it = c->graphs.emplace(sorts, ge).first;
+      }
+      ge = it->second;
     }
-    CK(cudaGraphLaunch(it->second, c->st));
-    c->launches += launches_per_step(c, sorts);
+    CK(cudaGraphLaunch(ge, c->st));
+    c->graph_launches += 1;
+    for (int64_t j = 1; j <= len; ++j) c->launches += launches_per_step(c, sort_set(c, S + j));
+    done += len;
     for (auto &e : c->ens) {
-      ++e.steps;
+      e.steps += len;
       if (e.d.ckpt_every > 0 && e.steps % e.d.ckpt_every == 0) {
         r = tape_store(c, e, e.steps / e.d.ckpt_every);
         if (r != LCS_OK) return r;
@@ -1071,15 +1172,19 @@ lcs_status lcs_backward(lcs_ctx *c, const double *gx, const double *gv, double *
   return read_status(c);
 }
 
-lcs_status lcs_profile_steps(lcs_ctx *c, int64_t nsteps, double *ms, int64_t *count) {
-  NvtxRange nvtx_range("lcs_profile_steps");
-  lcs_status r = check_ctx(c);
-  if (r != LCS_OK) return r;
-  if (nsteps < 0 || !ms) return reject(c, "lcs_profile_steps: bad argument");
+}  // extern "C"
+
+namespace {
+// lcs_profile_steps with, when group_ms is given, the step-kernel time of
+// every launch group accumulated per group.
+lcs_status profile_steps(lcs_ctx *c, int64_t nsteps, double *ms, int64_t *count,
+                         std::vector<double> *group_ms) {
   for (int k = 0; k < LCS_PROF_N; ++k) {
     ms[k] = 0.0;
     if (count) count[k] = 0;
   }
+  if (group_ms) group_ms->assign(c->groups.size(), 0.0);
+  lcs_status r = LCS_OK;
   for (int64_t k = 0; k < nsteps; ++k) {
     const std::vector<bool> sorts = sort_set(c, c->ens[0].steps + 1);
     {
@@ -1090,7 +1195,11 @@ lcs_status lcs_profile_steps(lcs_ctx *c, int64_t nsteps, double *ms, int64_t *co
         for (size_t i = 0; i + 1 < pf.ev.size(); ++i) {
           float t = 0.f;
           cudaEventElapsedTime(&t, pf.ev[i], pf.ev[i + 1]);
-          const int cls = pf.cls[i];
+          int cls = pf.cls[i];
+          if (cls >= 1000) {  // one step-kernel launch group
+            if (group_ms && cls - 1000 < (int)group_ms->size()) (*group_ms)[cls - 1000] += t;
+            cls = LCS_PROF_STEP;
+          }
           if (cls >= 0 && cls < LCS_PROF_N) {
             ms[cls] += t;
             if (count) count[cls] += 1;
@@ -1110,6 +1219,17 @@ lcs_status lcs_profile_steps(lcs_ctx *c, int64_t nsteps, double *ms, int64_t *co
   }
   return read_status(c);
 }
+}  // namespace
+
+extern "C" {
+
+lcs_status lcs_profile_steps(lcs_ctx *c, int64_t nsteps, double *ms, int64_t *count) {
+  NvtxRange nvtx_range("lcs_profile_steps");
+  lcs_status r = check_ctx(c);
+  if (r != LCS_OK) return r;
+  if (nsteps < 0 || !ms) return reject(c, "lcs_profile_steps: bad argument");
+  return profile_steps(c, nsteps, ms, count, nullptr);
+}
 
 // Step-kernel configurations: (threads per block, particles per thread, kernel mode)
 // Whether a context may use a step-kernel configuration: no staged-field
@@ -1128,8 +1248,8 @@ static bool step_config_allowed(const lcs_ctx *c, int block, int mode) {
 
 static const int kStepConfigs[LCS_TUNE_CONFIGS][3] = {
     {256, 2, 0}, {256, 1, 0}, {128, 2, 0}, {256, 2, 1}, {128, 2, 1}, {256, 2, 2},
-    {128, 2, 2}, {256, 1, 2}, {256, 2, 3}, {128, 2, 3}, {256, 1, 3}, {256, 1, 4},
-    {256, 2, 4}};
+    {128, 2, 2}, {256, 1, 2}, {256, 2, 3}, {128, 2, 3}, {256, 1, 3}, {128, 1, 3},
+    {256, 1, 4}, {256, 2, 4}};
 
 lcs_status lcs_set_step_config(lcs_ctx *c, int block, int items, int mode) {
   lcs_status r = check_ctx(c);
@@ -1139,13 +1259,22 @@ lcs_status lcs_set_step_config(lcs_ctx *c, int block, int items, int mode) {
   if (!known || !step_config_allowed(c, block, mode))
     return reject(c, "lcs_set_step_config: configuration not available");
   CK(cudaStreamSynchronize(c->st));
-  c->block = block;
-  c->items = items;
-  c->mode = mode;
+  for (auto &k : c->cfg) k = StepCfg{block, items, mode};
+  regroup(c, nullptr);
   r = retile(c);
   if (r != LCS_OK) return r;
   drop_graphs(c);
   return read_status(c);
+}
+
+lcs_status lcs_step_config_of(lcs_ctx *c, int ens, int *block, int *items, int *mode) {
+  lcs_status r = check_ctx(c);
+  if (r != LCS_OK) return r;
+  if (ens < 0 || ens >= (int)c->ens.size()) return reject(c, "lcs_step_config_of: bad ensemble");
+  if (block) *block = c->cfg[ens].block;
+  if (items) *items = c->cfg[ens].items;
+  if (mode) *mode = c->cfg[ens].mode;
+  return LCS_OK;
 }
 
 lcs_status lcs_staged_tiles(lcs_ctx *c, int64_t *count) {
@@ -1169,35 +1298,54 @@ lcs_status lcs_tune(lcs_ctx *c, int steps_per_trial, int *block, int *items, int
   lcs_status r = check_ctx(c);
   if (r != LCS_OK) return r;
   if (steps_per_trial < 1) return reject(c, "lcs_tune: steps_per_trial < 1");
+  // ensemble classes: grid size and decade of the particle count
+  const int n = (int)c->ens.size();
+  std::vector<int> cls(n);
+  {
+    std::map<std::pair<int, int>, int> ids;
+    for (int k = 0; k < n; ++k) {
+      int dec = 0;
+      for (int64_t v = c->ens[k].np; v >= 10; v /= 10) ++dec;
+      const auto key = std::make_pair(c->ens[k].d.n, dec);
+      auto it = ids.find(key);
+      if (it == ids.end()) it = ids.emplace(key, (int)ids.size()).first;
+      cls[k] = it->second;
+    }
+  }
+  int ncls = 0;
+  for (int v : cls) ncls = std::max(ncls, v + 1);
+  std::vector<double> best(ncls, 1e300);
+  std::vector<int> pick(ncls, -1);
   const auto &cfg = kStepConfigs;
-  double best = 1e300;
-  int bi = 0;
   for (int k = 0; k < LCS_TUNE_CONFIGS; ++k) {
     if (trial_ms) trial_ms[k] = -1.0;
     if (!step_config_allowed(c, cfg[k][0], cfg[k][2])) continue;
-    c->block = cfg[k][0];
-    c->items = cfg[k][1];
-    c->mode = cfg[k][2];
+    // every class in launches of its own, so that each is timed alone
+    for (auto &q : c->cfg) q = StepCfg{cfg[k][0], cfg[k][1], cfg[k][2]};
+    regroup(c, &cls);
     r = retile(c);
     if (r != LCS_OK) return r;
     double ms[LCS_PROF_N];
-    r = lcs_profile_steps(c, steps_per_trial, ms, nullptr);
+    std::vector<double> gms;
+    r = profile_steps(c, steps_per_trial, ms, nullptr, &gms);
     if (r != LCS_OK) return r;
     if (trial_ms) trial_ms[k] = ms[LCS_PROF_STEP];
-    if (ms[LCS_PROF_STEP] < best) {
-      best = ms[LCS_PROF_STEP];
-      bi = k;
-    }
+    std::vector<double> per(ncls, 0.0);
+    for (size_t g = 0; g < c->groups.size(); ++g) per[cls[c->groups[g].ens[0]]] += gms[g];
+    for (int q = 0; q < ncls; ++q)
+      if (per[q] < best[q]) best[q] = per[q], pick[q] = k;
   }
-  c->block = cfg[bi][0];
-  c->items = cfg[bi][1];
-  c->mode = cfg[bi][2];
+  for (int k = 0; k < n; ++k) {
+    const int b = pick[cls[k]] >= 0 ? pick[cls[k]] : 0;
+    c->cfg[k] = StepCfg{cfg[b][0], cfg[b][1], cfg[b][2]};
+  }
+  regroup(c, nullptr);  // ensembles that share a configuration share launches again
   r = retile(c);
   if (r != LCS_OK) return r;
   drop_graphs(c);  // graphs recorded with the old configuration are rebuilt
-  if (block) *block = c->block;
-  if (items) *items = c->items;
-  if (mode) *mode = c->mode;
+  if (block) *block = c->cfg[0].block;
+  if (items) *items = c->cfg[0].items;
+  if (mode) *mode = c->cfg[0].mode;
   return LCS_OK;
 }
 
@@ -1224,6 +1372,8 @@ void lcs_destroy(lcs_ctx *c) {
 }
 
 int64_t lcs_launch_count(lcs_ctx *c) { return c ? c->launches : 0; }
+
+int64_t lcs_graph_launch_count(lcs_ctx *c) { return c ? c->graph_launches : 0; }
 
 lcs_status lcs_partition(const uint32_t *keys, int64_t n, int nbins, uint32_t *perm,
                          int64_t *bin_off, int32_t *status, void *stream) {

@@ -88,13 +88,13 @@ struct Meta {
   unsigned long long *tile_status;  // look-back words                [max tiles]
   unsigned int *tile_counter;       // dynamic tile ids               [1]
   int *bincnt;           // migrants per (source, direction)          [Ptot*27]
-  int64_t *off_in;       // offset of (source, direction) in its dest [Ptot*27]
   int64_t *stay_tot;     // stayers per segment                       [Ptot]
   int64_t *mig_tot;      // migrants per segment                      [Ptot]
   unsigned long long *staged;  // step tiles served from a shared-memory field box [1]
   int64_t *nstep;        // steps taken since lcs_init                  [1]
   int *fin_tab;          // arrivals of each destination: source*27 + direction,
                          // by ascending source, -1 padded             [Ptot*26]
+  unsigned *tail_done;   // blocks of the step tail done (last-block count) [1]
 };
 
 struct StepArgs {
@@ -292,9 +292,7 @@ cudaError_t launch_build_bricks(const void *field, const Geom &g, FieldKind kind
 template <int CAP>
 cudaError_t launch_step_group(const StepGroup<CAP> &pb, FieldKind kind, int mode, int block,
                               int items, bool evolve, int stage, int grid, cudaStream_t st);
-cudaError_t launch_finish(const BatchArgs &bt, cudaStream_t st);
-cudaError_t launch_unpack(const BatchArgs &bt, int total_P, cudaStream_t st);
-cudaError_t launch_flip(const BatchArgs &bt, cudaStream_t st, int count_step);
+cudaError_t launch_tail(const BatchArgs &bt, int total_P, cudaStream_t st, int count_step);
 cudaError_t launch_field_expand(const void *src, int N, FieldKind kind, double *dst,
                                 cudaStream_t st);
 // Pair-separation histogram (lcs_stats.cu).

@@ -217,60 +217,46 @@ int step_kernel_occupancy(FieldKind kind, int mode, int block, int items, bool e
   return 0;
 }
 
-// ---------------------------------------------------------------- finish
+// ---------------------------------------------------------------- step tail
 
-// Per destination d: arrival offsets of every (source, direction) pair in
-// source order after the stayers, the new count, and the next layout.
-__device__ __forceinline__ void finish_body(const StepArgs &a) {
-  const int P = a.geo.Ptot;
-  const int ph = *a.m.phase;
-  const int64_t *capB = a.m.lay_cap[ph ^ 1];
+// The tail of a step, one kernel: one block of 1024 threads per (ensemble,
+// source subdomain) places that source's leavers after the stayers of their
+// destinations (unpack, Sec. 3.2.2) and clears its share of the look-back
+// words for the next step; the last block of an ensemble to finish computes
+// the new counts and the next layout and swaps the buffers.
+constexpr int TAIL_BLOCK = 1024;
+constexpr int TAIL_WARPS = TAIL_BLOCK / 32;
+
+// Offset, inside destination d, of the leavers of source s in direction b:
+// the stayers of d, then the arrivals of d in source order (the destination's
+// table fin_tab), up to (s, b).  Lane b of one warp computes direction b.
+__device__ __forceinline__ void tail_offsets(const StepArgs &a, int s, int64_t *s_off) {
   const int lane = threadIdx.x & 31;
-  // one warp per destination: lane j takes the j-th arriving (source,
-  // direction) pair of the destination's table, in source order
-  for (int d = threadIdx.x >> 5; d < P; d += blockDim.x >> 5) {
-    const int e = lane < NBIN - 1 ? a.m.fin_tab[d * (NBIN - 1) + lane] : -1;
-    const long long c = e >= 0 ? (long long)a.m.bincnt[e] : 0;
-    long long incl = c;
+  const Geom &g = a.geo;
+  if (lane < NBIN && lane != BIN_STAY) {
+    const int b = lane;
+    const int ps[3] = {s % g.P[0], (s / g.P[0]) % g.P[1], s / (g.P[0] * g.P[1])};
+    const int dir[3] = {b % 3 - 1, (b / 3) % 3 - 1, b / 9 - 1};
+    int pd[3];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const long long y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
+    for (int q = 0; q < 3; ++q) pd[q] = (ps[q] + dir[q] + g.P[q]) % g.P[q];
+    const int d = pd[0] + g.P[0] * (pd[1] + g.P[1] * pd[2]);
+    const int me = s * NBIN + b;
+    int64_t off = a.m.stay_tot[d];
+    const int *tab = a.m.fin_tab + d * (NBIN - 1);
+    for (int j = 0; j < NBIN - 1; ++j) {
+      const int e = tab[j];
+      if (e < 0 || e == me) break;
+      off += a.m.bincnt[e];
     }
-    const int64_t stay = a.m.stay_tot[d];
-    if (e >= 0) {
-      a.m.off_in[e] = stay + incl - c;
-      a.m.bincnt[e] = 0;
-    }
-    const long long arrived = __shfl_sync(0xffffffffu, incl, 31);
-    __syncwarp();
-    if (lane == 0) {
-      const int64_t tot = stay + arrived;
-      a.m.stay_tot[d] = 0;
-      if (tot > capB[d]) latch(a.m.status, LCS_ERR_CAPACITY);
-      a.m.cnt[d] = tot;
-    }
+    s_off[b] = off;
   }
-  __syncthreads();
-  layout_from_counts(P, a.step_tile, a.m.cnt, a.m.cstart, a.m.tile_off, a.m.stile_off,
-                     a.m.next_base, a.m.next_cap);
 }
 
-// One block per ensemble.
-__global__ void __launch_bounds__(1024) k_finish(BatchArgs bt) { finish_body(bt.args[blockIdx.x]); }
-
-cudaError_t launch_finish(const BatchArgs &bt, cudaStream_t st) {
-  k_finish<<<bt.n_ens, 1024, 0, st>>>(bt);
-  return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------- unpack
-
-// One block per source subdomain: place its packed leavers, in pack order,
-// after the stayers of their destination (offsets from k_finish), keeping
-// the order within each (source, direction) pair.
-__device__ __forceinline__ void unpack_body(const StepArgs &a, int s) {
-  __shared__ int s_wc[8][NBIN];
+// Place the packed leavers of source s (one block), in pack order, at their
+// offsets, keeping the order within each (source, direction) pair.
+__device__ __forceinline__ void tail_unpack(const StepArgs &a, int s, const int64_t *s_off) {
+  __shared__ int s_wc[TAIL_WARPS][NBIN];
   __shared__ int s_run[NBIN];
   const Geom &g = a.geo;
   const int ph = *a.m.phase;
@@ -282,7 +268,7 @@ __device__ __forceinline__ void unpack_body(const StepArgs &a, int s) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ps[3] = {s % g.P[0], (s / g.P[0]) % g.P[1], s / (g.P[0] * g.P[1])};
   if (threadIdx.x < NBIN) s_run[threadIdx.x] = 0;
-  for (int i = threadIdx.x; i < 8 * NBIN; i += blockDim.x) (&s_wc[0][0])[i] = 0;
+  for (int i = threadIdx.x; i < TAIL_WARPS * NBIN; i += blockDim.x) (&s_wc[0][0])[i] = 0;
   __syncthreads();
   for (int64_t c0 = 0; c0 < nm; c0 += blockDim.x) {
     const int64_t i = c0 + threadIdx.x;
@@ -300,7 +286,7 @@ __device__ __forceinline__ void unpack_body(const StepArgs &a, int s) {
     __syncthreads();
     if (threadIdx.x < NBIN) {
       int t = 0;
-      for (int w = 0; w < 8; ++w) {
+      for (int w = 0; w < TAIL_WARPS; ++w) {
         t += s_wc[w][threadIdx.x];
         s_wc[w][threadIdx.x] = 0;
       }
@@ -312,7 +298,7 @@ __device__ __forceinline__ void unpack_body(const StepArgs &a, int s) {
 #pragma unroll
       for (int q = 0; q < 3; ++q) pd[q] = (ps[q] + dir[q] + g.P[q]) % g.P[q];
       const int d = pd[0] + g.P[0] * (pd[1] + g.P[1] * pd[2]);
-      const int64_t rel = a.m.off_in[s * NBIN + b] + woff + rank;
+      const int64_t rel = s_off[b] + woff + rank;
       if (rel < capB[d]) {
         copy_rec(a.pack, bA + i, B, baseB[d] + rel);
       } else {
@@ -321,45 +307,81 @@ __device__ __forceinline__ void unpack_body(const StepArgs &a, int s) {
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) a.m.mig_tot[s] = 0;
 }
 
-// One block per (ensemble, source subdomain); ens_P_off is the prefix of the
-// ensembles' subdomain counts.
-__global__ void __launch_bounds__(256) k_unpack(BatchArgs bt) {
-  const int e = find_segment(bt.ens_P_off, bt.n_ens, (int)blockIdx.x);
-  unpack_body(bt.args[e], blockIdx.x - bt.ens_P_off[e]);
-}
-
-cudaError_t launch_unpack(const BatchArgs &bt, int total_P, cudaStream_t st) {
-  k_unpack<<<total_P, 256, 0, st>>>(bt);
-  return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------- flip
-
-// The old input buffer becomes the next output with the layout from
-// k_finish; the output becomes the input.
-// One block per ensemble; block 0 also resets the step groups' tile counters.
-__global__ void k_flip(BatchArgs bt, int count_step) {
-  const StepArgs &a = bt.args[blockIdx.x];
+// Last block of an ensemble: new counts (stayers + arrivals), the capacity
+// check, the next layout, the reset of the per-step counters, and the swap:
+// the old input buffer becomes the next output with the new layout, the
+// output becomes the input.
+__device__ __forceinline__ void tail_finish(const StepArgs &a, int count_step) {
+  const int P = a.geo.Ptot;
   const int ph = *a.m.phase;
-  for (int d = threadIdx.x; d < a.geo.Ptot; d += blockDim.x) {
+  const int64_t *capB = a.m.lay_cap[ph ^ 1];
+  const int lane = threadIdx.x & 31;
+  for (int d = threadIdx.x >> 5; d < P; d += TAIL_WARPS) {
+    const int e = lane < NBIN - 1 ? a.m.fin_tab[d * (NBIN - 1) + lane] : -1;
+    long long c = e >= 0 ? (long long)a.m.bincnt[e] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) {
+      const int64_t tot = a.m.stay_tot[d] + c;
+      if (tot > capB[d]) latch(a.m.status, LCS_ERR_CAPACITY);
+      a.m.cnt[d] = tot;
+    }
+  }
+  __syncthreads();
+  // every (source, direction) count and stayer total has been read
+  for (int i = threadIdx.x; i < P * NBIN; i += blockDim.x) a.m.bincnt[i] = 0;
+  for (int d = threadIdx.x; d < P; d += blockDim.x) a.m.stay_tot[d] = 0;
+  layout_from_counts(P, a.step_tile, a.m.cnt, a.m.cstart, a.m.tile_off, a.m.stile_off,
+                     a.m.next_base, a.m.next_cap);
+  __syncthreads();
+  for (int d = threadIdx.x; d < P; d += blockDim.x) {
     a.m.lay_base[ph][d] = a.m.next_base[d];
     a.m.lay_cap[ph][d] = a.m.next_cap[d];
   }
-  __syncthreads();
   if (threadIdx.x == 0) {
     *a.m.phase = ph ^ 1;
     *a.m.tile_counter = 0u;
     if (count_step) *a.m.nstep += 1;
+    *a.m.tail_done = 0u;
   }
-  if (blockIdx.x == 0)
-    for (int k = threadIdx.x; k < bt.ngroups; k += blockDim.x) bt.counter[k] = 0u;
 }
 
-cudaError_t launch_flip(const BatchArgs &bt, cudaStream_t st, int count_step) {
-  k_flip<<<bt.n_ens, 1024, 0, st>>>(bt, count_step);
+__global__ void __launch_bounds__(TAIL_BLOCK) k_tail(BatchArgs bt, int count_step) {
+  __shared__ int64_t s_off[NBIN];
+  __shared__ int s_last;
+  const int e = find_segment(bt.ens_P_off, bt.n_ens, (int)blockIdx.x);
+  const StepArgs &a = bt.args[e];
+  const int s = blockIdx.x - bt.ens_P_off[e];
+  const int P = a.geo.Ptot;
+  // the step kernels have finished: their tile counters start over
+  if (blockIdx.x == 0)
+    for (int k = threadIdx.x; k < bt.ngroups; k += blockDim.x) bt.counter[k] = 0u;
+  // look-back words of this step's tiles, cleared in P slices for the next
+  const int ntile = a.m.tile_off[P];
+  {
+    const int per = (ntile + P - 1) / P, t0 = s * per, t1 = min(ntile, t0 + per);
+    for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) a.m.tile_status[t] = 0ull;
+  }
+  if ((threadIdx.x >> 5) == 0) tail_offsets(a, s, s_off);
+  __syncthreads();
+  tail_unpack(a, s, s_off);
+  if (threadIdx.x == 0) a.m.mig_tot[s] = 0;
+  // the last block of the ensemble to get here finishes the step
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(a.m.tail_done, 1u) == (unsigned)(P - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  tail_finish(a, count_step);
+}
+
+cudaError_t launch_tail(const BatchArgs &bt, int total_P, cudaStream_t st, int count_step) {
+  k_tail<<<total_P, TAIL_BLOCK, 0, st>>>(bt, count_step);
   return cudaGetLastError();
 }
 

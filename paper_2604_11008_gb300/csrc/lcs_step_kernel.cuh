@@ -672,35 +672,45 @@ __device__ __forceinline__ void reload_rest(const StepArgs &a, const TileMeta &m
 // not stall the block.  The parked tile is then written out with coalesced
 // stores: its stayers form one contiguous run of the output window and its
 // leavers one contiguous run of the pack buffer.
+constexpr long long PF_WAIT_LIMIT = 1LL << 20;  // bounded wait for a tile's bulk copies
+
 template <int KIND, int BLOCK, int ITEMS, int CAP, bool EVOLVE, int STAGE, bool OWNED>
 __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockShared &sh,
                                               const int *s_off, unsigned char *pk) {
   constexpr int T = BLOCK * ITEMS;
-  // Placement of the block's tiles, alternating between two slots: the tile
-  // taken in iteration i sits in slot i & 1 and stays there, parked, through
-  // iteration i + 1 (every iteration passes block barriers, so no warp reads
-  // a slot after the next-but-one iteration has started to rewrite it).
-  __shared__ TileMeta s_meta[2];
+  static_assert(BLOCK >= 64, "the acquiring warp must differ from warp 0");
+  // Placement of the block's tiles, in three slots: the tile integrated in
+  // iteration i sits in slot i % 3, is parked through iteration i + 1, and
+  // the last warp takes tile i + 1 into slot (i + 1) % 3 after integrating,
+  // while warp 0 resolves the parked tile's prefix (so the tile counter and
+  // placement latency overlap the look-back instead of stalling the block).
+  // Every iteration passes block barriers, so no warp reads a slot that is
+  // being rewritten.
+  constexpr int ACQ = BLOCK / 32 - 1;
+  __shared__ TileMeta s_meta[3];
   __shared__ unsigned s_park_tot;
   const int n = pb.n, total = s_off[n];
   const bool lay_tau = pb.pf_tau != 0, lay_img = pb.pf_img != 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // the acquiring warp takes the next tile id and writes its placement
+  auto acquire = [&](int slot) {
+    int g = 0;
+    if (lane == 0) g = (int)atomicAdd(pb.counter, 1u);
+    g = __shfl_sync(0xffffffffu, g, 0);
+    TileMeta &m = s_meta[slot];
+    if (g < total) {
+      const int e = CAP == 1 ? 0 : find_ensemble(s_off, n, g);
+      tile_meta_warp<T>(pb.a[e], g, e, g - s_off[e], m);
+    } else if (lane == 0) {
+      m.gtile = g;
+    }
+  };
   bool parked = false;
   if (threadIdx.x < NBIN) sh.hist[threadIdx.x] = 0;
+  if (warp == ACQ) acquire(0);
+  __syncthreads();
   for (int it = 0;; ++it) {
-    TileMeta &cur = s_meta[it & 1];
-    if (warp == 0) {
-      int g = 0;
-      if (lane == 0) g = (int)atomicAdd(pb.counter, 1u);
-      g = __shfl_sync(0xffffffffu, g, 0);
-      if (g < total) {
-        const int e = CAP == 1 ? 0 : find_ensemble(s_off, n, g);
-        tile_meta_warp<T>(pb.a[e], g, e, g - s_off[e], cur);
-      } else if (lane == 0) {
-        cur.gtile = g;
-      }
-    }
-    __syncthreads();
+    TileMeta &cur = s_meta[it % 3];
     const bool fresh = cur.gtile < total;
     long long x[ITEMS][3];
     df v[ITEMS][3];
@@ -713,10 +723,11 @@ __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockSha
       const int e = CAP == 1 ? 0 : cur.e;
       packed = integrate_items<KIND, ITEMS, EVOLVE, STAGE, OWNED>(pb.a[e], cur, sh, x, v, tau,
                                                                   id, img, bin, vs);
+      if (warp == ACQ) acquire((it + 1) % 3);
       reload_rest<ITEMS>(pb.a[e], cur, tau, id, img, bin);
     }
     if (parked) {
-      const TileMeta &pm = s_meta[(it - 1) & 1];
+      const TileMeta &pm = s_meta[(it + 2) % 3];
       const StepArgs &pa = pb.a[CAP == 1 ? 0 : pm.e];
       const unsigned tot = s_park_tot;
       if (warp == 0) {
@@ -810,7 +821,6 @@ constexpr int step_min_blocks() {
                          : 1024 / BLOCK;
 }
 
-constexpr long long PF_WAIT_LIMIT = 1LL << 20;  // bounded wait for a tile's bulk copies
 
 // MODE 0: records read from global memory; 1: the same with the field box
 // staged in shared memory; 2: records of the next tile prefetched by bulk
@@ -915,17 +925,17 @@ __global__ void __launch_bounds__(BLOCK, (step_min_blocks<KIND, BLOCK, ITEMS>())
   X(K, 3, 256, 1, C, 1, 1) X(K, 3, 256, 1, C, 1, 2) X(K, 3, 256, 2, C, 1, 1)       \
   X(K, 3, 256, 2, C, 1, 2) X(K, 4, 256, 1, C, 1, 0) X(K, 4, 256, 2, C, 1, 0)       \
   X(K, 4, 256, 1, C, 1, 1) X(K, 4, 256, 1, C, 1, 2) X(K, 4, 256, 2, C, 1, 1)       \
-  X(K, 4, 256, 2, C, 1, 2)
+  X(K, 4, 256, 2, C, 1, 2) X(K, 3, 128, 1, C, 0, 0) X(K, 3, 128, 1, C, 1, 0)
 
 // Dynamic shared memory of a configuration: the staged field box (mode 1),
 // the two record buffers (mode 2) or the parked tile (modes 3 and 4).
 constexpr int step_dyn_smem(int kind, int mode, int tile, bool tau, bool img, bool vs = false) {
   return mode == 4 ? step_dyn_smem(kind, 3, tile, tau, img, vs)
-         : mode == 3 && vs ? step_dyn_smem(kind, 3, tile, tau, img) + 3 * tile * 8
+         : mode == 3 ? (6 + (tau ? 1 : 0)) * tile * 8 + (1 + (img ? 3 : 0)) * tile * 4 + tile +
+                           (vs ? 3 * tile * 8 : 0)
          : mode == 1 ? (kind != FK_F64 ? STAGE_BYTES : 0)
          : mode == 2 ? 2 * ((6 + (tau ? 1 : 0)) * (tile + 2) * 8 +
                             (1 + (img ? 3 : 0)) * (tile + 4) * 4)
-         : mode == 3 ? (6 + (tau ? 1 : 0)) * tile * 8 + (1 + (img ? 3 : 0)) * tile * 4 + tile
                      : 0;
 }
 

@@ -83,13 +83,18 @@ def test_tune_keeps_results(lcs):
     sp = specs("df", "f64")
     a = lcs.Simulator(None, None, None, None, ensembles=sp)
     b = lcs.Simulator(None, None, None, None, ensembles=sp)
-    a.step(22)
-    cfg = b.tune(2)   # 11 configurations x 2 steps (the owned-field mode is skipped)
+    cfg = b.tune(2)   # 12 configurations x 2 steps (the owned-field mode is skipped)
+    a.step(2 * int((b.tune_trials_ms > 0).sum()))
     assert cfg in ((256, 2, 0), (256, 1, 0), (128, 2, 0), (256, 2, 1), (128, 2, 1),
                    (256, 2, 2), (128, 2, 2), (256, 1, 2), (256, 2, 3), (128, 2, 3),
-                   (256, 1, 3))
-    assert (b.tune_trials_ms[:11] > 0).all()
-    assert (b.tune_trials_ms[11:] == -1).all()
+                   (256, 1, 3), (128, 1, 3))
+    assert (b.tune_trials_ms[:12] > 0).all()
+    assert (b.tune_trials_ms[12:] == -1).all()
+    # a configuration per class of ensembles (grid size, decade of np)
+    allowed = {(256, 2, 0), (256, 1, 0), (128, 2, 0), (256, 2, 1), (128, 2, 1), (256, 2, 2),
+               (128, 2, 2), (256, 1, 2), (256, 2, 3), (128, 2, 3), (256, 1, 3), (128, 1, 3)}
+    cfgs = [b.step_config_of(k) for k in range(len(sp))]
+    assert cfgs[0] == cfg and all(c in allowed for c in cfgs)
     for k in range(len(sp)):
         sa, sb = gpu_state(a, k), gpu_state(b, k)
         for key in ("seg", "ids", "x", "v"):
@@ -124,3 +129,24 @@ def test_batch_workload_ensembles_equal_solo(lcs):
         a, b = gpu_state(batch, k), gpu_state(solo)
         assert np.array_equal(a["ids"], b["ids"]) and np.array_equal(a["x"], b["x"])
         solo.close()
+
+
+def test_step_runs_in_one_graph_equal_single_steps(lcs):
+    """lcs_step records runs of steps up to the step period (lcm of the sort
+    and checkpoint intervals) as one graph each; any split of the same steps
+    into calls gives the same state bit for bit."""
+    sp = specs("df", "f64")
+    a = lcs.Simulator(None, None, None, None, ensembles=sp)
+    b = lcs.Simulator(None, None, None, None, ensembles=sp)
+    for n in (37, 3, 60):
+        a.step(n)
+        for _ in range(n):
+            b.step(1)
+        for k in range(len(sp)):
+            sa, sb = gpu_state(a, k), gpu_state(b, k)
+            for key in ("seg", "ids", "x", "v", "img"):
+                assert np.array_equal(sa[key], sb[key]), (n, k, key)
+    # sort intervals 3, 4, 5: period 60, so the 100 steps of `a` took one
+    # graph launch per run -- (0, 37), (37, 3), (40, 20), (0, 40) -- and `b` 100
+    assert a.graph_launches == 4 and b.graph_launches == 100, (a.graph_launches,
+                                                               b.graph_launches)

@@ -155,7 +155,7 @@ def test_owned_field_arguments(lcs):
             sim.set_step_config(*cfg)
         assert e.value.status == lcs.LCS_ERR_ARG
     assert owned.tune(1)[2] == lcs.STEP_OWNED_FIELD
-    assert (owned.tune_trials_ms[:11] == -1).all() and (owned.tune_trials_ms[11:] > 0).all()
+    assert (owned.tune_trials_ms[:12] == -1).all() and (owned.tune_trials_ms[12:] > 0).all()
     spec = dict(field=field, x0=x, v0=v, dt=0.01, tau=tau, sub=(2, 2, 2))
     with pytest.raises(lcs.LcsError) as e:
         lcs.Simulator(None, None, None, None, ensembles=[dict(spec, owned_field=True), spec])

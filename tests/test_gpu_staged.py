@@ -22,7 +22,7 @@ pytestmark = pytest.mark.gpu
 UNSTAGED = (256, 2, 0)
 STAGED = ((256, 2, 1), (128, 2, 1))
 PREFETCH = ((256, 2, 2), (128, 2, 2), (256, 1, 2))
-DEFERRED = ((256, 2, 3), (128, 2, 3), (256, 1, 3))
+DEFERRED = ((256, 2, 3), (128, 2, 3), (256, 1, 3), (128, 1, 3))
 
 
 @pytest.fixture(scope="module")
