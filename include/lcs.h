@@ -240,6 +240,15 @@ lcs_status lcs_get_field(lcs_ctx *ctx, int ens, double *out);
  * allocated with cudaMallocAsync on the context's stream.  Synchronising. */
 lcs_status lcs_pair_histogram(lcs_ctx *ctx, int ens, double r_max, int nbins, int64_t *counts);
 
+/* The radial distribution function of ensemble `ens` from the same counts:
+ * g[b] (host, nbins doubles) = counts[b] / (np (np - 1) / 2 * V_b / L^3),
+ * V_b = (4/3) pi (r_{b+1}^3 - r_b^3) with r_b = b r_max / nbins, and r[b]
+ * (host, may be NULL) the bin centres (r_b + r_{b+1}) / 2; g[b] = 0 where
+ * the expected count is 0 (np < 2).  counts (host, may be NULL) receives the
+ * counts.  Same requirements as lcs_pair_histogram.  Synchronising. */
+lcs_status lcs_pair_rdf(lcs_ctx *ctx, int ens, double r_max, int nbins, double *r, double *g,
+                        int64_t *counts);
+
 /* Evolving field: the second snapshot of ensemble `ens` becomes the first,
  * `field` (device [3][N][N][N] FP64, read during the call) at time t becomes
  * the second (t must exceed the current second snapshot's time); the step

@@ -39,7 +39,7 @@ EXPORTS = ("lcs_init", "lcs_step", "lcs_migrate", "lcs_sort", "lcs_set_state", "
            "lcs_launch_count", "lcs_partition", "lcs_profile_steps", "lcs_partition_noalloc",
            "lcs_tune", "lcs_set_step_config", "lcs_staged_tiles", "lcs_set_field",
            "lcs_pair_histogram", "lcs_selftest_waits", "lcs_get_state_by_id",
-           "lcs_step_config_of", "lcs_graph_launch_count")
+           "lcs_step_config_of", "lcs_graph_launch_count", "lcs_pair_rdf")
 PARTITION_NOALLOC_MAX_N = 1 << 20
 DRAGS = {"stokes": 0, "nonlinear": 1}  # lcs_drag: f = 1, or the factor of Eq. (7)
 PROF_CLASSES = ("step", "tail", "sort")
@@ -102,13 +102,14 @@ def lib():
         L.lcs_staged_tiles.argtypes = [P, P]
         L.lcs_set_field.argtypes = [P, i32, P, C.c_double]
         L.lcs_pair_histogram.argtypes = [P, i32, C.c_double, i32, P]
+        L.lcs_pair_rdf.argtypes = [P, i32, C.c_double, i32, P, P, P]
         L.lcs_selftest_waits.argtypes = [P, P, P]
         for name in ("lcs_init", "lcs_step", "lcs_migrate", "lcs_sort", "lcs_set_state",
                      "lcs_get_state", "lcs_get_field", "lcs_backward", "lcs_sync",
                      "lcs_partition", "lcs_profile_steps", "lcs_partition_noalloc", "lcs_tune",
                      "lcs_set_step_config", "lcs_staged_tiles", "lcs_set_field",
                      "lcs_pair_histogram", "lcs_selftest_waits", "lcs_get_state_by_id",
-                     "lcs_step_config_of"):
+                     "lcs_step_config_of", "lcs_pair_rdf"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -283,15 +284,14 @@ class Simulator:
         return counts
 
     def rdf(self, r_max: float, nbins: int, ens: int = 0):
-        """Radial distribution function: (bin centres, g, counts), with
+        """Radial distribution function (lcs_pair_rdf): (bin centres, g, counts),
         g = counts / (np (np - 1) / 2 * shell volume / L^3)."""
-        counts = self.pair_histogram(r_max, nbins, ens)
-        n, box = self.meta[ens]["np"], self.meta[ens]["box"]
-        edges = np.linspace(0.0, r_max, int(nbins) + 1)
-        shell = 4.0 / 3.0 * math.pi * (edges[1:] ** 3 - edges[:-1] ** 3)
-        expected = n * (n - 1) / 2.0 * shell / box ** 3
-        g = np.divide(counts, expected, out=np.zeros(len(counts)), where=expected > 0)
-        return 0.5 * (edges[1:] + edges[:-1]), g, counts
+        r = np.zeros(int(nbins), dtype=np.float64)
+        g = np.zeros(int(nbins), dtype=np.float64)
+        counts = np.zeros(int(nbins), dtype=np.int64)
+        self._check(lib().lcs_pair_rdf(self._ctx, int(ens), float(r_max), int(nbins), _ptr(r),
+                                       _ptr(g), _ptr(counts)))
+        return r, g, counts
 
     def step_config_of(self, ens: int = 0):
         """(threads per block, particles per thread, mode) of ensemble `ens`."""

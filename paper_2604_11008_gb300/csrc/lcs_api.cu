@@ -1099,6 +1099,26 @@ lcs_status lcs_pair_histogram(lcs_ctx *c, int ens, double r_max, int nbins, int6
   return read_status(c);
 }
 
+lcs_status lcs_pair_rdf(lcs_ctx *c, int ens, double r_max, int nbins, double *r, double *g,
+                        int64_t *counts) {
+  lcs_status st = check_ctx(c);
+  if (st != LCS_OK) return st;
+  if (!g || nbins < 1 || nbins > 4096) return reject(c, "lcs_pair_rdf: bad argument");
+  std::vector<int64_t> cnt(nbins);
+  st = lcs_pair_histogram(c, ens, r_max, nbins, cnt.data());
+  if (st != LCS_OK) return st;
+  const double n = (double)c->ens[ens].np, L = c->ens[ens].d.box;
+  const double pairs = n * (n - 1.0) / 2.0, pi = 3.14159265358979323846;
+  for (int b = 0; b < nbins; ++b) {
+    const double r0 = r_max * b / nbins, r1 = r_max * (b + 1) / nbins;
+    const double expected = pairs * (4.0 / 3.0 * pi * (r1 * r1 * r1 - r0 * r0 * r0)) / (L * L * L);
+    g[b] = expected > 0.0 ? (double)cnt[b] / expected : 0.0;
+    if (r) r[b] = 0.5 * (r0 + r1);
+    if (counts) counts[b] = cnt[b];
+  }
+  return LCS_OK;
+}
+
 lcs_status lcs_set_field(lcs_ctx *c, int ens, const double *field, double t) {
   lcs_status r = check_ctx(c);
   if (r != LCS_OK) return r;

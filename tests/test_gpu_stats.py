@@ -68,6 +68,12 @@ def test_uniform_particles_are_not_clustered(lcs):
     r, g, counts = sim.rdf(L / N, 8)
     assert counts[1:].min() > 1000
     assert np.all(np.abs(g[1:] - 1) < 0.05), g
+    # g is the counts over the pair count of an ideal gas in each shell
+    edges = np.linspace(0.0, L / N, 9)
+    expected = n * (n - 1) / 2 * (4 / 3 * math.pi * np.diff(edges ** 3)) / L ** 3
+    assert np.allclose(g, counts / expected, rtol=1e-12, atol=0)
+    assert np.allclose(r, 0.5 * (edges[1:] + edges[:-1]), rtol=1e-15)
+    assert np.array_equal(counts, sim.pair_histogram(L / N, 8))
 
 
 def test_pair_histogram_arguments_and_tiny_sets(lcs):
