@@ -170,15 +170,24 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
  * interpolate, integrate (Heun) and wrap every particle, flag it by
  * destination subdomain, and migrate (prefix scan, pack, unpack); after
  * steps whose 1-based count is a multiple of sort_every, sort every
- * subdomain's particles stably by cell.  All ensembles run in the same four
- * persistent kernel launches per step (their tiles share one work counter).
+ * subdomain's particles stably by cell.  A step is one persistent
+ * step-kernel launch per group of ensembles that share a step configuration
+ * (their tiles share one work counter), then one tail kernel for all
+ * ensembles; twice that with migration per stage.
  * Runs of consecutive steps are recorded as CUDA graphs and replayed: with a
  * step period Q (the least common multiple of the ensembles' sort_every and
  * ckpt_every, stretched to at least 8, at most 64) a run ends at the next
  * multiple of Q, at a checkpoint step or at the end of the call, so a call
  * of n steps costs about n / Q graph launches (one per sort period); with
  * no such period, one graph launch per step.  The first run of each kind is
- * recorded when it is first needed. */
+ * recorded when it is first needed.
+ * Under LCS_STEP_DEFERRED and LCS_STEP_OWNED_FIELD the sort after a step
+ * computes only the permutation: the next step kernel reads its records
+ * through it, so the sorted records are written once, by that step.  A
+ * permutation still pending when another call needs the records in sorted
+ * order (lcs_get_state, lcs_get_state_by_id, lcs_migrate,
+ * lcs_pair_histogram, a checkpoint) is applied then; none of this is
+ * visible in any result. */
 lcs_status lcs_step(lcs_ctx *ctx, int64_t nsteps);
 
 /* Standalone migration pass on the current state (asynchronous): a stable
@@ -272,7 +281,9 @@ lcs_status lcs_backward(lcs_ctx *ctx, const double *gx, const double *gv, double
 enum {
   LCS_PROF_STEP = 0,    /* fused interpolate + integrate + scan + pack kernel */
   LCS_PROF_TAIL = 1,    /* step tail: unpack, next layout, buffer swap (one kernel) */
-  LCS_PROF_SORT = 2,    /* the whole cell-sort pass */
+  LCS_PROF_SORT = 2,    /* the cell-sort kernels (keys, radix passes, and the
+                           permutation of the records where no step kernel
+                           reads through it) */
   LCS_PROF_N = 3
 };
 

@@ -63,6 +63,9 @@ struct Ens {
   int *to1 = nullptr;
   int64_t steps = 0;
   int id_bits = 32;  // key width of the id sort (ceil log2 np for the default ids)
+  // cell sort computed but not applied: its permutation sits in s.pay[perm],
+  // and the next step reads the records through it (-1: none pending)
+  int perm = -1;
   // adjoint tape: checkpoint k holds the state after k*ckpt_every steps
   std::vector<TapeSlot> tape;
   bool tape_ok = false;
@@ -91,16 +94,22 @@ struct lcs_ctx {
   int failed = 0;  // latched host-side status (LCS_ERR_*)
   std::string err;
   std::vector<void *> allocs;
-  // captured step graphs, keyed by which ensembles sort after that step
-  // (contexts without a step period, see below)
-  std::map<std::vector<bool>, cudaGraphExec_t> graphs;
   // Step period Q: the least common multiple of the ensembles' sort_every and
   // ckpt_every (0 when it exceeds MAX_PERIOD).  With Q > 0 lcs_step records
   // runs of consecutive steps that end at multiples of Q, checkpoint steps
-  // or the end of the call as one graph each, keyed by (step count mod Q at
-  // the start, number of steps): the same run of sorts repeats every Q steps.
+  // or the end of the call as one graph each: the same run of sorts repeats
+  // every Q steps.  Without a period every step is its own graph.
   int64_t period = 0;
-  std::map<std::pair<int64_t, int64_t>, cudaGraphExec_t> chunk_graphs;
+  struct RunGraph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int> perm_out;  // pending permutations a replay leaves
+    int64_t launches = 0;       // kernel launches of one replay
+  };
+  // Recorded runs, keyed by (step count mod Q at the start, or -1 without a
+  // period; number of steps; the pending permutation of every ensemble at
+  // the start; without a period, which ensembles sort after the step).
+  using RunKey = std::tuple<int64_t, int64_t, std::vector<int>, std::vector<bool>>;
+  std::map<RunKey, RunGraph> chunk_graphs;
   int64_t launches = 0;
   int64_t graph_launches = 0;  // cudaGraphLaunch calls of lcs_step
   int sms = 0;  // streaming multiprocessors of the context's device
@@ -259,17 +268,47 @@ lcs_status enqueue_migrate(lcs_ctx *c, Ens &e) {
   return LCS_OK;
 }
 
-// The cell sort: stable per-segment sort by brick-major cell key.
-lcs_status enqueue_sort(lcs_ctx *c, Ens &e, cudaStream_t st) {
+// The cell sort, first half: keys and the stable per-segment radix sort by
+// brick-major cell key; *ob receives the payload buffer holding the
+// permutation (sorted rank -> input slot).
+lcs_status enqueue_sort_keys(lcs_ctx *c, Ens &e, cudaStream_t st, int *ob) {
   const int gs = grid_for(e.np, 256, c->sms * 8);
   k_keys_cell<<<gs, 256, 0, st>>>(e.a, e.s.key[0], e.s.pay[0], e.brick, e.nb[0], e.nb[1]);
-  int ob = 0;
-  CK(radix_sort(e.s, e.key_bits, &ob, st, &c->launches));
+  *ob = 0;
+  CK(radix_sort(e.s, e.key_bits, ob, st, &c->launches));
+  c->launches += 1;
+  CK(cudaGetLastError());
+  return LCS_OK;
+}
+
+// The second half: the records permuted into the other buffer, which becomes
+// the input.
+lcs_status enqueue_apply_perm(lcs_ctx *c, Ens &e, cudaStream_t st, int ob) {
+  const int gs = grid_for(e.np, 256, c->sms * 8);
   k_relayout<<<1, 1024, 0, st>>>(e.a, 0);
   k_gather<<<gs, 256, 0, st>>>(e.a, e.s.pay[ob]);
   k_set_phase<<<1, 1024, 0, st>>>(e.a);
-  c->launches += 4;
+  c->launches += 3;
   CK(cudaGetLastError());
+  return LCS_OK;
+}
+
+// The whole cell sort.
+lcs_status enqueue_sort(lcs_ctx *c, Ens &e, cudaStream_t st) {
+  int ob = 0;
+  lcs_status r = enqueue_sort_keys(c, e, st, &ob);
+  return r == LCS_OK ? enqueue_apply_perm(c, e, st, ob) : r;
+}
+
+// Apply every pending sort permutation (before anything but the step kernel
+// reads the records, or before a configuration change).
+lcs_status materialize(lcs_ctx *c) {
+  for (auto &e : c->ens) {
+    if (e.perm < 0) continue;
+    lcs_status r = enqueue_apply_perm(c, e, c->st, e.perm);
+    if (r != LCS_OK) return r;
+    e.perm = -1;
+  }
   return LCS_OK;
 }
 
@@ -315,16 +354,69 @@ lcs_status launch_steps(lcs_ctx *c, cudaStream_t st, int stage, Prof *pf = nullp
   return LCS_OK;
 }
 
+// Whether the step kernel of ensemble k reads its records through a pending
+// cell-sort permutation (the modes that read every record by its slot).
+bool fuses_sort(const lcs_ctx *c, size_t k) {
+  const int m = c->cfg[k].mode;
+  return m == LCS_STEP_DEFERRED || m == LCS_STEP_OWNED_FIELD;
+}
+
+// Before a step: a pending permutation is handed to the step kernel where
+// its mode reads through it, else applied first.
+lcs_status take_pending(lcs_ctx *c, cudaStream_t st) {
+  for (size_t k = 0; k < c->ens.size(); ++k) {
+    Ens &e = c->ens[k];
+    e.a.perm = nullptr;
+    if (e.perm < 0) continue;
+    if (fuses_sort(c, k)) {
+      e.a.perm = e.s.pay[e.perm];
+    } else {
+      lcs_status r = enqueue_apply_perm(c, e, st, e.perm);
+      if (r != LCS_OK) return r;
+    }
+    e.perm = -1;
+  }
+  return LCS_OK;
+}
+
+void clear_step_perm(lcs_ctx *c) {
+  for (auto &e : c->ens) e.a.perm = nullptr;
+}
+
+// After a step: the cell sort of the ensembles in `sorts`; where the next
+// step kernel can read through the permutation, only the keys and the radix
+// passes run now.
+lcs_status enqueue_sorts(lcs_ctx *c, const std::vector<bool> &sorts, cudaStream_t st) {
+  for (size_t k = 0; k < c->ens.size(); ++k) {
+    if (!sorts[k]) continue;
+    Ens &e = c->ens[k];
+    lcs_status r;
+    if (fuses_sort(c, k)) {
+      int ob = 0;
+      r = enqueue_sort_keys(c, e, st, &ob);
+      e.perm = ob;
+    } else {
+      r = enqueue_sort(c, e, st);
+    }
+    if (r != LCS_OK) return r;
+  }
+  return LCS_OK;
+}
+
 // One step of every ensemble: (launch groups + 1) launches -- the step
 // kernel of every group, then the step tail (unpack, next layout, buffer
 // swap, look-back words cleared for the next step) -- whatever the number
 // of ensembles; twice that with migration per stage (the predictor pass,
-// then the corrector).
+// then the corrector).  A pending sort permutation is consumed by the first
+// pass.
 lcs_status enqueue_step(lcs_ctx *c, cudaStream_t st) {
+  lcs_status r = take_pending(c, st);
+  if (r != LCS_OK) return r;
   const int passes = c->per_stage ? 2 : 1;
   for (int p = 0; p < passes; ++p) {
     const int stage = c->per_stage ? p + 1 : 0;
     lcs_status rs = launch_steps(c, st, stage);
+    clear_step_perm(c);
     if (rs != LCS_OK) return rs;
     CK(launch_tail(c->bt, c->total_P, st, p == passes - 1));
     c->launches += 1;
@@ -357,9 +449,15 @@ lcs_status enqueue_step_profiled(lcs_ctx *c, const std::vector<bool> &sorts, Pro
     cudaEventRecord(e0, st);
     pf.cls.push_back(cls);
   };
+  bool pending = false;
+  for (auto &e : c->ens) pending |= e.perm >= 0;
+  if (pending) mark(LCS_PROF_SORT);  // a permutation applied before the step
+  lcs_status r = take_pending(c, st);
+  if (r != LCS_OK) return r;
   const int passes = c->per_stage ? 2 : 1;
   for (int p = 0; p < passes; ++p) {
     lcs_status rs = launch_steps(c, st, c->per_stage ? p + 1 : 0, &pf);
+    clear_step_perm(c);
     if (rs != LCS_OK) return rs;
     mark(LCS_PROF_TAIL);
     CK(launch_tail(c->bt, c->total_P, st, p == passes - 1));
@@ -369,11 +467,8 @@ lcs_status enqueue_step_profiled(lcs_ctx *c, const std::vector<bool> &sorts, Pro
   for (bool b : sorts) any |= b;
   if (any) {
     mark(LCS_PROF_SORT);
-    for (size_t k = 0; k < c->ens.size(); ++k) {
-      if (!sorts[k]) continue;
-      lcs_status r = enqueue_sort(c, c->ens[k], st);
-      if (r != LCS_OK) return r;
-    }
+    r = enqueue_sorts(c, sorts, st);
+    if (r != LCS_OK) return r;
   }
   mark(-1);
   return LCS_OK;
@@ -383,8 +478,12 @@ std::vector<bool> sort_set(lcs_ctx *c, int64_t next);
 
 // Record `len` consecutive steps of every ensemble as one CUDA graph, the
 // first of them step number first_step (1-based), each followed by the cell
-// sort of the ensembles that sort after it.
-lcs_status capture(lcs_ctx *c, int64_t first_step, int64_t len, cudaGraphExec_t *out) {
+// sort of the ensembles that sort after it.  The pending permutations of the
+// context move on as if the steps had run (the graph starts from the ones
+// given at capture and leaves the ones the context then holds); *nlaunch
+// receives the kernel launches of one replay.
+lcs_status capture(lcs_ctx *c, int64_t first_step, int64_t len, cudaGraphExec_t *out,
+                   int64_t *nlaunch) {
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(c->cap_st, cudaStreamCaptureModeThreadLocal));
   lcs_status r = LCS_OK;
@@ -392,9 +491,9 @@ lcs_status capture(lcs_ctx *c, int64_t first_step, int64_t len, cudaGraphExec_t 
   for (int64_t j = 0; j < len && r == LCS_OK; ++j) {
     const std::vector<bool> sorts = sort_set(c, first_step + j);
     r = enqueue_step(c, c->cap_st);
-    for (size_t k = 0; k < c->ens.size(); ++k)
-      if (r == LCS_OK && sorts[k]) r = enqueue_sort(c, c->ens[k], c->cap_st);
+    if (r == LCS_OK) r = enqueue_sorts(c, sorts, c->cap_st);
   }
+  *nlaunch = c->launches - l0;
   c->launches = l0;  // counted again at each replay
   cudaError_t ee = cudaStreamEndCapture(c->cap_st, &g);
   if (r != LCS_OK) {
@@ -419,22 +518,8 @@ std::vector<bool> sort_set(lcs_ctx *c, int64_t next) {
 }
 
 void drop_graphs(lcs_ctx *c) {
-  for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
-  c->graphs.clear();
-  for (auto &kv : c->chunk_graphs) cudaGraphExecDestroy(kv.second);
+  for (auto &kv : c->chunk_graphs) cudaGraphExecDestroy(kv.second.exec);
   c->chunk_graphs.clear();
-}
-
-int64_t launches_per_step(lcs_ctx *c, const std::vector<bool> &sorts) {
-  int64_t n = (1 + (int64_t)c->groups.size()) * (c->per_stage ? 2 : 1);
-  for (size_t k = 0; k < c->ens.size(); ++k) {
-    const Ens &e = c->ens[k];
-    if (sorts[k]) {
-      const int passes = e.key_bits ? (e.key_bits + SORT_MAX_BITS - 1) / SORT_MAX_BITS : 0;
-      n += 4 + 5 * passes;
-    }
-  }
-  return n;
 }
 
 // Record checkpoint k of ensemble e (allocating its slot on first use).
@@ -846,7 +931,9 @@ lcs_status lcs_step(lcs_ctx *c, int64_t nsteps) {
     // all ensembles of a context share the step count
     const int64_t S = c->ens[0].steps;
     int64_t len = 1;
-    cudaGraphExec_t ge = nullptr;
+    std::vector<int> pend(c->ens.size());
+    for (size_t k = 0; k < c->ens.size(); ++k) pend[k] = c->ens[k].perm;
+    lcs_ctx::RunKey key;
     if (c->period > 0) {
       // a run of steps up to the next multiple of the period, the next
       // checkpoint step of any ensemble, or the end of the call
@@ -855,32 +942,29 @@ lcs_status lcs_step(lcs_ctx *c, int64_t nsteps) {
       for (auto &e : c->ens)
         if (e.d.ckpt_every > 0)
           len = std::min<int64_t>(len, e.d.ckpt_every - S % e.d.ckpt_every);
-      const auto key = std::make_pair(phase, len);
-      auto it = c->chunk_graphs.find(key);
-      if (it == c->chunk_graphs.end()) {
-        r = capture(c, S + 1, len, &ge);
-        if (r != LCS_OK) return r;
-        it = c->chunk_graphs.emplace(key, ge).first;
-      }
-      ge = it->second;
+      key = lcs_ctx::RunKey(phase, len, pend, std::vector<bool>());
     } else {
-      const std::vector<bool> sorts = sort_set(c, S + 1);
-      auto it = c->graphs.find(sorts);
-      if (it == c->graphs.end()) {
-        r = capture(c, S + 1, 1, &ge);
-        if (r != LCS_OK) return r;
-        it = c->graphs.emplace(sorts, ge).first;
-      }
-      ge = it->second;
+      key = lcs_ctx::RunKey(-1, 1, pend, sort_set(c, S + 1));
     }
-    CK(cudaGraphLaunch(ge, c->st));
+    auto it = c->chunk_graphs.find(key);
+    if (it == c->chunk_graphs.end()) {
+      lcs_ctx::RunGraph rg;
+      r = capture(c, S + 1, len, &rg.exec, &rg.launches);
+      for (size_t k = 0; k < c->ens.size(); ++k) rg.perm_out.push_back(c->ens[k].perm);
+      for (size_t k = 0; k < c->ens.size(); ++k) c->ens[k].perm = pend[k];  // not run yet
+      if (r != LCS_OK) return r;
+      it = c->chunk_graphs.emplace(key, rg).first;
+    }
+    CK(cudaGraphLaunch(it->second.exec, c->st));
     c->graph_launches += 1;
-    for (int64_t j = 1; j <= len; ++j) c->launches += launches_per_step(c, sort_set(c, S + j));
+    c->launches += it->second.launches;
+    for (size_t k = 0; k < c->ens.size(); ++k) c->ens[k].perm = it->second.perm_out[k];
     done += len;
     for (auto &e : c->ens) {
       e.steps += len;
       if (e.d.ckpt_every > 0 && e.steps % e.d.ckpt_every == 0) {
-        r = tape_store(c, e, e.steps / e.d.ckpt_every);
+        r = materialize(c);  // a checkpoint holds the sorted records
+        if (r == LCS_OK) r = tape_store(c, e, e.steps / e.d.ckpt_every);
         if (r != LCS_OK) return r;
       }
     }
@@ -891,6 +975,7 @@ lcs_status lcs_step(lcs_ctx *c, int64_t nsteps) {
 lcs_status lcs_migrate(lcs_ctx *c) {
   NvtxRange nvtx_range("lcs_migrate");
   lcs_status r = check_ctx(c);
+  if (r == LCS_OK) r = materialize(c);  // the migration sort reuses the sort buffers
   if (r != LCS_OK) return r;
   for (auto &e : c->ens) {
     r = enqueue_migrate(c, e);
@@ -904,6 +989,9 @@ lcs_status lcs_sort(lcs_ctx *c) {
   lcs_status r = check_ctx(c);
   if (r != LCS_OK) return r;
   for (auto &e : c->ens) {
+    // a stable sort of the unsorted records gives the order a pending
+    // permutation stands for: that permutation is simply recomputed
+    e.perm = -1;
     r = enqueue_sort(c, e, c->st);
     if (r != LCS_OK) return r;
   }
@@ -926,6 +1014,7 @@ lcs_status lcs_set_state(lcs_ctx *c, int ens, const double *x, const double *v,
   if (e.a.buf[1].tau && e.np > 0 && !tau)
     return reject(c, "lcs_set_state: tau required (per-particle tau_p)");
   e.tape_ok = false;  // the recorded trajectory no longer leads to this state
+  e.perm = -1;        // and a pending sort of the old records is void
   cudaStream_t st = c->st;
   // Place into buffer 1 with the given segments as windows; a relayout copy
   // moves it to the other buffer with a fresh layout.
@@ -968,6 +1057,8 @@ lcs_status lcs_get_state(lcs_ctx *c, int ens, double *x, double *v, double *tau,
   if (!c) return LCS_ERR_ARG;
   if (c->failed) return LCS_ERR_STATE;
   if (ens < 0 || ens >= (int)c->ens.size()) return reject(c, "bad ensemble");
+  lcs_status mr = materialize(c);  // the records in their sorted order
+  if (mr != LCS_OK) return mr;
   Ens &e = c->ens[ens];
   cudaStream_t st = c->st;
   const int P = e.a.geo.Ptot;
@@ -1013,6 +1104,8 @@ lcs_status lcs_get_state_by_id(lcs_ctx *c, int ens, double *x, double *v, uint32
   if (!c) return LCS_ERR_ARG;
   if (c->failed) return LCS_ERR_STATE;
   if (ens < 0 || ens >= (int)c->ens.size()) return reject(c, "bad ensemble");
+  lcs_status mr = materialize(c);  // the id sort reuses the sort buffers
+  if (mr != LCS_OK) return mr;
   Ens &e = c->ens[ens];
   cudaStream_t st = c->st;
   if (e.np > 0) {
@@ -1069,6 +1162,8 @@ lcs_status lcs_pair_histogram(lcs_ctx *c, int ens, double r_max, int nbins, int6
   const Geom &g = e.a.geo;
   if (g.N < 3 || !(r_max > 0) || !(r_max <= g.L / g.N))
     return reject(c, "lcs_pair_histogram: needs N >= 3 and 0 < r_max <= L/N");
+  r = materialize(c);  // the cell sort of the pairs reuses the sort buffers
+  if (r != LCS_OK) return r;
   cudaStream_t st = c->st;
   const int64_t n = e.np;
   std::vector<unsigned long long> h(nbins, 0ull);

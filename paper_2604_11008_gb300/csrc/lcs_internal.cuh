@@ -123,6 +123,11 @@ struct StepArgs {
   // for the second snapshot of an evolving field (else nullptr)
   const void *bricks;
   const void *bricks_b;
+  // the cell sort's permutation, not yet applied: compacted rank r of the
+  // input (segments in order, cstart) is record perm[r] of the input buffer;
+  // set for the first step after a sort, which reads its records through it
+  // (nullptr: records in storage order)
+  const uint32_t *perm;
 };
 
 // The ensembles of one context, as the batched kernels see them.

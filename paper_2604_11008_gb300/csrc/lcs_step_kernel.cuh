@@ -183,6 +183,7 @@ struct TileMeta {
   int64_t cnt;    // live particles of the segment
   int64_t first;  // first particle of the tile within the segment
   int64_t bA;     // window start of the segment in the input buffer
+  int64_t cs;     // compacted start of the segment (index of its first rank)
 };
 
 template <int T>
@@ -200,6 +201,7 @@ __device__ __forceinline__ TileMeta tile_meta(const StepArgs &a, int gtile, int 
   m.ntile = a.m.tile_off[m.seg + 1] - m.t0;
   m.cnt = a.m.cnt[m.seg];
   m.bA = a.m.lay_base[m.ph][m.seg];
+  m.cs = a.m.cstart[m.seg];
   m.first = (int64_t)(tile - m.t0) * T;
   const int64_t rem = m.cnt - m.first;
   m.n = (int)(rem < 0 ? 0 : (rem > T ? T : rem));
@@ -215,6 +217,12 @@ __device__ __forceinline__ TileMeta tile_meta(const StepArgs &a, int gtile, int 
 // tile_off[s] is at most `tile`, minus one (tile_off is non-decreasing, so
 // those segments form a prefix): every lane counts a slice of tile_off
 // with independent loads, one warp sum adds the slices.
+// Input slot of particle l of a tile's segment: in storage order, or through
+// the pending permutation of a cell sort (its rank cs + l).
+__device__ __forceinline__ int64_t rec_slot(const StepArgs &a, const TileMeta &m, int64_t l) {
+  return a.perm ? (int64_t)__ldg(a.perm + m.cs + l) : m.bA + l;
+}
+
 template <int T>
 __device__ __forceinline__ void tile_meta_warp(const StepArgs &a, int gtile, int e, int tile,
                                                TileMeta &out) {
@@ -246,6 +254,7 @@ __device__ __forceinline__ void tile_meta_warp(const StepArgs &a, int gtile, int
     m.ntile = off[m.seg + 1] - m.t0;
     m.cnt = a.m.cnt[m.seg];
     m.bA = a.m.lay_base[m.ph][m.seg];
+    m.cs = a.m.cstart[m.seg];
     m.first = (int64_t)(tile - m.t0) * T;
     const int64_t rem = m.cnt - m.first;
     m.n = (int)(rem < 0 ? 0 : (rem > T ? T : rem));
@@ -610,7 +619,7 @@ __device__ __forceinline__ unsigned integrate_items(const StepArgs &a, const Til
       // id, tau_p and the image counts are read again after the integration
       // (reload_rest), so that they hold no registers across the gathers;
       // img counts the images crossed in this step until then
-      load_motion(A, mt.bA + l0 + k, x[k], v[k], tau[k], a.tau_const);
+      load_motion(A, rec_slot(a, mt, l0 + k), x[k], v[k], tau[k], a.tau_const);
       img[k][0] = img[k][1] = img[k][2] = 0;
       if (STAGE == 0) {
         if (KIND == FK_F64) heun_step64<EVOLVE>(a, x[k], v[k], tau[k], img[k], bad, tt);
@@ -624,7 +633,7 @@ __device__ __forceinline__ unsigned integrate_items(const StepArgs &a, const Til
         else
           heun_stage1_lo<KIND, OWNED, EVOLVE>(a, x[k], v[k], vs[k], tau[k], img[k], bad, fv, tt);
       } else {
-        const int64_t i = mt.bA + l0 + k;
+        const int64_t i = rec_slot(a, mt, l0 + k);
 #pragma unroll
         for (int s = 0; s < 3; ++s) vs[k][s] = df_from2(A.vs[s][i]);
         if (KIND == FK_F64) heun_stage2_64<EVOLVE>(a, x[k], v[k], vs[k], tau[k], img[k], bad, tt);
@@ -659,15 +668,16 @@ __device__ __forceinline__ void reload_rest(const StepArgs &a, const TileMeta &m
                                             double tau[], uint32_t id[], int img[][3],
                                             const int bin[]) {
   const Rec &A = a.buf[mt.ph];
-  const int64_t i0 = mt.bA + mt.first + (int64_t)threadIdx.x * ITEMS;
+  const int64_t l0 = mt.first + (int64_t)threadIdx.x * ITEMS;
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k) {
     if (bin[k] == -2) continue;
-    id[k] = A.id[i0 + k];
-    if (A.tau) tau[k] = A.tau[i0 + k];
+    const int64_t i = rec_slot(a, mt, l0 + k);
+    id[k] = A.id[i];
+    if (A.tau) tau[k] = A.tau[i];
     if (A.img[0]) {
 #pragma unroll
-      for (int s = 0; s < 3; ++s) img[k][s] += A.img[s][i0 + k];
+      for (int s = 0; s < 3; ++s) img[k][s] += A.img[s][i];
     }
   }
 }
@@ -694,7 +704,7 @@ __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockSha
   // being rewritten.
   constexpr int ACQ = BLOCK / 32 - 1;
   __shared__ TileMeta s_meta[3];
-  __shared__ unsigned s_park_tot;
+  __shared__ unsigned s_park_tot[2];
   const int n = pb.n, total = s_off[n];
   const bool lay_tau = pb.pf_tau != 0, lay_img = pb.pf_img != 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -710,6 +720,39 @@ __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockSha
     } else if (lane == 0) {
       m.gtile = g;
     }
+  };
+  // the parked tile: resolve its exclusive prefix (warp 0), then write its
+  // stayers to the output window and its leavers to the pack buffer
+  auto write_out = [&](const TileMeta &pm, unsigned tot) {
+    const StepArgs &pa = pb.a[CAP == 1 ? 0 : pm.e];
+    if (warp == 0) {
+      const unsigned long long agg = pack_sm(tot >> 16, tot & 0xffffu);
+      const unsigned long long ex =
+          resolve_prefix_warp(pa.m.tile_status, pm.tile, pm.t0, agg, pa.m.status);
+      if (lane == 0) {
+        sh.excl = ex;
+        if (pm.tile - pm.t0 == pm.ntile - 1) {
+          const unsigned long long inc = ex + agg;
+          pa.m.stay_tot[pm.seg] = (int64_t)(inc >> 31);
+          pa.m.mig_tot[pm.seg] = (int64_t)(inc & ((1ull << 31) - 1));
+        }
+      }
+    }
+    __syncthreads();
+    const unsigned long long ex = sh.excl;
+    const int nstay = (int)(tot >> 16), nmig = (int)(tot & 0xffffu);
+    const int64_t stay0 = (int64_t)(ex >> 31), mig0 = (int64_t)(ex & ((1ull << 31) - 1));
+    const int ph = pm.ph;
+    const Rec &B = pa.buf[ph ^ 1];
+    const int64_t bB = pa.m.lay_base[ph ^ 1][pm.seg], cB = pa.m.lay_cap[ph ^ 1][pm.seg];
+    for (int j = threadIdx.x; j < nstay; j += BLOCK) {
+      if (stay0 + j < cB) park_get<T>(pk, lay_tau, lay_img, j, B, bB + stay0 + j, nullptr);
+      else latch(pa.m.status, LCS_ERR_CAPACITY);
+    }
+    const int64_t bA = pm.bA;
+    for (int j = threadIdx.x; j < nmig; j += BLOCK)
+      park_get<T>(pk, lay_tau, lay_img, T - 1 - j, pa.pack, bA + mig0 + j, pa.pack_bin);
+    __syncthreads();
   };
   bool parked = false;
   if (threadIdx.x < NBIN) sh.hist[threadIdx.x] = 0;
@@ -732,39 +775,7 @@ __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockSha
       if (warp == ACQ) acquire((it + 1) % 3);
       reload_rest<ITEMS>(pb.a[e], cur, tau, id, img, bin);
     }
-    if (parked) {
-      const TileMeta &pm = s_meta[(it + 2) % 3];
-      const StepArgs &pa = pb.a[CAP == 1 ? 0 : pm.e];
-      const unsigned tot = s_park_tot;
-      if (warp == 0) {
-        const unsigned long long agg = pack_sm(tot >> 16, tot & 0xffffu);
-        const unsigned long long ex =
-            resolve_prefix_warp(pa.m.tile_status, pm.tile, pm.t0, agg, pa.m.status);
-        if (lane == 0) {
-          sh.excl = ex;
-          if (pm.tile - pm.t0 == pm.ntile - 1) {
-            const unsigned long long inc = ex + agg;
-            pa.m.stay_tot[pm.seg] = (int64_t)(inc >> 31);
-            pa.m.mig_tot[pm.seg] = (int64_t)(inc & ((1ull << 31) - 1));
-          }
-        }
-      }
-      __syncthreads();
-      const unsigned long long ex = sh.excl;
-      const int nstay = (int)(tot >> 16), nmig = (int)(tot & 0xffffu);
-      const int64_t stay0 = (int64_t)(ex >> 31), mig0 = (int64_t)(ex & ((1ull << 31) - 1));
-      const int ph = pm.ph;
-      const Rec &B = pa.buf[ph ^ 1];
-      const int64_t bB = pa.m.lay_base[ph ^ 1][pm.seg], cB = pa.m.lay_cap[ph ^ 1][pm.seg];
-      for (int j = threadIdx.x; j < nstay; j += BLOCK) {
-        if (stay0 + j < cB) park_get<T>(pk, lay_tau, lay_img, j, B, bB + stay0 + j, nullptr);
-        else latch(pa.m.status, LCS_ERR_CAPACITY);
-      }
-      const int64_t bA = pm.bA;
-      for (int j = threadIdx.x; j < nmig; j += BLOCK)
-        park_get<T>(pk, lay_tau, lay_img, T - 1 - j, pa.pack, bA + mig0 + j, pa.pack_bin);
-      __syncthreads();
-    }
+    if (parked) write_out(s_meta[(it + 2) % 3], s_park_tot[(it + 1) & 1]);
     if (!fresh) break;
     // block scan of the fresh tile's (stay, leave) counts
     unsigned incl = packed;
@@ -788,7 +799,7 @@ __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockSha
         sh.tot = wi;
         const StepArgs &a = pb.a[CAP == 1 ? 0 : cur.e];
         publish_aggregate(a.m.tile_status, cur.tile, cur.t0, pack_sm(wi >> 16, wi & 0xffffu));
-        s_park_tot = wi;
+        s_park_tot[it & 1] = wi;
       }
     }
     __syncthreads();

@@ -159,3 +159,42 @@ def test_prefetched_and_deferred_batch_against_oracle(lcs, mode):
         ex, ev, px, pv = traj_errors(st["x"], st["img"], st["v"], st["ids"], ref, s["x0"])
         assert max(ex, ev, px, pv) < 1e-12, (k, ex, ev, px, pv)
     batch.close()
+
+
+@pytest.mark.parametrize("first,second", [(DEFERRED[2], UNSTAGED), (UNSTAGED, DEFERRED[2]),
+                                          (DEFERRED[0], PREFETCH[0])])
+def test_pending_sort_across_calls(lcs, first, second):
+    """A cell sort whose permutation the next step kernel reads (modes 3 and
+    4) is left pending between calls: a switch to a mode that reads records
+    in storage order applies it first; the id-ordered read, an explicit sort
+    and the state read all see the sorted records.  Every path gives the
+    storage of a run in one mode."""
+    case = dense_case(905, 12, 9001)
+    kw = dict(sub=(3, 2, 2), sort_every=3, sort_brick=2, kernel="df", field_dtype="f64")
+
+    def make(cfg):
+        sim = lcs.Simulator(case["field"], case["x0"], case["v0"], case["dt"], tau=case["tau"],
+                            tau_const=case["tau_const"], g=case["g"], track_images=True, **kw)
+        sim.set_step_config(*cfg)
+        return sim
+
+    ref = make(UNSTAGED)
+    ref.step(9)
+    ref_x, ref_v = (t.cpu().numpy() for t in ref.final_state_by_id())
+    ref.sort()
+    ref.step(1)
+    want = gpu_state(ref)
+    ref.close()
+
+    sim = make(first)
+    sim.step(3)                    # the sort after step 3 may be left pending
+    sim.set_step_config(*second)
+    sim.step(6)                    # and the one after step 9
+    x, v = (t.cpu().numpy() for t in sim.final_state_by_id())
+    assert np.array_equal(x, ref_x) and np.array_equal(v, ref_v)
+    sim.sort()
+    sim.step(1)
+    got = gpu_state(sim)
+    sim.close()
+    for key in ("seg", "ids", "x", "v", "img", "tau"):
+        assert np.array_equal(got[key], want[key]), key
