@@ -226,31 +226,33 @@ int step_kernel_occupancy(FieldKind kind, int mode, int block, int items, bool e
 // the new counts and the next layout and swaps the buffers.
 constexpr int TAIL_BLOCK = 1024;
 constexpr int TAIL_WARPS = TAIL_BLOCK / 32;
+static_assert(TAIL_WARPS == 32 && TAIL_WARPS >= NBIN, "one warp per direction, one lane per warp");
 
 // Offset, inside destination d, of the leavers of source s in direction b:
 // the stayers of d, then the arrivals of d in source order (the destination's
-// table fin_tab), up to (s, b).  Lane b of one warp computes direction b.
+// table fin_tab), up to (s, b).  Warp b computes direction b: lane j reads
+// entry j of the table and its count, and the counts before (s, b) are
+// summed by a warp reduction -- two dependent loads per warp instead of a
+// walk along the table.
 __device__ __forceinline__ void tail_offsets(const StepArgs &a, int s, int64_t *s_off) {
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, b = threadIdx.x >> 5;
+  if (b >= NBIN || b == BIN_STAY) return;  // whole warps
   const Geom &g = a.geo;
-  if (lane < NBIN && lane != BIN_STAY) {
-    const int b = lane;
-    const int ps[3] = {s % g.P[0], (s / g.P[0]) % g.P[1], s / (g.P[0] * g.P[1])};
-    const int dir[3] = {b % 3 - 1, (b / 3) % 3 - 1, b / 9 - 1};
-    int pd[3];
+  const int ps[3] = {s % g.P[0], (s / g.P[0]) % g.P[1], s / (g.P[0] * g.P[1])};
+  const int dir[3] = {b % 3 - 1, (b / 3) % 3 - 1, b / 9 - 1};
+  int pd[3];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) pd[q] = (ps[q] + dir[q] + g.P[q]) % g.P[q];
-    const int d = pd[0] + g.P[0] * (pd[1] + g.P[1] * pd[2]);
-    const int me = s * NBIN + b;
-    int64_t off = a.m.stay_tot[d];
-    const int *tab = a.m.fin_tab + d * (NBIN - 1);
-    for (int j = 0; j < NBIN - 1; ++j) {
-      const int e = tab[j];
-      if (e < 0 || e == me) break;
-      off += a.m.bincnt[e];
-    }
-    s_off[b] = off;
-  }
+  for (int q = 0; q < 3; ++q) pd[q] = (ps[q] + dir[q] + g.P[q]) % g.P[q];
+  const int d = pd[0] + g.P[0] * (pd[1] + g.P[1] * pd[2]);
+  const int me = s * NBIN + b;
+  const int e = lane < NBIN - 1 ? __ldg(a.m.fin_tab + d * (NBIN - 1) + lane) : -1;
+  // the table ends at its first negative entry; (s, b) itself stops the sum
+  const unsigned stop = __ballot_sync(0xffffffffu, lane >= NBIN - 1 || e < 0 || e == me);
+  const int j = __ffs(stop) - 1;
+  long long c = lane < j ? (long long)a.m.bincnt[e] : 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) s_off[b] = a.m.stay_tot[d] + c;
 }
 
 // Place the packed leavers of source s (one block), in pack order, at their
@@ -268,7 +270,6 @@ __device__ __forceinline__ void tail_unpack(const StepArgs &a, int s, const int6
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ps[3] = {s % g.P[0], (s / g.P[0]) % g.P[1], s / (g.P[0] * g.P[1])};
   if (threadIdx.x < NBIN) s_run[threadIdx.x] = 0;
-  for (int i = threadIdx.x; i < TAIL_WARPS * NBIN; i += blockDim.x) (&s_wc[0][0])[i] = 0;
   __syncthreads();
   for (int64_t c0 = 0; c0 < nm; c0 += blockDim.x) {
     const int64_t i = c0 + threadIdx.x;
@@ -276,36 +277,41 @@ __device__ __forceinline__ void tail_unpack(const StepArgs &a, int s, const int6
     const int b = valid ? a.pack_bin[bA + i] : 255;
     const unsigned peers = __match_any_sync(0xffffffffu, b);
     const int rank = __popc(peers & ((1u << lane) - 1));
+    // row `warp` of s_wc: this warp's count per direction (only this warp
+    // touches its row outside the column scan below)
+    if (lane < NBIN) s_wc[warp][lane] = 0;
+    __syncwarp();
     if (valid && rank == 0) s_wc[warp][b] = __popc(peers);
     __syncthreads();
-    int woff = 0;
-    if (valid) {
-      woff = s_run[b];
-      for (int w = 0; w < warp; ++w) woff += s_wc[w][b];
+    // warp w < NBIN scans column w (direction w) over the warps of the chunk:
+    // each entry becomes the rank of that warp's first leaver of direction w
+    if (warp < NBIN) {
+      const int v = s_wc[lane][warp];
+      int incl = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      const int run = s_run[warp];
+      __syncwarp();
+      s_wc[lane][warp] = run + incl - v;
+      if (lane == 31) s_run[warp] = run + incl;
     }
     __syncthreads();
-    if (threadIdx.x < NBIN) {
-      int t = 0;
-      for (int w = 0; w < TAIL_WARPS; ++w) {
-        t += s_wc[w][threadIdx.x];
-        s_wc[w][threadIdx.x] = 0;
-      }
-      s_run[threadIdx.x] += t;
-    }
     if (valid) {
       const int dir[3] = {b % 3 - 1, (b / 3) % 3 - 1, b / 9 - 1};
       int pd[3];
 #pragma unroll
       for (int q = 0; q < 3; ++q) pd[q] = (ps[q] + dir[q] + g.P[q]) % g.P[q];
       const int d = pd[0] + g.P[0] * (pd[1] + g.P[1] * pd[2]);
-      const int64_t rel = s_off[b] + woff + rank;
+      const int64_t rel = s_off[b] + s_wc[warp][b] + rank;
       if (rel < capB[d]) {
         copy_rec(a.pack, bA + i, B, baseB[d] + rel);
       } else {
         latch(a.m.status, LCS_ERR_CAPACITY);
       }
     }
-    __syncthreads();
   }
 }
 
@@ -364,7 +370,7 @@ __global__ void __launch_bounds__(TAIL_BLOCK) k_tail(BatchArgs bt, int count_ste
     const int per = (ntile + P - 1) / P, t0 = s * per, t1 = min(ntile, t0 + per);
     for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) a.m.tile_status[t] = 0ull;
   }
-  if ((threadIdx.x >> 5) == 0) tail_offsets(a, s, s_off);
+  tail_offsets(a, s, s_off);
   __syncthreads();
   tail_unpack(a, s, s_off);
   if (threadIdx.x == 0) a.m.mig_tot[s] = 0;
