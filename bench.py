@@ -69,7 +69,6 @@ def library_source_hash() -> str:
     csrc = os.path.join(root, "paper_2604_11008_gb300", "csrc")
     files = sorted(glob.glob(os.path.join(csrc, "lcs_step_*.cu")) +
                    glob.glob(os.path.join(csrc, "*.cuh")))
-    files.append(os.path.join(root, "include", "lcs.h"))
     h = hashlib.sha256()
     for f in files:
         h.update(os.path.basename(f).encode())

@@ -603,7 +603,7 @@ __device__ __forceinline__ FieldBox owned_view(const StepArgs &a, const TileMeta
 
 template <int KIND, int ITEMS, bool EVOLVE, int STAGE, bool OWNED = false>
 __device__ __forceinline__ unsigned integrate_items(const StepArgs &a, const TileMeta &mt,
-                                                    BlockShared &sh, long long x[][3],
+                                                    int *hist, long long x[][3],
                                                     df v[][3], double tau[], uint32_t id[],
                                                     int img[][3], int bin[], df vs[][3]) {
   const Rec &A = a.buf[mt.ph];
@@ -652,7 +652,7 @@ __device__ __forceinline__ unsigned integrate_items(const StepArgs &a, const Til
         packed += 1u << 16;
       } else {
         packed += 1u;
-        atomicAdd(&sh.hist[b], 1);
+        atomicAdd(&hist[b], 1);
       }
     }
   }
@@ -755,7 +755,11 @@ __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockSha
     __syncthreads();
   };
   bool parked = false;
-  if (threadIdx.x < NBIN) sh.hist[threadIdx.x] = 0;
+  // per-direction leaver counts of a tile, in two buffers by iteration
+  // parity: a buffer is flushed and cleared after the scan barrier of its
+  // iteration and next written two iterations later, past further barriers
+  __shared__ int s_hist[2][NBIN];
+  if (threadIdx.x < 2 * NBIN) (&s_hist[0][0])[threadIdx.x] = 0;
   if (warp == ACQ) acquire(0);
   __syncthreads();
   for (int it = 0;; ++it) {
@@ -770,7 +774,7 @@ __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockSha
     unsigned packed = 0;
     if (fresh) {
       const int e = CAP == 1 ? 0 : cur.e;
-      packed = integrate_items<KIND, ITEMS, EVOLVE, STAGE, OWNED>(pb.a[e], cur, sh, x, v, tau,
+      packed = integrate_items<KIND, ITEMS, EVOLVE, STAGE, OWNED>(pb.a[e], cur, s_hist[it & 1], x, v, tau,
                                                                   id, img, bin, vs);
       if (warp == ACQ) acquire((it + 1) % 3);
       reload_rest<ITEMS>(pb.a[e], cur, tau, id, img, bin);
@@ -805,9 +809,10 @@ __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockSha
     __syncthreads();
     const StepArgs &a = pb.a[CAP == 1 ? 0 : cur.e];
     if (threadIdx.x < NBIN) {
-      if (threadIdx.x != BIN_STAY && sh.hist[threadIdx.x])
-        atomicAdd(&a.m.bincnt[cur.seg * NBIN + threadIdx.x], sh.hist[threadIdx.x]);
-      sh.hist[threadIdx.x] = 0;
+      int *hist = s_hist[it & 1];
+      if (threadIdx.x != BIN_STAY && hist[threadIdx.x])
+        atomicAdd(&a.m.bincnt[cur.seg * NBIN + threadIdx.x], hist[threadIdx.x]);
+      hist[threadIdx.x] = 0;
     }
     const unsigned excl = incl - packed + sh.warp[warp];
     int rs = (int)(excl >> 16), rm = (int)(excl & 0xffffu);
