@@ -28,8 +28,16 @@ __global__ void __launch_bounds__(SORT_BLOCK) k_upsweep(SortArgs s, const uint32
     const int t0 = s.tile_off[seg], nt = s.tile_off[seg + 1] - t0, jt = tile - t0;
     const int64_t a = s.cstart[seg] + (int64_t)jt * SORT_TILE;
     const int64_t e = min(s.cstart[seg + 1], a + SORT_TILE);
-    for (int64_t i = a + threadIdx.x; i < e; i += blockDim.x)
-      atomicAdd(&h[(key[i] >> shift) & (D - 1)], 1);
+    // all of a thread's keys in flight at once, then the counts
+    uint32_t kk[SORT_ITEMS];
+#pragma unroll
+    for (int r = 0; r < SORT_ITEMS; ++r) {
+      const int64_t i = a + r * SORT_BLOCK + threadIdx.x;
+      kk[r] = i < e ? key[i] : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < SORT_ITEMS; ++r)
+      if (a + r * SORT_BLOCK + threadIdx.x < e) atomicAdd(&h[(kk[r] >> shift) & (D - 1)], 1);
     __syncthreads();
     int *out = s.hist + (int64_t)t0 * D;
     for (int d = threadIdx.x; d < D; d += blockDim.x) out[(int64_t)d * nt + jt] = h[d];
@@ -157,12 +165,19 @@ __global__ void __launch_bounds__(SORT_BLOCK, 3) k_downsweep(SortArgs s, const u
     __syncthreads();
     uint32_t k[SORT_ITEMS], p[SORT_ITEMS];
     int rk[SORT_ITEMS];
+    // every key and payload of the thread in flight at once (the ranking
+    // below passes warp barriers, which loads inside it would wait behind)
 #pragma unroll
     for (int r = 0; r < SORT_ITEMS; ++r) {
       const int64_t i = a + warp * PER_WARP + r * 32 + lane;
       const bool valid = i < e;
       k[r] = valid ? kin[i] : 0u;
       p[r] = valid ? pin[i] : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < SORT_ITEMS; ++r) {
+      const int64_t i = a + warp * PER_WARP + r * 32 + lane;
+      const bool valid = i < e;
       const int dg = valid ? (int)((k[r] >> shift) & (D - 1)) : MAXD;
       const unsigned peers = __match_any_sync(0xffffffffu, dg);
       const int rank = __popc(peers & lt);
