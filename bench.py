@@ -61,19 +61,25 @@ def build_workload(name: str, device: str, n_override: int | None = None):
 # ---------------------------------------------------------------- traffic
 
 def library_source_hash() -> str:
-    """SHA-256 over the sources that define the step kernel (its templates,
-    the physics and arithmetic headers, the per-storage instantiations)."""
+    """SHA-256 over the code of the sources that define the step kernel (its
+    templates, the physics and arithmetic headers, the per-storage
+    instantiations), comments and whitespace removed."""
     import glob
     import hashlib
     root = os.path.dirname(os.path.abspath(__file__))
     csrc = os.path.join(root, "paper_2604_11008_gb300", "csrc")
     files = sorted(glob.glob(os.path.join(csrc, "lcs_step_*.cu")) +
                    glob.glob(os.path.join(csrc, "*.cuh")))
+    import re
     h = hashlib.sha256()
     for f in files:
         h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        with open(f, encoding="utf-8") as fh:
+            src = fh.read()
+        # code only: comments and layout do not change the kernels
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()
 
 

@@ -3,15 +3,17 @@
 // GB300 issues FP64 instructions (DFMA, DADD, DMUL and the f32<->f64
 // conversions) at roughly 1/70 of the FP32 rate, so a plain FP64 step is
 // bound by the FP64 pipe far below the memory roofline.  The DF step keeps
-// the particle state in FP64 memory but evaluates the interpolation and the
-// Heun increments with unevaluated sums of two floats (h + l, about 48
-// significant bits) built from error-free transformations:
+// positions in int64 fixed point (52 fraction bits, grid-cell units) and
+// velocities as float pairs in its record buffers, and evaluates the
+// interpolation and the Heun increments with unevaluated sums of two floats
+// (h + l, about 48 significant bits) built from error-free transformations:
 //   two_sum (Knuth 1969), fast_two_sum (Dekker 1971), and the exact product
-//   error fma(a, b, -a*b) (the FMA-based variant of Dekker's TwoProduct).
-// Conversions between double and float pairs use integer bit operations,
-// not the FP64 pipe.  The FP64 pipe is used only where the result must be an
-// exact FP64 function of the stored state: the product x * N/L that fixes
-// the cell (and the subdomain key), and the final x + dx, v + dv.
+// error fma(a, b, -a*b) (the FMA-based variant of Dekker's TwoProduct).
+// Position increments are added exactly in fixed point.  Conversions between
+// double and float pairs use integer bit operations, not the FP64 pipe; the
+// only FP64-pipe instructions on the Stokes path are the float -> int64
+// conversions of the fixed-point increments.  FP64 values appear only at the
+// boundary (import of the initial state, export of the state).
 #pragma once
 
 #include <cstdint>
