@@ -704,7 +704,6 @@ __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockSha
   // being rewritten.
   constexpr int ACQ = BLOCK / 32 - 1;
   __shared__ TileMeta s_meta[3];
-  __shared__ unsigned s_park_tot[2];
   const int n = pb.n, total = s_off[n];
   const bool lay_tau = pb.pf_tau != 0, lay_img = pb.pf_img != 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -755,6 +754,7 @@ __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockSha
     __syncthreads();
   };
   bool parked = false;
+  unsigned park_tot = 0;  // (stay, leave) counts of the parked tile
   // per-direction leaver counts of a tile, in two buffers by iteration
   // parity: a buffer is flushed and cleared after the scan barrier of its
   // iteration and next written two iterations later, past further barriers
@@ -779,7 +779,7 @@ __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockSha
       if (warp == ACQ) acquire((it + 1) % 3);
       reload_rest<ITEMS>(pb.a[e], cur, tau, id, img, bin);
     }
-    if (parked) write_out(s_meta[(it + 2) % 3], s_park_tot[(it + 1) & 1]);
+    if (parked) write_out(s_meta[(it + 2) % 3], park_tot);
     if (!fresh) break;
     // block scan of the fresh tile's (stay, leave) counts
     unsigned incl = packed;
@@ -790,23 +790,25 @@ __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockSha
     }
     if (lane == 31) sh.warp[warp] = incl;
     __syncthreads();
-    if (warp == 0) {
-      const unsigned wv = lane < BLOCK / 32 ? sh.warp[lane] : 0u;
+    // every warp scans the warp sums itself (no second barrier); the parked
+    // tile's total stays in a register of every thread
+    unsigned woff;
+    {
+      constexpr int NW = BLOCK / 32;
+      const unsigned wv = lane < NW ? sh.warp[lane] : 0u;
       unsigned wi = wv;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
+      for (int o = 1; o < NW; o <<= 1) {
         const unsigned y = __shfl_up_sync(0xffffffffu, wi, o);
         if (lane >= o) wi += y;
       }
-      if (lane < BLOCK / 32) sh.warp[lane] = wi - wv;
-      if (lane == BLOCK / 32 - 1) {
-        sh.tot = wi;
+      woff = __shfl_sync(0xffffffffu, wi - wv, warp);
+      park_tot = __shfl_sync(0xffffffffu, wi, NW - 1);
+      if (warp == 0 && lane == NW - 1) {
         const StepArgs &a = pb.a[CAP == 1 ? 0 : cur.e];
         publish_aggregate(a.m.tile_status, cur.tile, cur.t0, pack_sm(wi >> 16, wi & 0xffffu));
-        s_park_tot[it & 1] = wi;
       }
     }
-    __syncthreads();
     const StepArgs &a = pb.a[CAP == 1 ? 0 : cur.e];
     if (threadIdx.x < NBIN) {
       int *hist = s_hist[it & 1];
@@ -814,7 +816,7 @@ __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockSha
         atomicAdd(&a.m.bincnt[cur.seg * NBIN + threadIdx.x], hist[threadIdx.x]);
       hist[threadIdx.x] = 0;
     }
-    const unsigned excl = incl - packed + sh.warp[warp];
+    const unsigned excl = incl - packed + woff;
     int rs = (int)(excl >> 16), rm = (int)(excl & 0xffffu);
     const Rec &A = a.buf[cur.ph];
 #pragma unroll
