@@ -521,38 +521,49 @@ __device__ __forceinline__ int find_ensemble(const int *off, int n, int g) {
   return e;
 }
 
-// Shared-memory rows of a parked tile (mode 3): x0 x1 x2 v0 v1 v2 [tau] of
-// T doubles, id [img0 img1 img2] of T words, then T destination bins.
-// Stayers sit at their tile-local rank from the front, leavers at their
-// rank from the back.
+// Shared-memory rows of a parked tile (modes 3 and 4): x0 x1 x2 v0 v1 v2
+// [tau] of T doubles, id [img0 img1 img2] of T words, then T 16-bit words
+// holding the destination bin (bits 0-4) and the images crossed in this step
+// per axis (2 bits each, + 1).  Stayers sit at their tile-local rank from
+// the front, leavers at their rank from the back.  The id, tau_p and stored
+// image counts are not held by the integrating thread: they are copied from
+// the input record straight into the rows by asynchronous copies when the
+// tile is parked, and the parking thread waits for its copies before the
+// block barrier that precedes the write-out, one iteration later.
 template <int T>
 struct ParkLayout {
   __host__ __device__ static constexpr int bytes(bool tau, bool img) {
-    return (6 + (tau ? 1 : 0)) * T * 8 + (1 + (img ? 3 : 0)) * T * 4 + T;
+    return (6 + (tau ? 1 : 0)) * T * 8 + (1 + (img ? 3 : 0)) * T * 4 + 2 * T;
   }
+  __host__ __device__ static constexpr int flags(bool tau, bool img) { return bytes(tau, img) - 2 * T; }
 };
 
-// Stage-velocity rows (migration per stage) follow the bins: 3 rows of T
-// float pairs at offset ParkLayout<T>::bytes(tau, img).
+// Stage-velocity rows (migration per stage) follow the flag words: 3 rows of
+// T float pairs at offset ParkLayout<T>::bytes(tau, img).  Row j receives the
+// particle in input slot i of A; dimg are the images crossed in this step.
 template <int T>
 __device__ __forceinline__ void park_put(unsigned char *pk, bool lay_tau, bool lay_img,
-                                         const Rec &A, int j, const long long x[3],
-                                         const df v[3], double tau, uint32_t id,
-                                         const int img[3], int bin, const df *vs = nullptr) {
+                                         const Rec &A, int64_t i, int j, const long long x[3],
+                                         const df v[3], const int dimg[3], int bin,
+                                         const df *vs = nullptr) {
   long long *r8 = (long long *)pk;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     r8[s * T + j] = x[s];
     ((float2 *)r8)[(3 + s) * T + j] = df_to2(v[s]);
   }
-  if (A.tau) r8[6 * T + j] = __double_as_longlong(tau);
+  if (A.tau) cp_async8(r8 + 6 * T + j, A.tau + i);
   uint32_t *r4 = (uint32_t *)(pk + (lay_tau ? 7 : 6) * T * 8);
-  r4[j] = id;
+  cp_async4(r4 + j, A.id + i);
+  unsigned fl = (unsigned)bin;
   if (A.img[0]) {
 #pragma unroll
-    for (int s = 0; s < 3; ++s) r4[(1 + s) * T + j] = (uint32_t)img[s];
+    for (int s = 0; s < 3; ++s) {
+      cp_async4(r4 + (1 + s) * T + j, A.img[s] + i);
+      fl |= (unsigned)(dimg[s] + 1) << (5 + 2 * s);
+    }
   }
-  pk[ParkLayout<T>::bytes(lay_tau, lay_img) - T + j] = (unsigned char)bin;
+  ((uint16_t *)(pk + ParkLayout<T>::flags(lay_tau, lay_img)))[j] = (uint16_t)fl;
   if (vs) {
     float2 *rv = (float2 *)(pk + ParkLayout<T>::bytes(lay_tau, lay_img));
 #pragma unroll
@@ -573,11 +584,13 @@ __device__ __forceinline__ void park_get(const unsigned char *pk, bool lay_tau, 
   if (R.tau) R.tau[i] = __longlong_as_double(r8[6 * T + j]);
   const uint32_t *r4 = (const uint32_t *)(pk + (lay_tau ? 7 : 6) * T * 8);
   R.id[i] = r4[j];
+  const unsigned fl = ((const uint16_t *)(pk + ParkLayout<T>::flags(lay_tau, lay_img)))[j];
   if (R.img[0]) {
 #pragma unroll
-    for (int s = 0; s < 3; ++s) R.img[s][i] = (int32_t)r4[(1 + s) * T + j];
+    for (int s = 0; s < 3; ++s)
+      R.img[s][i] = (int32_t)r4[(1 + s) * T + j] + (int)((fl >> (5 + 2 * s)) & 3u) - 1;
   }
-  if (bins) bins[i] = pk[ParkLayout<T>::bytes(lay_tau, lay_img) - T + j];
+  if (bins) bins[i] = (uint8_t)(fl & 31u);
   if (R.vs[0]) {
     const float2 *rv = (const float2 *)(pk + ParkLayout<T>::bytes(lay_tau, lay_img));
 #pragma unroll
@@ -616,9 +629,9 @@ __device__ __forceinline__ unsigned integrate_items(const StepArgs &a, const Til
   for (int k = 0; k < ITEMS; ++k) {
     bin[k] = -2;
     if (l0 + k < mt.cnt) {
-      // id, tau_p and the image counts are read again after the integration
-      // (reload_rest), so that they hold no registers across the gathers;
-      // img counts the images crossed in this step until then
+      // id, tau_p and the stored image counts go from the input record to
+      // the park rows by asynchronous copies (park_put), so that they hold
+      // no registers here; img counts the images crossed in this step
       load_motion(A, rec_slot(a, mt, l0 + k), x[k], v[k], tau[k], a.tau_const);
       img[k][0] = img[k][1] = img[k][2] = 0;
       if (STAGE == 0) {
@@ -659,27 +672,6 @@ __device__ __forceinline__ unsigned integrate_items(const StepArgs &a, const Til
   if (bad & 1) latch(a.m.status, LCS_ERR_NONFINITE);
   if (bad & 2) latch(a.m.status, LCS_ERR_DISPLACEMENT);
   return packed;
-}
-
-// The rest of the integrated records: id and tau_p as stored, image counts
-// as stored plus the images crossed in this step.
-template <int ITEMS>
-__device__ __forceinline__ void reload_rest(const StepArgs &a, const TileMeta &mt,
-                                            double tau[], uint32_t id[], int img[][3],
-                                            const int bin[]) {
-  const Rec &A = a.buf[mt.ph];
-  const int64_t l0 = mt.first + (int64_t)threadIdx.x * ITEMS;
-#pragma unroll
-  for (int k = 0; k < ITEMS; ++k) {
-    if (bin[k] == -2) continue;
-    const int64_t i = rec_slot(a, mt, l0 + k);
-    id[k] = A.id[i];
-    if (A.tau) tau[k] = A.tau[i];
-    if (A.img[0]) {
-#pragma unroll
-      for (int s = 0; s < 3; ++s) img[k][s] += A.img[s][i];
-    }
-  }
 }
 
 // Mode 3, deferred scatter: a block integrates its next tile while its
@@ -737,6 +729,7 @@ __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockSha
         }
       }
     }
+    cp_async_wait_all();  // this thread's copies into the parked rows
     __syncthreads();
     const unsigned long long ex = sh.excl;
     const int nstay = (int)(tot >> 16), nmig = (int)(tot & 0xffffu);
@@ -777,7 +770,6 @@ __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockSha
       packed = integrate_items<KIND, ITEMS, EVOLVE, STAGE, OWNED>(pb.a[e], cur, s_hist[it & 1], x, v, tau,
                                                                   id, img, bin, vs);
       if (warp == ACQ) acquire((it + 1) % 3);
-      reload_rest<ITEMS>(pb.a[e], cur, tau, id, img, bin);
     }
     if (parked) write_out(s_meta[(it + 2) % 3], park_tot);
     if (!fresh) break;
@@ -823,7 +815,8 @@ __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockSha
     for (int k = 0; k < ITEMS; ++k) {
       if (bin[k] == -2) continue;
       const int j = bin[k] == BIN_STAY ? rs++ : T - 1 - rm++;
-      park_put<T>(pk, lay_tau, lay_img, A, j, x[k], v[k], tau[k], id[k], img[k], bin[k],
+      park_put<T>(pk, lay_tau, lay_img, A, rec_slot(a, cur, cur.first + threadIdx.x * ITEMS + k),
+                  j, x[k], v[k], img[k], bin[k],
                   STAGE == 1 ? vs[k] : nullptr);
     }
     parked = true;
@@ -955,8 +948,8 @@ __global__ void __launch_bounds__(BLOCK, (step_min_blocks<KIND, BLOCK, ITEMS>())
 // the two record buffers (mode 2) or the parked tile (modes 3 and 4).
 constexpr int step_dyn_smem(int kind, int mode, int tile, bool tau, bool img, bool vs = false) {
   return mode == 4 ? step_dyn_smem(kind, 3, tile, tau, img, vs)
-         : mode == 3 ? (6 + (tau ? 1 : 0)) * tile * 8 + (1 + (img ? 3 : 0)) * tile * 4 + tile +
-                           (vs ? 3 * tile * 8 : 0)
+         : mode == 3 ? (6 + (tau ? 1 : 0)) * tile * 8 + (1 + (img ? 3 : 0)) * tile * 4 +
+                           2 * tile + (vs ? 3 * tile * 8 : 0)
          : mode == 1 ? (kind != FK_F64 ? STAGE_BYTES : 0)
          : mode == 2 ? 2 * ((6 + (tau ? 1 : 0)) * (tile + 2) * 8 +
                             (1 + (img ? 3 : 0)) * (tile + 4) * 4)

@@ -48,6 +48,24 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
       : "memory");
 }
 
+// Per-thread asynchronous copy of 4 bytes from global to shared memory
+// (both 4-byte aligned); complete after this thread's cp_async_wait_all.
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src)
+               : "memory");
+}
+
+// The same for 8 bytes (both 8-byte aligned).
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src)
+               : "memory");
+}
+
+// Wait for all of this thread's cp_async4 / cp_async8 copies.
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 // Non-blocking test of the phase with the given parity.
 __device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, unsigned parity) {
   unsigned ok;
