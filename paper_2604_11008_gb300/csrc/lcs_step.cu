@@ -274,14 +274,19 @@ __device__ __forceinline__ void tail_unpack(const StepArgs &a, int s, const int6
   for (int64_t c0 = 0; c0 < nm; c0 += blockDim.x) {
     const int64_t i = c0 + threadIdx.x;
     const bool valid = i < nm;
-    const int b = valid ? a.pack_bin[bA + i] : 255;
+    int b = valid ? a.pack_bin[bA + i] : 255;
+    if (valid && (b >= NBIN || b == BIN_STAY)) {  // not a leaver's bin: report, skip
+      latch(a.m.status, LCS_ERR_STATE);
+      b = 255;
+    }
+    const bool leaver = b != 255;
     const unsigned peers = __match_any_sync(0xffffffffu, b);
     const int rank = __popc(peers & ((1u << lane) - 1));
     // row `warp` of s_wc: this warp's count per direction (only this warp
     // touches its row outside the column scan below)
     if (lane < NBIN) s_wc[warp][lane] = 0;
     __syncwarp();
-    if (valid && rank == 0) s_wc[warp][b] = __popc(peers);
+    if (leaver && rank == 0) s_wc[warp][b] = __popc(peers);
     __syncthreads();
     // warp w < NBIN scans column w (direction w) over the warps of the chunk:
     // each entry becomes the rank of that warp's first leaver of direction w
@@ -299,7 +304,7 @@ __device__ __forceinline__ void tail_unpack(const StepArgs &a, int s, const int6
       if (lane == 31) s_run[warp] = run + incl;
     }
     __syncthreads();
-    if (valid) {
+    if (leaver) {
       const int dir[3] = {b % 3 - 1, (b / 3) % 3 - 1, b / 9 - 1};
       int pd[3];
 #pragma unroll
