@@ -314,22 +314,43 @@ __global__ void k_keys_cell(StepArgs a, uint32_t *key, uint32_t *pay, int B, int
   const int64_t *base = a.m.lay_base[ph];
   const int P = a.geo.Ptot;
   const int64_t n = a.m.cstart[P];
+  // brick edge a power of two (the default 8): shifts and masks instead of
+  // divisions (the same key)
+  const int lb = (B & (B - 1)) == 0 ? __ffs(B) - 1 : -1;
+  const uint32_t B3 = (uint32_t)(B * B * B);
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int seg = i < n ? find_segment64(a.m.cstart, P, i) : 0;  // then tracked: i only grows
+  int seg_c = -1;  // segment whose origin is in o[]
+  int64_t seg_s = 0, seg_b = 0;
+  int o[3] = {0, 0, 0};
   for (; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     while (seg + 1 < P && a.m.cstart[seg + 1] <= i) ++seg;
-    const int64_t slot = base[seg] + (i - a.m.cstart[seg]);
-    const int ps[3] = {seg % a.geo.P[0], (seg / a.geo.P[0]) % a.geo.P[1],
-                       seg / (a.geo.P[0] * a.geo.P[1])};
+    if (seg != seg_c) {
+      seg_c = seg;
+      seg_s = a.m.cstart[seg];
+      seg_b = base[seg];
+      const int ps[3] = {seg % a.geo.P[0], (seg / a.geo.P[0]) % a.geo.P[1],
+                         seg / (a.geo.P[0] * a.geo.P[1])};
+#pragma unroll
+      for (int s = 0; s < 3; ++s) o[s] = ps[s] * a.geo.W[s];
+    }
+    const int64_t slot = seg_b + (i - seg_s);
     int l[3];
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
       const int c = cell_of(a.geo, A.x[s][slot]);
-      l[s] = min(max(c - ps[s] * a.geo.W[s], 0), a.geo.W[s] - 1);
+      l[s] = min(max(c - o[s], 0), a.geo.W[s] - 1);
     }
-    const uint32_t brick = (uint32_t)((l[2] / B * nby + l[1] / B) * nbx + l[0] / B);
-    const uint32_t in = (uint32_t)(((l[2] % B) * B + l[1] % B) * B + l[0] % B);
-    key[i] = brick * (uint32_t)(B * B * B) + in;
+    uint32_t brick, in;
+    if (lb >= 0) {
+      const int m = B - 1;
+      brick = (uint32_t)((((l[2] >> lb) * nby + (l[1] >> lb)) * nbx) + (l[0] >> lb));
+      in = (uint32_t)((((l[2] & m) << lb) + (l[1] & m)) << lb) + (uint32_t)(l[0] & m);
+    } else {
+      brick = (uint32_t)((l[2] / B * nby + l[1] / B) * nbx + l[0] / B);
+      in = (uint32_t)(((l[2] % B) * B + l[1] % B) * B + l[0] % B);
+    }
+    key[i] = brick * B3 + in;
     pay[i] = (uint32_t)slot;
   }
 }
