@@ -185,9 +185,9 @@ lcs_status lcs_init(const lcs_desc *ens, int n_ens, void *stream, lcs_ctx **out)
  * computes only the permutation: the next step kernel reads its records
  * through it, so the sorted records are written once, by that step.  A
  * permutation still pending when another call needs the records in sorted
- * order (lcs_get_state, lcs_get_state_by_id, lcs_migrate,
- * lcs_pair_histogram, a checkpoint) is applied then; none of this is
- * visible in any result. */
+ * order is read through (lcs_get_state) or applied then (lcs_get_state_by_id,
+ * lcs_migrate, lcs_pair_histogram, a checkpoint); none of this is visible in
+ * any result. */
 lcs_status lcs_step(lcs_ctx *ctx, int64_t nsteps);
 
 /* Standalone migration pass on the current state (asynchronous): a stable

@@ -1057,13 +1057,15 @@ lcs_status lcs_get_state(lcs_ctx *c, int ens, double *x, double *v, double *tau,
   if (!c) return LCS_ERR_ARG;
   if (c->failed) return LCS_ERR_STATE;
   if (ens < 0 || ens >= (int)c->ens.size()) return reject(c, "bad ensemble");
-  lcs_status mr = materialize(c);  // the records in their sorted order
-  if (mr != LCS_OK) return mr;
   Ens &e = c->ens[ens];
   cudaStream_t st = c->st;
   const int P = e.a.geo.Ptot;
   Rec tmp = e.a.pack;
-  k_compact<<<grid_for(e.np, 256, c->sms * 8), 256, 0, st>>>(e.a, tmp);
+  // the records in their sorted order: a pending sort permutation is read
+  // through (and stays pending for the next step)
+  StepArgs ea = e.a;
+  ea.perm = e.perm >= 0 ? e.s.pay[e.perm] : nullptr;
+  k_compact<<<grid_for(e.np, 256, c->sms * 8), 256, 0, st>>>(ea, tmp);
   k_export<<<grid_for(e.np, 256, c->sms * 8), 256, 0, st>>>(tmp, e.np, e.a.geo);
   c->launches += 2;
   CK(cudaGetLastError());

@@ -525,8 +525,18 @@ __global__ void k_compact(StepArgs a, Rec out) {
   const int64_t n = a.m.cstart[P];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int seg = find_segment64(a.m.cstart, P, i);
-    copy_rec(A, base[seg] + (i - a.m.cstart[seg]), out, i);
+    int64_t slot;
+    if (a.perm) {  // a pending cell-sort permutation: rank i is input slot perm[i]
+      slot = a.perm[i];
+      if (slot >= a.cap) {  // corrupt permutation: report, never read out of bounds
+        latch(a.m.status, LCS_ERR_STATE);
+        continue;
+      }
+    } else {
+      const int seg = find_segment64(a.m.cstart, P, i);
+      slot = base[seg] + (i - a.m.cstart[seg]);
+    }
+    copy_rec(A, slot, out, i);
   }
 }
 

@@ -198,3 +198,27 @@ def test_pending_sort_across_calls(lcs, first, second):
     sim.close()
     for key in ("seg", "ids", "x", "v", "img", "tau"):
         assert np.array_equal(got[key], want[key]), key
+
+
+def test_state_read_through_pending_sort(lcs):
+    """lcs_get_state right after a sort step reads the records through the
+    pending permutation (which stays pending): the state equals that of a
+    mode that applies every sort at once, then and after further steps."""
+    case = dense_case(906, 12, 9001)
+    kw = dict(sub=(3, 2, 2), sort_every=4, sort_brick=2, kernel="df", field_dtype="f64")
+
+    def make(cfg):
+        sim = lcs.Simulator(case["field"], case["x0"], case["v0"], case["dt"], tau=case["tau"],
+                            tau_const=case["tau_const"], g=case["g"], track_images=True, **kw)
+        sim.set_step_config(*cfg)
+        return sim
+
+    fused, plain = make(DEFERRED[2]), make(UNSTAGED)
+    for n in (8, 3, 1):  # the first and the last read follow a sort
+        fused.step(n)
+        plain.step(n)
+        a, b = gpu_state(fused), gpu_state(plain)
+        for key in ("seg", "ids", "x", "v", "img", "tau"):
+            assert np.array_equal(a[key], b[key]), (n, key)
+    fused.close()
+    plain.close()
