@@ -624,10 +624,10 @@ lcs_status setup_batch(lcs_ctx *c) {
   }
   c->owned = c->ens[0].d.owned_field != 0;
   // default step kernel (lcs_tune / lcs_set_step_config change it): the
-  // deferred scatter, one particle per thread (two for BF16 fields), the
-  // fastest of the configurations on the 16.8M-particle workload
+  // deferred scatter, one particle per thread (two for FP32 and BF16
+  // fields), the fastest of the configurations on the 16.8M-particle workload
   c->cfg.assign(c->ens.size(),
-                StepCfg{256, c->kind == FK_BF16 ? 2 : 1,
+                StepCfg{256, c->kind == FK_BF16 || c->kind == FK_F32 ? 2 : 1,
                         c->owned ? LCS_STEP_OWNED_FIELD : LCS_STEP_DEFERRED});
   c->total_tiles = 0;
   c->total_P = 0;

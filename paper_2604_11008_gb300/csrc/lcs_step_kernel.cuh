@@ -826,15 +826,17 @@ __device__ __forceinline__ void step_deferred(const StepGroup<CAP> &pb, BlockSha
 // Persistent step kernel with block tiles: blocks take tile ids from one
 // counter in order (predecessors always belong to running blocks).
 // Resident threads per SM asked of the compiler (so registers per thread,
-// measured): 512 for the all-FP64 kernel (128 registers), 768 for the
-// float-float kernel with two particles per thread (80), 1024 otherwise (64).
+// measured): 512 for the all-FP64 kernel (128 registers), 768 with two
+// particles per thread (80: no spills; at 64 the FP32 kernel spilled and ran
+// 7 % slower), 1024 with one (64).
 #ifndef LCS_DF1_THREADS
 #define LCS_DF1_THREADS 1024
 #endif
 template <int KIND, int BLOCK, int ITEMS>
 constexpr int step_min_blocks() {
   return KIND == FK_F64 ? 512 / BLOCK
-         : KIND == FK_DF ? (ITEMS == 2 ? 768 : LCS_DF1_THREADS) / BLOCK
+         : ITEMS == 2   ? 768 / BLOCK
+         : KIND == FK_DF ? LCS_DF1_THREADS / BLOCK
                          : 1024 / BLOCK;
 }
 
