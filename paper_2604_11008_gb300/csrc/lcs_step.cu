@@ -320,32 +320,99 @@ __device__ __forceinline__ void tail_unpack(const StepArgs &a, int s, const int6
   }
 }
 
-// Last block of an ensemble: new counts (stayers + arrivals), the capacity
-// check, the next layout, the reset of the per-step counters, and the swap:
-// the old input buffer becomes the next output with the new layout, the
-// output becomes the input.
+// New count of destination d (stayers + arrivals) and the capacity check,
+// by one warp: lane j reads entry j of d's arrival table and its count.
+// Every block computes its own subdomain's count while the others unpack,
+// so the last block only lays out.
+__device__ __forceinline__ void tail_count(const StepArgs &a, int d) {
+  const int lane = threadIdx.x & 31;
+  const int ph = *a.m.phase;
+  const int e = lane < NBIN - 1 ? a.m.fin_tab[d * (NBIN - 1) + lane] : -1;
+  long long c = e >= 0 ? (long long)a.m.bincnt[e] : 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) {
+    const int64_t tot = a.m.stay_tot[d] + c;
+    if (tot > a.m.lay_cap[ph ^ 1][d]) latch(a.m.status, LCS_ERR_CAPACITY);
+    a.m.cnt[d] = tot;
+  }
+}
+
+// The layout of the new counts (the same as layout_from_counts): compacted
+// starts, step / sort tile prefixes and the next window layout, with the
+// four exclusive scans taken together -- one warp-sum barrier and one
+// broadcast barrier per 1024 segments instead of three per scan.
+__device__ __forceinline__ void tail_layout(int P, int step_tile, const int64_t *cnt,
+                                            int64_t *cstart, int *tile_off, int *stile_off,
+                                            int64_t *base, int64_t *cap) {
+  __shared__ int64_t s_w[4][TAIL_WARPS];
+  __shared__ int64_t s_tot[4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t carry[4] = {0, 0, 0, 0};
+  for (int d0 = 0; d0 < P; d0 += TAIL_BLOCK) {
+    const int d = d0 + threadIdx.x;
+    const int64_t c = d < P ? cnt[d] : 0;
+    int64_t v[4];
+    v[0] = c;                                             // particles
+    v[1] = d < P ? c + c / 16 + SLACK_MIN : 0;            // window capacity
+    v[2] = d < P ? (c + step_tile - 1) / step_tile : 0;   // step tiles
+    v[3] = d < P ? (c + SORT_TILE - 1) / SORT_TILE : 0;   // sort tiles
+    int64_t inc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      inc[q] = v[q];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, inc[q], o);
+        if (lane >= o) inc[q] += y;
+      }
+      if (lane == 31) s_w[q][warp] = inc[q];
+    }
+    __syncthreads();
+    if (warp < 4) {  // warp q scans the warp sums of value q
+      const int64_t wv = s_w[warp][lane];
+      int64_t wi = wv;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += y;
+      }
+      s_w[warp][lane] = wi - wv;
+      if (lane == 31) s_tot[warp] = wi;
+    }
+    __syncthreads();
+    int64_t ex[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ex[q] = carry[q] + inc[q] - v[q] + s_w[q][warp];
+    if (d < P) {
+      if (cstart) cstart[d] = ex[0];
+      if (base) base[d] = ex[1];
+      if (cap) cap[d] = v[1];
+      if (tile_off) tile_off[d] = (int)ex[2];
+      if (stile_off) stile_off[d] = (int)ex[3];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) carry[q] += s_tot[q];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (cstart) cstart[P] = carry[0];
+    if (tile_off) tile_off[P] = (int)carry[2];
+    if (stile_off) stile_off[P] = (int)carry[3];
+  }
+}
+
+// Last block of an ensemble (every count is in place): the reset of the
+// per-step counters, the next layout, and the swap: the old input buffer
+// becomes the next output with the new layout, the output becomes the input.
 __device__ __forceinline__ void tail_finish(const StepArgs &a, int count_step) {
   const int P = a.geo.Ptot;
   const int ph = *a.m.phase;
-  const int64_t *capB = a.m.lay_cap[ph ^ 1];
-  const int lane = threadIdx.x & 31;
-  for (int d = threadIdx.x >> 5; d < P; d += TAIL_WARPS) {
-    const int e = lane < NBIN - 1 ? a.m.fin_tab[d * (NBIN - 1) + lane] : -1;
-    long long c = e >= 0 ? (long long)a.m.bincnt[e] : 0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if (lane == 0) {
-      const int64_t tot = a.m.stay_tot[d] + c;
-      if (tot > capB[d]) latch(a.m.status, LCS_ERR_CAPACITY);
-      a.m.cnt[d] = tot;
-    }
-  }
-  __syncthreads();
   // every (source, direction) count and stayer total has been read
   for (int i = threadIdx.x; i < P * NBIN; i += blockDim.x) a.m.bincnt[i] = 0;
   for (int d = threadIdx.x; d < P; d += blockDim.x) a.m.stay_tot[d] = 0;
-  layout_from_counts(P, a.step_tile, a.m.cnt, a.m.cstart, a.m.tile_off, a.m.stile_off,
-                     a.m.next_base, a.m.next_cap);
+  tail_layout(P, a.step_tile, a.m.cnt, a.m.cstart, a.m.tile_off, a.m.stile_off,
+              a.m.next_base, a.m.next_cap);
   __syncthreads();
   for (int d = threadIdx.x; d < P; d += blockDim.x) {
     a.m.lay_base[ph][d] = a.m.next_base[d];
@@ -375,7 +442,8 @@ __global__ void __launch_bounds__(TAIL_BLOCK) k_tail(BatchArgs bt, int count_ste
     const int per = (ntile + P - 1) / P, t0 = s * per, t1 = min(ntile, t0 + per);
     for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) a.m.tile_status[t] = 0ull;
   }
-  tail_offsets(a, s, s_off);
+  tail_offsets(a, s, s_off);  // warps 0-26
+  if ((threadIdx.x >> 5) == TAIL_WARPS - 1) tail_count(a, s);
   __syncthreads();
   tail_unpack(a, s, s_off);
   if (threadIdx.x == 0) a.m.mig_tot[s] = 0;
