@@ -321,13 +321,15 @@ __global__ void k_keys_cell(StepArgs a, uint32_t *key, uint32_t *pay, int B, int
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int seg = i < n ? find_segment64(a.m.cstart, P, i) : 0;  // then tracked: i only grows
   int seg_c = -1;  // segment whose origin is in o[]
-  int64_t seg_s = 0, seg_b = 0;
+  int64_t seg_s = 0, seg_b = 0, seg_e = 0;
   int o[3] = {0, 0, 0};
   for (; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    while (seg + 1 < P && a.m.cstart[seg + 1] <= i) ++seg;
+    if (seg_c >= 0 && i >= seg_e)  // past the segment in registers: find the next
+      while (seg + 1 < P && a.m.cstart[seg + 1] <= i) ++seg;
     if (seg != seg_c) {
       seg_c = seg;
       seg_s = a.m.cstart[seg];
+      seg_e = a.m.cstart[seg + 1];
       seg_b = base[seg];
       const int ps[3] = {seg % a.geo.P[0], (seg / a.geo.P[0]) % a.geo.P[1],
                          seg / (a.geo.P[0] * a.geo.P[1])};
