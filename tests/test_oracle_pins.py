@@ -642,3 +642,28 @@ def test_openmp_build_of_the_oracle_gives_identical_bits():
     a, b = out
     for k in ("x", "v", "img", "ids", "seg"):
         assert np.array_equal(getattr(a, k), getattr(b, k)), k
+
+
+def test_loss_worked_example_and_image_invariance():
+    """orc_loss, the adjoint's objective: the mean over all n particles of the
+    (masked) squared distance between the unwrapped final position X + L img
+    and the target.  Worked by hand on two particles with binary-exact
+    values, so that a dropped image term, a dropped component or a mean over
+    the masked count instead of n changes the result; and the same loss when
+    a position moves by one box length while its image count moves back."""
+    Lb = 2.0 * np.pi
+    x = np.array([[1.0, 0.5], [2.0, 0.25], [3.0, 0.0]])
+    img = np.array([[1, 0], [0, 0], [-1, 0]], np.int32)
+    target = np.array([[1.0 + Lb, 0.0], [2.0, 0.0], [3.0 - Lb, 0.0]])
+    # particle 0 sits on its target once unwrapped; particle 1 is
+    # (0.5, 0.25, 0) away: 0.25 + 0.0625 = 0.3125; mean over n = 2
+    assert oracle.loss(Lb, x, img, target) == 0.15625
+    assert oracle.loss(Lb, x, img, target, mask=np.array([1.0, 2.0])) == 0.3125
+    assert oracle.loss(Lb, x, img, target, mask=np.array([0.0, 1.0])) == 0.15625
+    # without image counts particle 0 is one box length off in x and z
+    assert oracle.loss(Lb, x, None, target) == pytest.approx((2 * Lb * Lb + 0.3125) / 2,
+                                                             rel=1e-15)
+    x2, img2 = x.copy(), img.copy()
+    x2[1, 1] += Lb
+    img2[1, 1] -= 1
+    assert oracle.loss(Lb, x2, img2, target) == pytest.approx(0.15625, abs=1e-15)
